@@ -1,0 +1,191 @@
+/*
+ * cqk.h -- C ABI of libcqk, a B300 (sm_103a) solver for the continuous quadratic
+ * knapsack problem (CQK) by the semismooth Newton method of Secchin & Silva,
+ * "Parallel Newton methods for the continuous quadratic knapsack problem: A
+ * Jacobi and Gauss-Seidel tale" (arXiv 2603.15910).
+ *
+ *   (CQK)   min  1/2 x'Dx - a'x   s.t.  b'x = r,  l <= x <= u,
+ *           D = diag(d), d > 0, b > 0 (Sec. 1, eq. (CQK)); l_i may be -inf and
+ *           u_i may be +inf.
+ *
+ * The dual multiplier lambda parametrises x_i(lambda) = clip((a_i + lambda b_i)/d_i,
+ * l_i, u_i) (Sec. 2.1, eq. (xopt)); x(lambda*) is optimal iff
+ * phi(lambda*) = b'x(lambda*) = r (eq. (opt)).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every array argument (a, b, d, l, u, y, x, g, gradients, masks, offsets, info,
+ *    workspace) is a DEVICE pointer of the current CUDA device, owned by the
+ *    caller.  The library allocates no memory and keeps no pointer after the call
+ *    returns.  16-byte alignment of the arrays enables 128-bit loads; unaligned
+ *    arrays are accepted and read with scalar loads.
+ *  - dtype selects the storage of every floating-point array of the call:
+ *    CQK_F64 (double) or CQK_F32 (float).  Scalars (r, lambda, sums) are always
+ *    double; with CQK_F32 the multiplier is still kept and updated in double.
+ *  - stream is a cudaStream_t passed as void*; NULL means the legacy default
+ *    stream.  Every call is asynchronous on that stream and does not synchronise
+ *    the host (except cqk_solve with n = 0, which writes info synchronously).
+ *  - workspace/ws_bytes: caller-provided device scratch of at least
+ *    cqk_workspace_bytes(...) bytes, 256-byte aligned.  It is overwritten; calls
+ *    that may run concurrently need distinct workspaces.
+ *  - Two levels of error reporting:
+ *      return value   host-detectable problems: CQK_BAD_ARG (n < 0, NULL where
+ *                     an array is required, bad dtype, workspace too small or
+ *                     misaligned, r not usable) or CQK_CUDA_ERROR (a launch
+ *                     failed; cqk_last_cuda_error() gives the cudaError_t).
+ *                     Nothing is launched when the return value is not CQK_OK.
+ *      info_dev       the outcome of the solve, written on the device at the
+ *                     end of the call (status CQK_OK, CQK_INFEASIBLE,
+ *                     CQK_MAXITER, CQK_BAD_INPUT, CQK_TIMEOUT).  Read it after
+ *                     synchronising the stream.
+ */
+#ifndef CQK_H
+#define CQK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { CQK_F64 = 0, CQK_F32 = 1 } cqk_dtype;
+
+typedef enum {
+    CQK_OK = 0,          /* solved                                                         */
+    CQK_INFEASIBLE = 1,  /* r outside [b'l, b'u]: no breakpoint in the needed direction    */
+                         /* (Alg. 1, the zero-derivative branches)                         */
+    CQK_MAXITER = 2,     /* max_iter phi evaluations without meeting a stopping test       */
+    CQK_BAD_INPUT = 3,   /* d <= 0, b <= 0, l > u, or a NaN in the data (sanity checks of  */
+                         /* Sec. 5.1.1)                                                    */
+    CQK_NONDIFF = 4,     /* backward: the free set is empty, lambda is not differentiable  */
+    CQK_TIMEOUT = 5,     /* a device-wide wait exceeded spin_limit_us; results invalid     */
+    CQK_CUDA_ERROR = 6,  /* a CUDA call failed (return value only)                         */
+    CQK_BAD_ARG = 7      /* invalid host argument (return value only)                      */
+} cqk_status;
+
+typedef enum {
+    CQK_INIT_FORMULA = 0, /* eq. (CQKlambda0) with J = all variables; for the simplex and    */
+                          /* l1 ball also line 1 of Alg. 4 (lambda_0 >= min_i(-y_i))         */
+    CQK_INIT_CONDAT = 1,  /* simplex / l1 only: Alg. 2 run independently on every chunk of a */
+                          /* fixed partition, lambda_0 from eq. (lambdaJ) on the union of the */
+                          /* J's (Sec. 4); the partition is reported in cqk_info             */
+    CQK_INIT_GIVEN = 3    /* lambda_0 = options.lambda0                                      */
+} cqk_init;
+
+/* Which test ended the Newton loop (cqk_info.stop). */
+typedef enum {
+    CQK_STOP_NONE = 0,
+    CQK_STOP_EXACT = 1,    /* phi(lambda_k) == r                                (Alg. 1, Alg. 4) */
+    CQK_STOP_RESIDUAL = 2, /* |phi - r| < eps^{3/4}(sum|b_i x_i| + |r|)        (Sec. 4, crit. 1) */
+    CQK_STOP_STEP = 3,     /* |(phi - r)/phi'| < eps^{3/4}                      (Sec. 4, crit. 2) */
+    CQK_STOP_SAME = 4,     /* lambda_{k+1} == lambda_k                          (Sec. 4, crit. 2) */
+    CQK_STOP_BRACKET = 5,  /* upper - lower < eps^{3/4} max(|upper|, |lower|)   (Sec. 4, crit. 3) */
+    CQK_STOP_BELOW = 6,    /* phi(lambda_k) <= r, k >= 1                        (Alg. 4)          */
+    CQK_STOP_INSIDE = 7    /* l1 ball: sum |y_i| <= r, x = y                    (Sec. 3.2)        */
+} cqk_stop;
+
+typedef struct cqk_options {
+    int32_t max_iter;       /* cap on phi evaluations; default 100                              */
+    int32_t init;           /* cqk_init; -1 (default): FORMULA for cqk_solve, CONDAT for the    */
+                            /* projections                                                      */
+    double lambda0;         /* start for CQK_INIT_GIVEN                                         */
+    int32_t validate;       /* 1 (default): flag d <= 0, b <= 0, l > u, NaN as CQK_BAD_INPUT    */
+    int32_t final_step;     /* 1 (default): after a stop by stopping criterion 1 or 2, form x   */
+                            /* at lambda_k plus the Newton step already computed from lambda_k  */
+                            /* (when it stays inside the bracket); 0: x = x(lambda_k)           */
+    int64_t spin_limit_us;  /* bound on every device-wide wait, microseconds; default 2000000    */
+    int32_t max_blocks;     /* 0 = automatic grid size; otherwise an upper bound                */
+    int32_t fault_inject;   /* testing only: 1 = make every device-wide wait unsatisfiable so   */
+                            /* that the call ends with CQK_TIMEOUT after spin_limit_us          */
+    int32_t reserved[8];
+} cqk_options;
+
+/* Written on the device by every solve. */
+typedef struct cqk_info {
+    double lambda;    /* final multiplier; x = x(lambda)                                       */
+    double residual;  /* sum b_i x_i - r of the stored x (l1 ball: sum |x_i| - r)               */
+    double abs_bx;    /* sum |b_i x_i| of the stored x (the scale of stopping criterion 1)       */
+    double slope;     /* lateral derivative used in the last Newton step                        */
+    double lambda0;   /* initial multiplier actually used                                       */
+    int64_t nfree;    /* |{i : l_i < x_i < u_i}| (simplex / l1: number of nonzero x_i)           */
+    int32_t iters;    /* phi evaluations (Newton iterations)                                    */
+    int32_t status;   /* cqk_status                                                             */
+    int32_t passes;   /* passes over the data, all phases                                       */
+    int32_t stop;     /* cqk_stop                                                               */
+    int32_t nchunks;  /* CQK_INIT_CONDAT: number of chunks of the partition (0 otherwise)        */
+    int32_t tile;     /* CQK_INIT_CONDAT: variable i is in chunk (i / tile) % nchunks            */
+} cqk_info;
+
+/* Fills *opt with the defaults listed above. */
+void cqk_default_options(cqk_options* opt);
+
+/* Workspace size, in bytes, for one call on n_total variables split into `batch` instances
+ * (batch = 1 for cqk_solve / cqk_phi / cqk_project_*).  Returns 0 for invalid arguments. */
+size_t cqk_workspace_bytes(int64_t n_total, int32_t batch, int32_t dtype);
+
+/*
+ * Solve one general CQK instance (Alg. 1 with the stopping tests of Sec. 4).
+ *   n              number of variables, n >= 0 (n = 0: nothing is launched; info_dev
+ *                  receives status CQK_OK if r == 0, else CQK_INFEASIBLE)
+ *   a, b, d, l, u  device arrays of n elements of `dtype`; l may hold -inf, u +inf
+ *   r              right-hand side of b'x = r
+ *   x              device output, n elements of `dtype`: x(lambda*) (eq. (xopt))
+ *   free_mask      nullable device output of ceil(n/32) uint32 words: bit i%32 of word
+ *                  i/32 is set iff l_i < x_i < u_i
+ *   info_dev       device pointer to one cqk_info
+ *   opt            nullable; NULL means cqk_default_options()
+ * Every Newton iteration is one Jacobi map-reduce pass over a, b, d, l, u (Sec. 4)
+ * producing phi, phi'_+, phi'_- and sum|b_i x_i| (eq. (opt), eq. (phideriv)); the
+ * multiplier update (Newton step, secant step, closest breakpoint) runs on the device with
+ * no host synchronisation.
+ */
+int cqk_solve(int64_t n, int32_t dtype, const void* a, const void* b, const void* d,
+              const void* l, const void* u, double r, void* x, uint32_t* free_mask,
+              cqk_info* info_dev, const cqk_options* opt, void* workspace, size_t ws_bytes,
+              void* stream);
+
+/*
+ * One map-reduce pass at a given lambda (eq. (opt) and eq. (phideriv)); writes 4 doubles
+ * to out_dev (device): phi(lambda), phi'_+(lambda), phi'_-(lambda), sum |b_i x_i(lambda)|.
+ * x (nullable) receives x(lambda).  Same array conventions as cqk_solve; n >= 1.
+ */
+int cqk_phi(int64_t n, int32_t dtype, const void* a, const void* b, const void* d,
+            const void* l, const void* u, double lambda, void* x, double* out_dev,
+            void* workspace, size_t ws_bytes, void* stream);
+
+/*
+ * Project y onto the r-simplex {x >= 0, sum x = r} (eq. (proj_Delta); r > 0, n >= 1) by
+ * Alg. 4 from the start selected in opt->init (default CQK_INIT_CONDAT).
+ *   y, x       device arrays of n elements of `dtype` (x may not alias y)
+ *   free_mask  nullable, ceil(n/32) words, bit set iff x_i > 0
+ */
+int cqk_project_simplex(int64_t n, int32_t dtype, const void* y, double r, void* x,
+                        uint32_t* free_mask, cqk_info* info_dev, const cqk_options* opt,
+                        void* workspace, size_t ws_bytes, void* stream);
+
+/*
+ * Project y onto the l1 ball {sum |x_i| <= r} (Sec. 3.2; r > 0, n >= 1): x = y when
+ * sum |y_i| <= r; otherwise x_i = sgn(y_i) max{0, |y_i| + lambda*} with lambda* <= 0
+ * solving the simplex dual for |y| (Lemma 3.2), found by Alg. 4; with CQK_INIT_CONDAT the
+ * Alg. 2 test is the strengthened min{|y|, |y| + lambda} > 0.  Arguments as
+ * cqk_project_simplex; free_mask bit set iff x_i != 0.
+ */
+int cqk_project_l1(int64_t n, int32_t dtype, const void* y, double r, void* x,
+                   uint32_t* free_mask, cqk_info* info_dev, const cqk_options* opt,
+                   void* workspace, size_t ws_bytes, void* stream);
+
+/* Name of a cqk_status value (static string). */
+const char* cqk_status_string(int status);
+
+/* The cudaError_t of the last failed CUDA call made by this library in this thread. */
+int cqk_last_cuda_error(void);
+
+/* ABI version: 10000 * major + 100 * minor + patch. */
+int cqk_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CQK_H */

@@ -1,0 +1,146 @@
+// cqk_api.cu -- the extern "C" entry points of libcqk (declared in include/cqk.h): host-side
+// argument checks, option defaults, workspace sizing and grid sizing.  All compute is in the
+// kernels of cqk_simplex.cu and cqk_general.cu.
+#include <string.h>
+
+#include "cqk_internal.h"
+
+namespace cqk {
+
+static thread_local int g_last_cuda_error = 0;
+void set_last_cuda_error(cudaError_t e) { g_last_cuda_error = (int)e; }
+
+Opts resolve_options(const cqk_options* opt, int dtype, int default_init) {
+    (void)dtype;
+    cqk_options d;
+    cqk_default_options(&d);
+    if (opt) d = *opt;
+    Opts o;
+    o.max_iter = d.max_iter > 0 ? d.max_iter : 100;
+    o.init = d.init >= 0 ? d.init : default_init;
+    o.lambda0 = d.lambda0;
+    o.validate = d.validate != 0;
+    o.final_step = d.final_step != 0;
+    o.limit_ns = (unsigned long long)(d.spin_limit_us > 0 ? d.spin_limit_us : 2000000) * 1000ull;
+    o.max_blocks = d.max_blocks > 0 ? d.max_blocks : 0;
+    o.fault_inject = d.fault_inject;
+    return o;
+}
+
+int persistent_grid(const void* kernel, int threads, size_t smem, int64_t work_items, int max_blocks) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) { set_last_cuda_error(e); return -1; }
+    int sms = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) { set_last_cuda_error(e); return -1; }
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
+    if (e != cudaSuccess) { set_last_cuda_error(e); return -1; }
+    if (per_sm < 1) return -1;
+    int64_t g = (int64_t)sms * per_sm;
+    if (g > kMaxBlocks) g = kMaxBlocks;
+    // at least ~8 vectors per thread and pass before another block is added
+    int64_t want = (work_items + (int64_t)threads * 8 - 1) / ((int64_t)threads * 8);
+    if (want < 1) want = 1;
+    if (g > want) g = want;
+    if (max_blocks > 0 && g > max_blocks) g = max_blocks;
+    return (int)g;
+}
+
+}  // namespace cqk
+
+using namespace cqk;
+
+static bool ws_ok(const void* ws, size_t bytes, size_t need) { return ws && bytes >= need && ((uintptr_t)ws % 256) == 0; }
+
+extern "C" {
+
+void cqk_default_options(cqk_options* opt) {
+    if (!opt) return;
+    memset(opt, 0, sizeof(*opt));
+    opt->max_iter = 100;
+    opt->init = -1;
+    opt->lambda0 = 0.0;
+    opt->validate = 1;
+    opt->final_step = 1;
+    opt->spin_limit_us = 2000000;
+    opt->max_blocks = 0;
+    opt->fault_inject = 0;
+}
+
+size_t cqk_workspace_bytes(int64_t n_total, int32_t batch, int32_t dtype) {
+    if (n_total < 0 || batch < 1 || (dtype != CQK_F64 && dtype != CQK_F32)) return 0;
+    return kSingleWsBytes;
+}
+
+int cqk_solve(int64_t n, int32_t dtype, const void* a, const void* b, const void* d, const void* l, const void* u,
+              double r, void* x, uint32_t* free_mask, cqk_info* info_dev, const cqk_options* opt, void* workspace,
+              size_t ws_bytes, void* stream) {
+    if (n < 0 || (dtype != CQK_F64 && dtype != CQK_F32) || !info_dev) return CQK_BAD_ARG;
+    if (n > 0 && (!a || !b || !d || !l || !u || !x)) return CQK_BAD_ARG;
+    if (!ws_ok(workspace, ws_bytes, kSingleWsBytes)) return CQK_BAD_ARG;
+    if (r != r) return CQK_BAD_ARG;
+    Opts o = resolve_options(opt, dtype, CQK_INIT_FORMULA);
+    if (o.init != CQK_INIT_FORMULA && o.init != CQK_INIT_GIVEN) return CQK_BAD_ARG;
+    if (n == 0) {
+        cqk_info inf;
+        memset(&inf, 0, sizeof(inf));
+        inf.status = (r == 0.0) ? CQK_OK : CQK_INFEASIBLE;
+        inf.residual = -r;
+        cudaError_t e = cudaMemcpyAsync(info_dev, &inf, sizeof(inf), cudaMemcpyHostToDevice, (cudaStream_t)stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+        if (e != cudaSuccess) { set_last_cuda_error(e); return CQK_CUDA_ERROR; }
+        return CQK_OK;
+    }
+    return launch_general(n, dtype, a, b, d, l, u, r, x, free_mask, info_dev, o, workspace, (cudaStream_t)stream);
+}
+
+int cqk_phi(int64_t n, int32_t dtype, const void* a, const void* b, const void* d, const void* l, const void* u,
+            double lambda, void* x, double* out_dev, void* workspace, size_t ws_bytes, void* stream) {
+    if (n <= 0 || (dtype != CQK_F64 && dtype != CQK_F32) || !out_dev) return CQK_BAD_ARG;
+    if (!a || !b || !d || !l || !u) return CQK_BAD_ARG;
+    if (!ws_ok(workspace, ws_bytes, kSingleWsBytes)) return CQK_BAD_ARG;
+    return launch_phi(n, dtype, a, b, d, l, u, lambda, x, out_dev, workspace, (cudaStream_t)stream);
+}
+
+static int project(int64_t n, int32_t dtype, const void* y, double r, void* x, uint32_t* mask, cqk_info* info,
+                   const cqk_options* opt, void* ws, size_t ws_bytes, void* stream, int l1) {
+    if (n <= 0 || (dtype != CQK_F64 && dtype != CQK_F32) || !y || !x || !info) return CQK_BAD_ARG;
+    if (!(r > 0.0) || !(r < INFINITY)) return CQK_BAD_ARG;
+    if (x == y) return CQK_BAD_ARG;
+    if (!ws_ok(ws, ws_bytes, kSingleWsBytes)) return CQK_BAD_ARG;
+    Opts o = resolve_options(opt, dtype, CQK_INIT_CONDAT);
+    if (o.init != CQK_INIT_FORMULA && o.init != CQK_INIT_CONDAT && o.init != CQK_INIT_GIVEN) return CQK_BAD_ARG;
+    return launch_simplex(n, dtype, y, r, l1, x, mask, info, o, ws, (cudaStream_t)stream);
+}
+
+int cqk_project_simplex(int64_t n, int32_t dtype, const void* y, double r, void* x, uint32_t* free_mask,
+                        cqk_info* info_dev, const cqk_options* opt, void* workspace, size_t ws_bytes, void* stream) {
+    return project(n, dtype, y, r, x, free_mask, info_dev, opt, workspace, ws_bytes, stream, 0);
+}
+
+int cqk_project_l1(int64_t n, int32_t dtype, const void* y, double r, void* x, uint32_t* free_mask,
+                   cqk_info* info_dev, const cqk_options* opt, void* workspace, size_t ws_bytes, void* stream) {
+    return project(n, dtype, y, r, x, free_mask, info_dev, opt, workspace, ws_bytes, stream, 1);
+}
+
+const char* cqk_status_string(int status) {
+    switch (status) {
+        case CQK_OK: return "ok";
+        case CQK_INFEASIBLE: return "infeasible";
+        case CQK_MAXITER: return "maxiter";
+        case CQK_BAD_INPUT: return "bad_input";
+        case CQK_NONDIFF: return "nondiff";
+        case CQK_TIMEOUT: return "timeout";
+        case CQK_CUDA_ERROR: return "cuda_error";
+        case CQK_BAD_ARG: return "bad_arg";
+        default: return "unknown";
+    }
+}
+
+int cqk_last_cuda_error(void) { return g_last_cuda_error; }
+
+int cqk_version(void) { return 100; }
+
+}  // extern "C"

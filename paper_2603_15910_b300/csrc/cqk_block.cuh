@@ -1,0 +1,189 @@
+// cqk_block.cuh -- streaming loads and deterministic block / grid reductions shared by the
+// persistent kernels of libcqk.
+#pragma once
+
+#include "cqk_device.cuh"
+#include "cqk_internal.h"
+
+namespace cqk {
+
+template <typename T>
+struct VecOf;
+template <>
+struct VecOf<double> {
+    using type = double2;
+    static constexpr int V = 2;
+};
+template <>
+struct VecOf<float> {
+    using type = float4;
+    static constexpr int V = 4;
+};
+
+constexpr int NT = kBlockThreads;
+constexpr int NWARP = NT / 32;
+
+// Load the V elements of vector q (elements q*V ... q*V+V-1); out-of-range elements get
+// ok = false.  One 128-bit load when the arrays are 16-byte aligned and the vector is full.
+template <typename T>
+__device__ __forceinline__ void load_vec(const T* __restrict__ p, int64_t n, int64_t q, bool aligned,
+                                         T (&v)[VecOf<T>::V], bool (&ok)[VecOf<T>::V]) {
+    constexpr int V = VecOf<T>::V;
+    const int64_t e0 = q * V;
+    if (aligned && e0 + V <= n) {
+        using VT = typename VecOf<T>::type;
+        VT w = __ldg(reinterpret_cast<const VT*>(p) + q);
+        const T* s = reinterpret_cast<const T*>(&w);
+#pragma unroll
+        for (int j = 0; j < V; j++) {
+            v[j] = s[j];
+            ok[j] = true;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < V; j++) {
+            ok[j] = e0 + j < n;
+            v[j] = ok[j] ? __ldg(p + e0 + j) : T(0);
+        }
+    }
+}
+
+// Store the V elements of vector q (full vector: one 128-bit store when aligned).
+template <typename T>
+__device__ __forceinline__ void store_vec(T* __restrict__ p, int64_t n, int64_t q, bool aligned,
+                                          const T (&v)[VecOf<T>::V]) {
+    constexpr int V = VecOf<T>::V;
+    const int64_t e0 = q * V;
+    if (aligned && e0 + V <= n) {
+        using VT = typename VecOf<T>::type;
+        VT w;
+        T* s = reinterpret_cast<T*>(&w);
+#pragma unroll
+        for (int j = 0; j < V; j++) s[j] = v[j];
+        reinterpret_cast<VT*>(p)[q] = w;
+    } else {
+#pragma unroll
+        for (int j = 0; j < V; j++)
+            if (e0 + j < n) p[e0 + j] = v[j];
+    }
+}
+
+// Free-mask word of a warp's 32 consecutive vectors (starting at vector qw, a multiple of
+// 32): bit e % 32 of word e / 32 is set iff sel[j] of element e.  Called by all lanes.
+template <int V>
+__device__ __forceinline__ void store_mask(uint32_t* mask, int64_t n, int64_t qw, const bool (&sel)[V]) {
+    const int lane = threadIdx.x & 31;
+    unsigned bitsv = 0;
+#pragma unroll
+    for (int j = 0; j < V; j++) bitsv |= (sel[j] ? 1u : 0u) << ((lane * V + j) & 31);
+    constexpr int LPW = 32 / V;  // lanes per mask word
+#pragma unroll
+    for (int o = 1; o < LPW; o <<= 1) bitsv |= __shfl_xor_sync(0xffffffffu, bitsv, o);
+    if ((lane % LPW) == 0) {
+        const int64_t word = (qw * V) / 32 + lane / LPW;
+        if (word * 32 < n) mask[word] = bitsv;
+    }
+}
+
+__device__ __forceinline__ unsigned long long bits_of(double v) { return (unsigned long long)__double_as_longlong(v); }
+
+// Sum NQ doubles over the block (fixed order); result valid in thread 0.
+template <int NQ>
+__device__ __forceinline__ void block_sum(double (&v)[NQ], double (*sh)[NWARP]) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NQ; q++) v[q] = warp_sum(v[q]);
+    if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < NQ; q++) sh[q][wid] = v[q];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < NQ; q++) {
+            double s = 0.0;
+            for (int w = 0; w < NWARP; w++) s += sh[q][w];
+            v[q] = s;
+        }
+    }
+    __syncthreads();
+}
+
+// Reduce the partials of all blocks for pass parity `par` (sums, and a max for q == qmax);
+// every block computes the same values in the same order.  Result in out[] (all threads).
+template <int NQ>
+__device__ __forceinline__ void grid_reduce(const double* part, int par, int qmax, double (&out)[NQ],
+                                            double (*sh)[NWARP], double* bc) {
+    const int G = gridDim.x;
+    double v[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; q++) v[q] = (q == qmax) ? -INFINITY : 0.0;
+    for (int bIdx = threadIdx.x; bIdx < G; bIdx += NT) {
+#pragma unroll
+        for (int q = 0; q < NQ; q++) {
+            double t = ld_cg(part + ((size_t)par * kPartialQ + q) * G + bIdx);
+            v[q] = (q == qmax) ? fmax(v[q], t) : v[q] + t;
+        }
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NQ; q++) v[q] = (q == qmax) ? warp_max(v[q]) : warp_sum(v[q]);
+    if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < NQ; q++) sh[q][wid] = v[q];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < NQ; q++) {
+            double s = (q == qmax) ? -INFINITY : 0.0;
+            for (int w = 0; w < NWARP; w++) s = (q == qmax) ? fmax(s, sh[q][w]) : s + sh[q][w];
+            bc[q] = s;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < NQ; q++) out[q] = bc[q];
+    __syncthreads();
+}
+
+template <int NQ>
+__device__ __forceinline__ void write_partials(double* part, int par, const double (&v)[NQ]) {
+    if (threadIdx.x == 0) {
+        const int G = gridDim.x;
+#pragma unroll
+        for (int q = 0; q < NQ; q++) part[((size_t)par * kPartialQ + q) * G + blockIdx.x] = v[q];
+    }
+}
+
+// Last-block-done reduction of NQ <= 3 sums stored in slots 5..5+NQ of parity 0; returns
+// true in the last block, whose out[] then holds the grid sums (all threads).
+template <int NQ>
+__device__ __forceinline__ bool last_block_sums(double* part, unsigned* ticket, double (&v)[NQ], double (&out)[NQ],
+                                                double (*sh)[NWARP]) {
+    __shared__ unsigned s_last;
+    const int G = gridDim.x;
+    block_sum<NQ>(v, sh);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < NQ; q++) part[(size_t)(5 + q) * G + blockIdx.x] = v[q];
+        __threadfence();
+        unsigned t = atomicAdd(ticket, 1u);
+        s_last = (t == (unsigned)G - 1) ? 1u : 0u;
+    }
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+    double w[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; q++) w[q] = 0.0;
+    for (int b = threadIdx.x; b < G; b += NT)
+#pragma unroll
+        for (int q = 0; q < NQ; q++) w[q] += ld_cg(part + (size_t)(5 + q) * G + b);
+    block_sum<NQ>(w, sh);
+#pragma unroll
+    for (int q = 0; q < NQ; q++) out[q] = w[q];
+    return true;
+}
+
+}  // namespace cqk
