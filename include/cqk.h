@@ -175,6 +175,30 @@ int cqk_project_l1(int64_t n, int32_t dtype, const void* y, double r, void* x,
                    uint32_t* free_mask, cqk_info* info_dev, const cqk_options* opt,
                    void* workspace, size_t ws_bytes, void* stream);
 
+/*
+ * Allocation-free variant of cqk_project_simplex (the paper has no counterpart: this is a
+ * calling convenience of this library).
+ *
+ * Some callers cannot allocate device memory when they need a projection -- for instance a
+ * plugin whose host application owns the device allocator, or a real-time loop whose device
+ * memory is fixed at start-up -- and so cannot pass the workspace that cqk_project_simplex
+ * takes.  This entry point takes the same arguments without the workspace and runs the same
+ * kernel with its scratch in a static device array of CQK_NOALLOC_SCRATCH_BYTES bytes that
+ * every GPU loading the library holds until the process exits.  It calls no allocator.
+ *   - The array holds partial sums for at most CQK_NOALLOC_MAX_BLOCKS blocks, so the grid is
+ *     capped there; options->max_blocks above that limit is rejected with CQK_BAD_ARG.
+ *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ *     with that device current; make that first call before any stream capture.
+ *   - Every call on a device shares the one array, and each call clears the part that must
+ *     start at zero.  Calls whose executions overlap on the GPU (different streams, or
+ *     several host threads) race on it: issue them in order on one stream.
+ */
+#define CQK_NOALLOC_MAX_BLOCKS 592
+#define CQK_NOALLOC_SCRATCH_BYTES 76032
+int cqk_project_simplex_noalloc(int64_t n, int32_t dtype, const void* y, double r, void* x,
+                                uint32_t* free_mask, cqk_info* info_dev, const cqk_options* opt,
+                                void* stream);
+
 /* Name of a cqk_status value (static string). */
 const char* cqk_status_string(int status);
 
