@@ -56,56 +56,85 @@ def measured_peak_hbm():
 
 # ------------------------------------------------------------------------------ clocks
 class ClockSampler:
-    """Samples SM clock and clock-event reasons through NVML while running."""
+    """Samples the SM clock and the clock-event reasons of the CUDA device while running:
+    NVML addressed by the device's PCI bus id, or `nvidia-smi -lms` when NVML is unusable."""
 
-    REASONS = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap", 0x8: "hw_slowdown",
-               0x10: "sync_boost", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
-               0x80: "hw_power_brake_slowdown", 0x100: "display_clock_setting"}
+    REASONS = {0x2: "applications_clocks_setting", 0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x10: "sync_boost",
+               0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown",
+               0x100: "display_clock_setting"}
 
-    def __init__(self, index):
-        self.index = index
-        self.samples = []
-        self.reasons = set()
-        self.max_mhz = None
+    def __init__(self, cuda_index):
+        import torch
+        self.samples, self.reasons, self.max_mhz = [], set(), None
+        self.source, self.error = None, None
         self._stop = threading.Event()
         self._t = None
+        self._proc = None
+        p = torch.cuda.get_device_properties(cuda_index)
+        self.bus = f"{p.pci_domain_id:08X}:{p.pci_bus_id:02X}:{p.pci_device_id:02X}.0"
         try:
             import pynvml
             pynvml.nvmlInit()
             self.nv = pynvml
-            self.h = pynvml.nvmlDeviceGetHandleByIndex(index)
+            self.h = pynvml.nvmlDeviceGetHandleByPciBusId(self.bus.encode())
             self.max_mhz = pynvml.nvmlDeviceGetMaxClockInfo(self.h, pynvml.NVML_CLOCK_SM)
-        except Exception:
+            self.source = "nvml"
+        except Exception as e:  # noqa: BLE001
             self.nv = None
+            self.error = f"nvml: {type(e).__name__}: {e}"
 
     def _run(self):
         while not self._stop.is_set():
             try:
                 self.samples.append(self.nv.nvmlDeviceGetClockInfo(self.h, self.nv.NVML_CLOCK_SM))
                 bits = self.nv.nvmlDeviceGetCurrentClocksEventReasons(self.h)
-                for b, name in self.REASONS.items():
-                    if bits & b and name != "gpu_idle":
-                        self.reasons.add(name)
-            except Exception:
-                pass
+                self._bits(bits)
+            except Exception as e:  # noqa: BLE001
+                self.error = f"nvml sample: {type(e).__name__}: {e}"
             time.sleep(0.02)
+
+    def _bits(self, bits):
+        for b, name in self.REASONS.items():
+            if bits & b:
+                self.reasons.add(name)
 
     def __enter__(self):
         if self.nv is not None:
             self._t = threading.Thread(target=self._run, daemon=True)
             self._t.start()
+        else:
+            import subprocess
+            try:
+                self._proc = subprocess.Popen(
+                    ["nvidia-smi", "-i", self.bus, "--query-gpu=clocks.sm,clocks.max.sm,clocks_event_reasons.active",
+                     "--format=csv,noheader,nounits", "-lms", "100"], stdout=subprocess.PIPE, text=True)
+                self.source = "nvidia-smi"
+            except Exception as e:  # noqa: BLE001
+                self.error = (self.error or "") + f"; nvidia-smi: {e}"
         return self
 
     def __exit__(self, *exc):
         self._stop.set()
         if self._t is not None:
             self._t.join()
+        if self._proc is not None:
+            self._proc.terminate()
+            out, _ = self._proc.communicate(timeout=5)
+            for line in out.splitlines():
+                parts = [x.strip() for x in line.split(",")]
+                try:
+                    self.samples.append(float(parts[0]))
+                    self.max_mhz = float(parts[1])
+                    self._bits(int(parts[2], 16))
+                except Exception:  # noqa: BLE001
+                    pass
 
     def summary(self):
-        if not self.samples:
-            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": sorted(self.reasons)}
-        return {"sm_mhz": statistics.median(self.samples), "sm_max_mhz": self.max_mhz,
-                "reasons": sorted(self.reasons), "samples": len(self.samples)}
+        d = {"sm_mhz": statistics.median(self.samples) if self.samples else None, "sm_max_mhz": self.max_mhz,
+             "reasons": sorted(self.reasons), "samples": len(self.samples), "source": self.source}
+        if self.error and not self.samples:
+            d["error"] = self.error
+        return d
 
 
 # ------------------------------------------------------------------------------ our arm

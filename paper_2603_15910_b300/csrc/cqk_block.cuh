@@ -85,6 +85,46 @@ __device__ __forceinline__ void store_mask(uint32_t* mask, int64_t n, int64_t qw
     }
 }
 
+// Warp-contiguous traversal of nv vectors: iteration i of warp w (of W) covers the vectors
+// [base, base + 32*U) with base = (w + i*W)*32*U, lane L taking base + k*32 + L (k < U), so
+// every load instruction of a warp reads 512 contiguous bytes and each lane has U
+// independent 16-byte loads in flight.  rev = true visits the same iterations in reverse
+// order: a pass that follows a forward pass then starts on the data that the forward pass
+// read last, which is still in L2.
+struct WarpSweep {
+    int64_t first, step, count;
+    __device__ __forceinline__ WarpSweep(int64_t nv, int U) {
+        const int64_t gwarp = (int64_t)blockIdx.x * NWARP + (threadIdx.x >> 5);
+        const int64_t nwarps = (int64_t)gridDim.x * NWARP;
+        first = gwarp * 32 * U;
+        step = nwarps * 32 * U;
+        count = first < nv ? (nv - first + step - 1) / step : 0;
+    }
+    __device__ __forceinline__ int64_t base(int64_t i, bool rev) const { return first + (rev ? count - 1 - i : i) * step; }
+};
+
+// a[j] for a runtime index j without dynamic register indexing (unrolled selects)
+template <typename X, int N>
+__device__ __forceinline__ X pick(const X (&a)[N], int j) {
+    X v = a[0];
+#pragma unroll
+    for (int t = 1; t < N; t++) v = (t == j) ? a[t] : v;
+    return v;
+}
+template <typename X, int N, int M>
+__device__ __forceinline__ X pick2(const X (&a)[N][M], int uj) {
+    X v = a[0][0];
+#pragma unroll
+    for (int t = 1; t < N * M; t++) v = (t == uj) ? a[t / M][t % M] : v;
+    return v;
+}
+template <typename X, int N>
+__device__ __forceinline__ void put(X (&a)[N], int j, X v) {
+#pragma unroll
+    for (int t = 0; t < N; t++)
+        if (t == j) a[t] = v;
+}
+
 __device__ __forceinline__ unsigned long long bits_of(double v) { return (unsigned long long)__double_as_longlong(v); }
 
 // Sum NQ doubles over the block (fixed order); result valid in thread 0.

@@ -167,6 +167,29 @@ __device__ __forceinline__ bool gt_bits(unsigned long long ybits, const GtThresh
     return t.neg ? (ybits < t.bits) : ((long long)ybits > (long long)t.bits);
 }
 
+// Order-preserving integer key of a double (non-NaN): x < y  <=>  key(x) < key(y) (as signed
+// 64-bit integers; -0 and +0 map to adjacent keys).  Used for max/min without FP64 instructions.
+__device__ __forceinline__ long long order_key(double x) {
+    const long long b = __double_as_longlong(x);
+    return b >= 0 ? b : (long long)(0x8000000000000000ull - (unsigned long long)b) - 1;
+}
+__device__ __forceinline__ double from_order_key(long long k) {
+    return __longlong_as_double(k >= 0 ? k : (long long)(0x8000000000000000ull - (unsigned long long)(k + 1)));
+}
+
+// FP64 classification on the bit pattern (integer pipe).
+__device__ __forceinline__ bool f64_is_nan(double x) {
+    return ((unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull) > 0x7FF0000000000000ull;
+}
+__device__ __forceinline__ bool f64_is_finite(double x) {
+    return ((unsigned)__double2hiint(x) & 0x7FF00000u) != 0x7FF00000u;
+}
+// finite and > 0
+__device__ __forceinline__ bool f64_pos_finite(double x) {
+    const long long b = __double_as_longlong(x);
+    return b > 0 && b < 0x7FF0000000000000ll;
+}
+
 // Largest float <= c: for a float y, y > c  <=>  y > rd(c).
 __device__ __forceinline__ float f32_rd(double c) { return __double2float_rd(c); }
 // Smallest float >= c: for a float y, y >= c  <=>  y >= ru(c).

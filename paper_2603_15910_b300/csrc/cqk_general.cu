@@ -56,9 +56,10 @@ struct GeneralArgs {
 };
 
 // Per-thread accumulators of one pass.  The df sums are flushed into the FP64 ones every
-// kFlushEvery vector steps, bounding the df summation error by ~kFlushEvery*V*2^-47 of the
-// flushed partial sums.
-constexpr int kFlushEvery = 16;
+// kFlushEvery sweep iterations (16 vectors), bounding the df summation error by ~16*V*2^-47 of
+// the flushed partial sums.
+constexpr int kFlushEvery = 8;   // sweep iterations (kGenU vectors each) between flushes
+constexpr int kGenU = 2;         // 16-byte vectors per array in flight per lane
 struct EvalAcc {
     df phi, absbx, sfree;
     double phi64, absbx64, sfree64, satl, satu;
@@ -85,7 +86,7 @@ struct Cls {
 };
 
 // ---- FP64 data, exact FP64 (values outside the df range) -------------------------------
-__device__ __forceinline__ double elem_f64_exact(double a, double b, double d, double l, double u, double lam,
+__device__ __noinline__ double elem_f64_exact(double a, double b, double d, double l, double u, double lam,
                                                  EvalAcc& acc, bool want_acc, Cls& cl) {
     const double lb = lam * b;
     const double v = a + lb;
@@ -114,7 +115,7 @@ __device__ __forceinline__ double elem_f64_exact(double a, double b, double d, d
 
 // ---- FP64 data in the df range ----------------------------------------------------------
 __device__ __forceinline__ df elem_df(double a, double b, double d, double l, double u, df Lm, EvalAcc& acc,
-                                      bool want_acc, Cls& cl) {
+                                      bool want_acc, Cls& cl, df& beta_out) {
     const df A = split_f64(a), B = split_f64(b), D = split_f64(d), Lo = split_f64(l), Up = split_f64(u);
     const df lb = df_mul(Lm, B);
     const df v = df_add(A, lb);
@@ -141,15 +142,16 @@ __device__ __forceinline__ df elem_df(double a, double b, double d, double l, do
         acc.absbx = df_add(acc.absbx, bx.hi < 0.0f ? df_neg(bx) : bx);
         const df beta = df_mul(df_mul(B, B), invd);
         acc.sfree = df_add(acc.sfree, cl.c == 0 ? beta : df_make(0.0f));
-        if (tieL && !tieU) acc.satl += df_to_f64(beta);
-        if (tieU && !tieL) acc.satu += df_to_f64(beta);
+        beta_out = beta;
     }
     return x;
 }
 
+// sanity checks of Sec. 5.1.1 on the bit patterns: d > 0, b > 0 finite; a finite; l <= u;
+// no NaN (integer pipe only)
 __device__ __forceinline__ bool bad_elem(double a, double b, double d, double l, double u) {
-    // sanity checks of Sec. 5.1.1: d > 0, b > 0, l <= u; a, b, d finite; no NaN
-    return !(d > 0.0) || !(b > 0.0) || !(l <= u) || isinf(d) || isinf(b) || !(fabs(a) < INFINITY);
+    return !f64_pos_finite(d) || !f64_pos_finite(b) || !f64_is_finite(a) || f64_is_nan(l) || f64_is_nan(u) ||
+           order_key(l) > order_key(u);
 }
 
 // ---- FP32 data -----------------------------------------------------------------------------
@@ -157,7 +159,7 @@ __device__ __forceinline__ bool bad_elem(double a, double b, double d, double l,
 // with the exact products d*l, d*u (TwoProd); x = v/d rounded to float; b*x, |b x| and
 // b^2/d are accumulated in df.
 __device__ __forceinline__ float elem_f32(float a, float b, float d, float l, float u, df Lm, EvalAcc& acc,
-                                          bool want_acc, Cls& cl) {
+                                          bool want_acc, Cls& cl, df& beta_out) {
     const df lb = df_mul_f(Lm, b);
     const df v = df_add_f(lb, a);
     const bool linf = isinf(l), uinf = isinf(u);
@@ -186,16 +188,17 @@ __device__ __forceinline__ float elem_f32(float a, float b, float d, float l, fl
         float beta = __fmul_rn(bb, rd);
         beta = fmaf(fmaf(-beta, d, bb), rd, beta);
         acc.sfree = df_add_f(acc.sfree, cl.c == 0 ? beta : 0.0f);
-        if (tieL && !tieU) acc.satl += (double)beta;
-        if (tieU && !tieL) acc.satu += (double)beta;
+        beta_out = df_make(beta);
     }
     return x;
 }
 
 // ---- one pass over all elements: accumulate (write_x = false) or write x / mask / residual
 template <typename T>
-__device__ __forceinline__ void eval_pass(const GeneralArgs& A, double lam, bool write_x, bool check, EvalAcc& acc) {
+__device__ __forceinline__ void eval_pass(const GeneralArgs& A, double lam, bool write_x, bool check, bool rev,
+                                          EvalAcc& acc) {
     constexpr int V = VecOf<T>::V;
+    constexpr int U = kGenU;
     const T* __restrict__ pa = static_cast<const T*>(A.a);
     const T* __restrict__ pb = static_cast<const T*>(A.b);
     const T* __restrict__ pd = static_cast<const T*>(A.d);
@@ -205,73 +208,112 @@ __device__ __forceinline__ void eval_pass(const GeneralArgs& A, double lam, bool
     const int64_t n = A.n;
     const int64_t nv = (n + V - 1) / V;
     const int lane = threadIdx.x & 31;
-    const int64_t gwarp = (int64_t)blockIdx.x * NWARP + (threadIdx.x >> 5);
-    const int64_t nwarps = (int64_t)gridDim.x * NWARP;
     const bool aligned = A.aligned != 0;
     const df Lm = df_from_f64(lam);
     const bool lam_ok = fabs(lam) <= 1.152921504606847e18;  // 2^60
+    const WarpSweep sw(nv, U);
     int steps = 0;
-    for (int64_t qw = gwarp * 32; qw < nv; qw += nwarps * 32) {
+    for (int64_t it = 0; it < sw.count; it++) {
         if (++steps == kFlushEvery) {
             acc.flush();
             steps = 0;
         }
-        const int64_t q = qw + lane;
-        T va[V], vb[V], vd[V], vl[V], vu[V];
-        bool ok[V];
-        load_vec<T>(pa, n, q, aligned, va, ok);
-        load_vec<T>(pb, n, q, aligned, vb, ok);
-        load_vec<T>(pd, n, q, aligned, vd, ok);
-        load_vec<T>(pl, n, q, aligned, vl, ok);
-        load_vec<T>(pu, n, q, aligned, vu, ok);
-        T xo[V];
-        bool fr[V];
+        const int64_t base = sw.base(it, rev);
+        T va[U][V], vb[U][V], vd[U][V], vl[U][V], vu[U][V];
+        bool ok[U][V];
 #pragma unroll
-        for (int j = 0; j < V; j++) {
-            fr[j] = false;
-            xo[j] = T(0);
-            if (!ok[j]) continue;
-            Cls cl;
-            if constexpr (sizeof(T) == 8) {
-                if (check) acc.bad |= bad_elem(va[j], vb[j], vd[j], vl[j], vu[j]);
-                const bool inr = lam_ok && df_in_range(va[j], false) && df_in_range(vb[j], false) &&
-                                 df_in_range(vd[j], false) && df_in_range(vl[j], true) && df_in_range(vu[j], true);
-                if (inr) {
-                    const df xv = elem_df(va[j], vb[j], vd[j], vl[j], vu[j], Lm, acc, !write_x, cl);
-                    if (write_x) xo[j] = cl.c == 1 ? vl[j] : (cl.c == 2 ? vu[j] : df_to_f64(xv));
-                } else {
-                    xo[j] = elem_f64_exact(va[j], vb[j], vd[j], vl[j], vu[j], lam, acc, !write_x, cl);
-                }
-            } else {
-                if (check) acc.bad |= bad_elem(va[j], vb[j], vd[j], vl[j], vu[j]);
-                xo[j] = elem_f32(va[j], vb[j], vd[j], vl[j], vu[j], Lm, acc, !write_x, cl);
-            }
-            fr[j] = cl.c == 0;
+        for (int w = 0; w < U; w++) {
+            const int64_t q = base + w * 32 + lane;
+            load_vec<T>(pa, n, q, aligned, va[w], ok[w]);
+            load_vec<T>(pb, n, q, aligned, vb[w], ok[w]);
+            load_vec<T>(pd, n, q, aligned, vd[w], ok[w]);
+            load_vec<T>(pl, n, q, aligned, vl[w], ok[w]);
+            load_vec<T>(pu, n, q, aligned, vu[w], ok[w]);
         }
-        if (write_x) {
-            // sums of the stored x: b'x, sum |b x|, number of free variables
+#pragma unroll
+        for (int w = 0; w < U; w++) {
+            const int64_t qw = base + w * 32;
+            const int64_t q = qw + lane;
+            T xo[V];
+            bool fr[V];
+            df beta[V];
+            unsigned tiem = 0, widem = 0;
 #pragma unroll
             for (int j = 0; j < V; j++) {
-                if (!ok[j]) continue;
+                fr[j] = false;
+                xo[j] = T(0);
+                beta[j] = df_make(0.0f);
+                if (!ok[w][j]) continue;
+                const T a = va[w][j], b = vb[w][j], d = vd[w][j], l = vl[w][j], u = vu[w][j];
+                Cls cl;
                 if constexpr (sizeof(T) == 8) {
-                    if (df_in_range(vb[j], false) && df_in_range(xo[j], false)) {
-                        const df p = df_mul(split_f64(vb[j]), split_f64(xo[j]));
+                    if (check) acc.bad |= bad_elem(a, b, d, l, u);
+                    const bool inr = lam_ok && df_in_range(a, false) && df_in_range(b, false) &&
+                                     df_in_range(d, false) && df_in_range(l, true) && df_in_range(u, true);
+                    if (!inr) {
+                        widem |= 1u << j;
+                        continue;
+                    }
+                    const df xv = elem_df(a, b, d, l, u, Lm, acc, !write_x, cl, beta[j]);
+                    if (write_x) xo[j] = cl.c == 1 ? l : (cl.c == 2 ? u : df_to_f64(xv));
+                } else {
+                    if (check) acc.bad |= bad_elem(a, b, d, l, u);
+                    xo[j] = elem_f32(a, b, d, l, u, Lm, acc, !write_x, cl, beta[j]);
+                }
+                fr[j] = cl.c == 0;
+                tiem |= ((cl.tieL && !cl.tieU) ? 1u : 0u) << (2 * j);
+                tiem |= ((cl.tieU && !cl.tieL) ? 2u : 0u) << (2 * j);
+            }
+            // rare cases, one loop trip per element concerned (a data-dependent loop keeps FP64
+            // instructions off the common path): elements on a breakpoint (lateral-slope ties)
+            // and FP64 values outside the df operating range (exact FP64)
+            if (!write_x) {
+                for (unsigned m = tiem; m; m &= m - 1) {
+                    const int bit = __ffs(m) - 1;
+                    const double bj = df_to_f64(pick(beta, bit >> 1));
+                    if (bit & 1) acc.satu += bj;
+                    else acc.satl += bj;
+                }
+            }
+            if constexpr (sizeof(T) == 8) {
+                for (unsigned m = widem; m; m &= m - 1) {
+                    const int j = __ffs(m) - 1;
+                    Cls cl;
+                    const T xj = elem_f64_exact(pick(va[w], j), pick(vb[w], j), pick(vd[w], j), pick(vl[w], j),
+                                                pick(vu[w], j), lam, acc, !write_x, cl);
+                    put(xo, j, xj);
+                    put(fr, j, cl.c == 0);
+                }
+            }
+            if (write_x) {
+                // sums of the stored x: b'x, sum |b x|, number of free variables
+                unsigned wide2 = 0;
+#pragma unroll
+                for (int j = 0; j < V; j++) {
+                    if (!ok[w][j]) continue;
+                    const T b = vb[w][j];
+                    if constexpr (sizeof(T) == 8) {
+                        const bool inr = df_in_range(b, false) && df_in_range(xo[j], false);
+                        const df p = inr ? df_mul(split_f64(b), split_f64(xo[j])) : df_make(0.0f);
                         acc.phi = df_add(acc.phi, p);
                         acc.absbx = df_add(acc.absbx, p.hi < 0.0f ? df_neg(p) : p);
+                        wide2 |= (inr ? 0u : 1u) << j;
                     } else {
-                        const double bx = vb[j] * xo[j];
-                        acc.phi64 += bx;
-                        acc.absbx64 += fabs(bx);
+                        const df p = two_prod((float)b, (float)xo[j]);
+                        acc.phi = df_add(acc.phi, p);
+                        acc.absbx = df_add(acc.absbx, p.hi < 0.0f ? df_neg(p) : p);
                     }
-                } else {
-                    const df p = two_prod((float)vb[j], (float)xo[j]);
-                    acc.phi = df_add(acc.phi, p);
-                    acc.absbx = df_add(acc.absbx, p.hi < 0.0f ? df_neg(p) : p);
+                    acc.nfree += fr[j];
                 }
-                acc.nfree += fr[j];
+                for (unsigned m = wide2; m; m &= m - 1) {
+                    const int j = __ffs(m) - 1;
+                    const double bx = (double)pick(vb[w], j) * (double)pick(xo, j);
+                    acc.phi64 += bx;
+                    acc.absbx64 += fabs(bx);
+                }
+                if (px) store_vec<T>(px, n, q, aligned, xo);
+                if (A.mask) store_mask<V>(A.mask, n, qw, fr);
             }
-            if (px) store_vec<T>(px, n, q, aligned, xo);
-            if (A.mask) store_mask<V>(A.mask, n, qw, fr);
         }
     }
 }
@@ -309,45 +351,55 @@ __device__ __forceinline__ void lambda0_pass(const GeneralArgs& A, double& s_out
     const int64_t n = A.n;
     const int64_t nv = (n + V - 1) / V;
     const int lane = threadIdx.x & 31;
-    const int64_t gwarp = (int64_t)blockIdx.x * NWARP + (threadIdx.x >> 5);
-    const int64_t nwarps = (int64_t)gridDim.x * NWARP;
     const bool aligned = A.aligned != 0;
     df s = df_make(0.0f), q = df_make(0.0f);
     double s64 = 0.0, q64 = 0.0;
     int steps = 0;
-    for (int64_t qw = gwarp * 32; qw < nv; qw += nwarps * 32) {
+    constexpr int U = kGenU;
+    const WarpSweep sw(nv, U);
+    for (int64_t it = 0; it < sw.count; it++) {
         if (++steps == kFlushEvery) {
             s64 += df_to_f64(s);
             q64 += df_to_f64(q);
             s = q = df_make(0.0f);
             steps = 0;
         }
-        T va[V], vb[V], vd[V];
-        bool ok[V];
-        load_vec<T>(pa, n, qw + lane, aligned, va, ok);
-        load_vec<T>(pb, n, qw + lane, aligned, vb, ok);
-        load_vec<T>(pd, n, qw + lane, aligned, vd, ok);
+        const int64_t base = sw.base(it, false);
+        T va[U][V], vb[U][V], vd[U][V];
+        bool ok[U][V];
 #pragma unroll
-        for (int j = 0; j < V; j++) {
-            if (!ok[j]) continue;
+        for (int w = 0; w < U; w++) {
+            load_vec<T>(pa, n, base + w * 32 + lane, aligned, va[w], ok[w]);
+            load_vec<T>(pb, n, base + w * 32 + lane, aligned, vb[w], ok[w]);
+            load_vec<T>(pd, n, base + w * 32 + lane, aligned, vd[w], ok[w]);
+        }
+        unsigned wide = 0;
+#pragma unroll
+        for (int wj = 0; wj < U * V; wj++) {
+            const int w = wj / V, j = wj % V;
+            if (!ok[w][j]) continue;
+            const T a = va[w][j], b = vb[w][j], d = vd[w][j];
             if constexpr (sizeof(T) == 8) {
-                if (df_in_range(va[j], false) && df_in_range(vb[j], false) && df_in_range(vd[j], false) &&
-                    vd[j] > 0.0) {
-                    const df B = split_f64(vb[j]), D = split_f64(vd[j]);
-                    const df w = df_mul(B, df_div(df_make(1.0f), D, rcp_approx(D.hi)));
-                    s = df_add(s, df_mul(w, split_f64(va[j])));
-                    q = df_add(q, df_mul(w, B));
-                } else {
-                    s64 += vb[j] * va[j] / vd[j];
-                    q64 += vb[j] * vb[j] / vd[j];
-                }
+                const bool inr = df_in_range(a, false) && df_in_range(b, false) && df_in_range(d, false) &&
+                                 f64_pos_finite(d);
+                const df B = split_f64(inr ? b : 1.0), D = split_f64(inr ? d : 1.0);
+                const df wgt = df_mul(B, df_div(df_make(1.0f), D, rcp_approx(D.hi)));
+                s = df_add(s, inr ? df_mul(wgt, split_f64(a)) : df_make(0.0f));
+                q = df_add(q, inr ? df_mul(wgt, B) : df_make(0.0f));
+                wide |= (inr ? 0u : 1u) << wj;
             } else {
-                const float rd = rcp_approx(vd[j]);
-                float w = __fmul_rn(vb[j], rd);
-                w = fmaf(fmaf(-w, vd[j], vb[j]), rd, w);
-                s = df_add(s, two_prod(w, va[j]));
-                q = df_add(q, two_prod(w, vb[j]));
+                const float rd = rcp_approx(d);
+                float wgt = __fmul_rn(b, rd);
+                wgt = fmaf(fmaf(-wgt, d, b), rd, wgt);
+                s = df_add(s, two_prod(wgt, a));
+                q = df_add(q, two_prod(wgt, b));
             }
+        }
+        for (unsigned m = wide; m; m &= m - 1) {  // exact FP64 outside the df range (rare)
+            const int wj = __ffs(m) - 1;
+            const double a = pick(va[wj / V], wj % V), b = pick(vb[wj / V], wj % V), d = pick(vd[wj / V], wj % V);
+            s64 += b * a / d;
+            q64 += b * b / d;
         }
     }
     s_out = df_to_f64(s) + s64;
@@ -364,7 +416,7 @@ __device__ __forceinline__ void lambda0_pass(const GeneralArgs& A, double& s_out
     } while (0)
 
 template <typename T>
-__global__ void __launch_bounds__(NT) general_kernel(GeneralArgs A) {
+__global__ void __launch_bounds__(NT, 2) general_kernel(GeneralArgs A) {
     __shared__ double sh[kPartialQ][NWARP];
     __shared__ double bc[kPartialQ];
     const int G = gridDim.x;
@@ -377,7 +429,7 @@ __global__ void __launch_bounds__(NT) general_kernel(GeneralArgs A) {
     if (A.phi_only) {  // cqk_phi: one evaluation at A.lambda0 (and x when requested)
         EvalAcc acc;
         acc.init();
-        eval_pass<T>(A, A.lambda0, false, false, acc);
+        eval_pass<T>(A, A.lambda0, false, false, false, acc);
         acc.flush();
         double pv[3] = {acc.phi64, acc.sfree64, acc.absbx64};
         double pt[2] = {acc.satl, acc.satu};
@@ -390,7 +442,7 @@ __global__ void __launch_bounds__(NT) general_kernel(GeneralArgs A) {
         if (A.x) {
             EvalAcc acc2;
             acc2.init();
-            eval_pass<T>(A, A.lambda0, true, false, acc2);
+            eval_pass<T>(A, A.lambda0, true, false, true, acc2);
         }
         double dummy[1] = {0.0}, tot[1];
         if (last_block_sums<1>(A.part, &A.hdr->ticket, dummy, tot, sh)) {
@@ -434,7 +486,7 @@ __global__ void __launch_bounds__(NT) general_kernel(GeneralArgs A) {
         }
         EvalAcc acc;
         acc.init();
-        eval_pass<T>(A, lam, false, k == 0 && A.validate, acc);
+        eval_pass<T>(A, lam, false, k == 0 && A.validate, (k & 1) == 1, acc);
         acc.flush();
         passes++;
         if (__any_sync(0xffffffffu, acc.bad) && (threadIdx.x & 31) == 0) atomicOr(&A.hdr->flags, kFlagBadInput);
@@ -563,7 +615,7 @@ __global__ void __launch_bounds__(NT) general_kernel(GeneralArgs A) {
     EvalAcc acc;
     acc.init();
     if (!bad_input && status != CQK_INFEASIBLE) {
-        eval_pass<T>(A, final_lam, true, false, acc);
+        eval_pass<T>(A, final_lam, true, false, (k & 1) == 1, acc);
         passes++;
     }
     acc.flush();

@@ -26,7 +26,11 @@
 namespace cqk {
 namespace {
 
-constexpr int kCondatVecsPerLane = 4;  // vectors per lane in one Alg. 2 tile
+constexpr int kStreamU = 8;  // 16-byte vectors in flight per lane in the streaming passes
+
+// vectors per lane in one Alg. 2 tile: a tile is 512 elements for FP64 and FP32 data
+template <typename T>
+__host__ __device__ constexpr int condat_k() { return 512 / (32 * VecOf<T>::V); }
 
 struct SimplexArgs {
     int64_t n;
@@ -65,6 +69,7 @@ struct SimplexArgs {
 // the last restart with the same test.
 template <typename T, bool L1>
 __device__ __forceinline__ bool condat_test(T v, const GtThreshold& g, float rd) {
+    // exact test "y > c" (l1: "|y| > c") on the bit pattern / against the rounded-down threshold
     if constexpr (sizeof(T) == 8) {
         unsigned long long b = bits_of((double)v);
         if (L1) b &= 0x7FFFFFFFFFFFFFFFull;
@@ -79,38 +84,52 @@ __device__ __forceinline__ bool condat_test(T v, const GtThreshold& g, float rd)
 template <bool L1>
 __device__ __forceinline__ double condat_c(double lam) { return L1 ? fmax(0.0, -lam) : -lam; }
 
+// Warp-uniform state of one chunk's scan: lambda_J, sum_J y, |J|, the index of the last
+// restart, and the test threshold derived from lambda (recomputed only when lambda changes,
+// which keeps FP64 instructions off the per-slab path).
+struct CondatState {
+    double lam, S;
+    long long nJ;
+    int64_t rs;
+    GtThreshold g;
+    float rd;
+};
+
+template <bool L1>
+__device__ __forceinline__ void condat_set_lam(CondatState& st, double lam) {
+    st.lam = lam;
+    const double c = condat_c<L1>(lam);
+    st.g = make_gt(c);
+    st.rd = f32_rd(c);
+}
+
 template <typename T, bool L1>
 __device__ __forceinline__ void condat_slab(const T (&vals)[VecOf<T>::V], const bool (&okv)[VecOf<T>::V],
                                             int64_t eidx0, int64_t before, bool first_loop, double r,
-                                            double& lam, double& S, long long& nJ, int64_t& rs) {
+                                            CondatState& st) {
     constexpr int V = VecOf<T>::V;
     const int lane = threadIdx.x & 31;
     bool pass[V];
-    if (first_loop && nJ == 0) {
+    if (first_loop && st.nJ == 0) {
         // the first element of the chunk starts J unconditionally (first line of Alg. 2)
-        unsigned any_ok = __ballot_sync(0xffffffffu, okv[0]);
+        const unsigned any_ok = __ballot_sync(0xffffffffu, okv[0]);
         if (!any_ok) return;
         const int L0 = __ffs(any_ok) - 1;
         double y0 = (double)__shfl_sync(0xffffffffu, vals[0], L0);
         if (L1) y0 = fabs(y0);
-        S = y0;
-        nJ = 1;
-        lam = r - y0;
-        rs = __shfl_sync(0xffffffffu, eidx0, L0);
-        const double c = condat_c<L1>(lam);
-        const GtThreshold g = make_gt(c);
-        const float rd = f32_rd(c);
+        st.S = y0;
+        st.nJ = 1;
+        st.rs = __shfl_sync(0xffffffffu, eidx0, L0);
+        condat_set_lam<L1>(st, r - y0);
 #pragma unroll
         for (int j = 0; j < V; j++) {
             const bool after = (lane > L0) || (lane == L0 && j > 0);
-            pass[j] = okv[j] && after && condat_test<T, L1>(vals[j], g, rd);
+            pass[j] = okv[j] && after && condat_test<T, L1>(vals[j], st.g, st.rd);
         }
     } else {
-        const double c = condat_c<L1>(lam);
-        const GtThreshold g = make_gt(c);
-        const float rd = f32_rd(c);
 #pragma unroll
-        for (int j = 0; j < V; j++) pass[j] = okv[j] && (eidx0 + j < before) && condat_test<T, L1>(vals[j], g, rd);
+        for (int j = 0; j < V; j++)
+            pass[j] = okv[j] && (eidx0 + j < before) && condat_test<T, L1>(vals[j], st.g, st.rd);
     }
     while (true) {
         unsigned m[V];
@@ -126,37 +145,31 @@ __device__ __forceinline__ void condat_slab(const T (&vals)[VecOf<T>::V], const 
 #pragma unroll
         for (int j = V - 1; j >= 0; j--)
             if ((m[j] >> Lf) & 1u) jf = j;
-        T mine = vals[0];
-#pragma unroll
-        for (int j = 1; j < V; j++)
-            if (j == jf) mine = vals[j];
-        double yv = (double)__shfl_sync(0xffffffffu, mine, Lf);
+        double yv = (double)__shfl_sync(0xffffffffu, pick(vals, jf), Lf);
         if (L1) yv = fabs(yv);
         const int64_t e = __shfl_sync(0xffffffffu, eidx0, Lf) + jf;
         if (first_loop) {
-            const double lamn = (r - S - yv) / (double)(nJ + 1);
+            const double lamn = (r - st.S - yv) / (double)(st.nJ + 1);
             if (lamn < r - yv) {
-                S += yv;
-                nJ += 1;
-                lam = lamn;
+                st.S += yv;
+                st.nJ += 1;
+                condat_set_lam<L1>(st, lamn);
             } else {  // restart: J~ <- J~ u J, J <- {j}
-                rs = e;
-                S = yv;
-                nJ = 1;
-                lam = r - yv;
+                st.rs = e;
+                st.S = yv;
+                st.nJ = 1;
+                condat_set_lam<L1>(st, r - yv);
             }
         } else {
-            lam = (r - S - yv) / (double)(nJ + 1);
-            S += yv;
-            nJ += 1;
+            const double lamn = (r - st.S - yv) / (double)(st.nJ + 1);
+            st.S += yv;
+            st.nJ += 1;
+            condat_set_lam<L1>(st, lamn);
         }
-        const double c = condat_c<L1>(lam);
-        const GtThreshold g = make_gt(c);
-        const float rd = f32_rd(c);
 #pragma unroll
         for (int j = 0; j < V; j++) {
             const bool after = (lane > Lf) || (lane == Lf && j > jf);
-            pass[j] = pass[j] && after && condat_test<T, L1>(vals[j], g, rd);
+            pass[j] = pass[j] && after && condat_test<T, L1>(vals[j], st.g, st.rd);
         }
     }
 }
@@ -165,13 +178,15 @@ template <typename T, bool L1>
 __device__ void condat_chunk(const T* __restrict__ y, int64_t n, bool aligned, double r, int64_t w, int64_t W,
                              double& S_out, long long& nJ_out) {
     constexpr int V = VecOf<T>::V;
-    constexpr int K = kCondatVecsPerLane;
+    constexpr int K = condat_k<T>();
     constexpr int TILE = 32 * K * V;
     const int lane = threadIdx.x & 31;
     const int64_t ntiles = (n + TILE - 1) / TILE;
-    double lam = 0.0, S = 0.0;
-    long long nJ = 0;
-    int64_t rs = -1;
+    CondatState st;
+    st.S = 0.0;
+    st.nJ = 0;
+    st.rs = -1;
+    condat_set_lam<L1>(st, 0.0);
     for (int64_t t = w; t < ntiles; t += W) {
         T vals[K][V];
         bool okv[K][V];
@@ -179,11 +194,12 @@ __device__ void condat_chunk(const T* __restrict__ y, int64_t n, bool aligned, d
         for (int k = 0; k < K; k++) load_vec<T>(y, n, t * 32 * K + k * 32 + lane, aligned, vals[k], okv[k]);
 #pragma unroll
         for (int k = 0; k < K; k++)
-            condat_slab<T, L1>(vals[k], okv[k], (t * 32 * K + k * 32 + lane) * V, INT64_MAX, true, r, lam, S, nJ, rs);
+            condat_slab<T, L1>(vals[k], okv[k], (t * 32 * K + k * 32 + lane) * V, INT64_MAX, true, r, st);
     }
     // final loop of Alg. 2: re-scan the chunk prefix before the last restart
-    if (nJ > 0 && rs >= 0) {
-        const int64_t tlast = rs / TILE;
+    if (st.nJ > 0 && st.rs >= 0) {
+        const int64_t tlast = st.rs / TILE;
+        const int64_t before = st.rs;
         for (int64_t t = w; t <= tlast; t += W) {
             T vals[K][V];
             bool okv[K][V];
@@ -191,19 +207,145 @@ __device__ void condat_chunk(const T* __restrict__ y, int64_t n, bool aligned, d
             for (int k = 0; k < K; k++) load_vec<T>(y, n, t * 32 * K + k * 32 + lane, aligned, vals[k], okv[k]);
 #pragma unroll
             for (int k = 0; k < K; k++)
-                condat_slab<T, L1>(vals[k], okv[k], (t * 32 * K + k * 32 + lane) * V, rs, false, r, lam, S, nJ, rs);
+                condat_slab<T, L1>(vals[k], okv[k], (t * 32 * K + k * 32 + lane) * V, before, false, r, st);
         }
     }
-    S_out = S;
-    nJ_out = nJ;
+    S_out = st.S;
+    nJ_out = st.nJ;
+}
+
+// ---- one Newton pass (Alg. 4 evaluation) over all elements --------------------------------
+// phi(lambda) = sum over y_i > -lambda of (y_i + lambda), phi'_- = #{y_i > -lambda} and, in the
+// first pass only (FIRST), the ties #{y_i = -lambda} for phi'_+ and the NaN check.  The test
+// is one 64-bit integer compare (FP64 data; NEG = sign of the threshold) or one float
+// compare (FP32 data); y_i + lambda is formed only for the selected elements.
+struct PassAcc {
+    double acc64;
+    df acc32;
+    unsigned cm, ct;
+    bool nan;
+};
+
+template <typename T, bool L1, bool NEG, bool FIRST>
+__device__ __forceinline__ void newton_sweep(const T* __restrict__ y, int64_t n, int64_t nv, bool aligned, bool rev,
+                                             unsigned long long tb, float rd, float ru, double lam, df Lm,
+                                             PassAcc& pa) {
+    constexpr int V = VecOf<T>::V;
+    constexpr int U = kStreamU;
+    using VT = typename VecOf<T>::type;
+    const int lane = threadIdx.x & 31;
+    const WarpSweep sw(nv, U);
+    for (int64_t it = 0; it < sw.count; it++) {
+        const int64_t base = sw.base(it, rev);
+        const bool full = aligned && (base + 32 * U) * V <= n;  // warp-uniform
+        T vv[U][V];
+        bool okk[U][V];
+        if (full) {
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const VT w = __ldg(reinterpret_cast<const VT*>(y) + base + u * 32 + lane);
+                const T* s = reinterpret_cast<const T*>(&w);
+#pragma unroll
+                for (int j = 0; j < V; j++) {
+                    vv[u][j] = s[j];
+                    okk[u][j] = true;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < U; u++) load_vec<T>(y, n, base + u * 32 + lane, aligned, vv[u], okk[u]);
+        }
+        unsigned selm = 0;
+#pragma unroll
+        for (int uj = 0; uj < U * V; uj++) {
+            const int u = uj / V, j = uj % V;
+            bool sel, tie = false, nan = false;
+            if constexpr (sizeof(T) == 8) {
+                unsigned long long b = bits_of((double)vv[u][j]);
+                if (L1) b &= 0x7FFFFFFFFFFFFFFFull;
+                sel = NEG ? (b < tb) : ((long long)b > (long long)tb);
+                if (FIRST) {
+                    tie = !sel && (b == tb || ((b | tb) << 1) == 0ull);
+                    nan = (b & 0x7FFFFFFFFFFFFFFFull) > 0x7FF0000000000000ull;
+                }
+            } else {
+                const float f = L1 ? fabsf((float)vv[u][j]) : (float)vv[u][j];
+                sel = f > rd;
+                if (FIRST) {
+                    tie = !sel && f >= ru;
+                    nan = f != f;
+                }
+            }
+            sel = sel && okk[u][j];
+            selm |= (sel ? 1u : 0u) << uj;
+            if (FIRST) {
+                pa.ct += (tie && okk[u][j]) ? 1u : 0u;
+                pa.nan |= nan && okk[u][j];
+            }
+        }
+        pa.cm += __popc(selm);
+        // y_i + lambda, one loop trip per selected element: B300's FP64 pipe takes ~20 cycles
+        // per warp instruction, so none may sit on the path of the unselected elements
+        for (unsigned m = selm; m; m &= m - 1) {
+            const T tv = pick2(vv, __ffs(m) - 1);
+            if constexpr (sizeof(T) == 8) {
+                pa.acc64 += (L1 ? fabs((double)tv) : (double)tv) + lam;
+            } else {
+                pa.acc32 = df_add(pa.acc32, df_add_f(Lm, L1 ? fabsf((float)tv) : (float)tv));
+            }
+        }
+    }
+}
+
+// per-block totals of a pass (fixed order) -> partials slot `par`
+__device__ __forceinline__ void write_pass_partials(double* part, int par, double acc, unsigned cm, unsigned ct,
+                                                    double* sh_d, unsigned* sh_u) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    acc = warp_sum(acc);
+    cm = __reduce_add_sync(0xffffffffu, cm);
+    ct = __reduce_add_sync(0xffffffffu, ct);
+    if (lane == 0) {
+        sh_d[wid] = acc;
+        sh_u[wid] = cm;
+        sh_u[NWARP + wid] = ct;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        unsigned long long c0 = 0, c1 = 0;
+        for (int w = 0; w < NWARP; w++) {
+            t += sh_d[w];
+            c0 += sh_u[w];
+            c1 += sh_u[NWARP + w];
+        }
+        const double pv[3] = {t, (double)c0, (double)(c0 + c1)};
+        write_partials<3>(part, par, pv);
+    }
+}
+
+// grid totals of slot `par` by warp 0 (fixed order); valid in lane 0 of warp 0
+__device__ __forceinline__ void warp0_grid_sums(const double* part, int par, double (&out)[3]) {
+    const int G = gridDim.x;
+    const int lane = threadIdx.x & 31;
+    double v[3] = {0.0, 0.0, 0.0};
+    for (int bI = lane; bI < G; bI += 32)
+#pragma unroll
+        for (int q = 0; q < 3; q++) v[q] += ld_cg(part + ((size_t)par * kPartialQ + q) * G + bI);
+#pragma unroll
+    for (int q = 0; q < 3; q++) out[q] = warp_sum(v[q]);
 }
 
 // ---- the persistent kernel ----------------------------------------------------------------
 template <typename T, bool L1>
-__global__ void __launch_bounds__(NT) simplex_kernel(SimplexArgs A) {
+__global__ void __launch_bounds__(NT, 2) simplex_kernel(SimplexArgs A) {
     constexpr int V = VecOf<T>::V;
     __shared__ double sh[kPartialQ][NWARP];
     __shared__ double bc[kPartialQ];
+    __shared__ double sh_d[NWARP];
+    __shared__ unsigned sh_u[2 * NWARP];
+    // loop state written by thread 0 after each update, read by all threads
+    __shared__ double s_lam, s_final;
+    __shared__ int s_done, s_bad;
     const T* __restrict__ y = static_cast<const T*>(A.y);
     const int64_t n = A.n;
     const int64_t nv = (n + V - 1) / V;
@@ -228,27 +370,47 @@ __global__ void __launch_bounds__(NT) simplex_kernel(SimplexArgs A) {
         if (sum_pass) {
             df acc = df_make(0.0f);
             double acc_wide = 0.0;  // FP64 values outside the df operating range
-            double mx = -INFINITY;
-            for (int64_t qw = gwarp * 32; qw < nv; qw += nwarps * 32) {
-                T v[V];
-                bool ok[V];
-                load_vec<T>(y, n, qw + lane, aligned, v, ok);
+            long long mxk = order_key(-INFINITY);
+            float mxf = -INFINITY;
+            const WarpSweep sw(nv, kStreamU);
+            for (int64_t it = 0; it < sw.count; it++) {
+                const int64_t base = sw.base(it, false);
+                T vv[kStreamU][V];
+                bool okk[kStreamU][V];
 #pragma unroll
-                for (int j = 0; j < V; j++) {
-                    if (!ok[j]) continue;
-                    const T t = L1 ? (T)fabs((double)v[j]) : v[j];
+                for (int u = 0; u < kStreamU; u++) load_vec<T>(y, n, base + u * 32 + lane, aligned, vv[u], okk[u]);
+                unsigned widem = 0;
+#pragma unroll
+                for (int uj = 0; uj < kStreamU * V; uj++) {
+                    const int u = uj / V, j = uj % V;
+                    if (!okk[u][j]) continue;
                     if constexpr (sizeof(T) == 8) {
-                        if (df_in_range((double)t, false)) acc = df_add(acc, split_f64((double)t));
-                        else acc_wide += (double)t;
+                        const double t = L1 ? __longlong_as_double(__double_as_longlong(vv[u][j]) & 0x7FFFFFFFFFFFFFFFll)
+                                            : (double)vv[u][j];
+                        const bool inr = df_in_range(t, false);
+                        acc = df_add(acc, inr ? split_f64(t) : df_make(0.0f));
+                        widem |= (inr ? 0u : 1u) << uj;
+                        bad |= f64_is_nan(t);
+                        const long long kk = order_key(t);
+                        mxk = kk > mxk ? kk : mxk;
                     } else {
-                        acc = df_add_f(acc, (float)t);
+                        const float t = L1 ? fabsf((float)vv[u][j]) : (float)vv[u][j];
+                        acc = df_add_f(acc, t);
+                        bad |= (t != t);
+                        mxf = fmaxf(mxf, t);
                     }
-                    mx = fmax(mx, (double)t);
-                    bad |= (v[j] != v[j]);
+                }
+                if constexpr (sizeof(T) == 8) {
+                    // values outside the df operating range: exact FP64, one trip per element
+                    for (unsigned m = widem; m; m &= m - 1) {
+                        const T tv = pick2(vv, __ffs(m) - 1);
+                        acc_wide += L1 ? fabs((double)tv) : (double)tv;
+                    }
                 }
             }
             q[0] = df_to_f64(acc) + acc_wide;
-            q[3] = mx;
+            if constexpr (sizeof(T) == 8) q[3] = from_order_key(mxk);
+            else q[3] = (double)mxf;
             passes++;
         }
         if (condat) {
@@ -293,7 +455,7 @@ __global__ void __launch_bounds__(NT) simplex_kernel(SimplexArgs A) {
         if (condat) {
             lam0 = (r - red[1]) / red[2];  // eq. (lambdaJ) on the union of the chunks' J
             nchunks = (int)nwarps;
-            tile = 32 * kCondatVecsPerLane * V;
+            tile = 32 * condat_k<T>() * V;
         } else if (A.init == CQK_INIT_GIVEN) {
             lam0 = fmax(A.lambda0, -red[3]);  // Alg. 4, line 1
         } else {
@@ -303,9 +465,11 @@ __global__ void __launch_bounds__(NT) simplex_kernel(SimplexArgs A) {
     bool bad_input = A.validate && (__ldcg(&A.hdr->flags) & kFlagBadInput);
 
     // ------------------------------------------------------------------ Newton loop (Alg. 4)
-    double lam = lam0, lower = -INFINITY, upper = INFINITY, slope = 0.0, final_lam = lam0;
-    int status = CQK_OK, stop = CQK_STOP_NONE, k = 0;
-    bool copy = false;  // l1 ball, y inside
+    // thread 0 keeps the bracket and the stopping logic; every thread keeps lambda
+    double lam = lam0, final_lam = lam0;
+    double lower = -INFINITY, upper = INFINITY, slope = 0.0;  // thread 0
+    int status = CQK_OK, stop = CQK_STOP_NONE, k = 0;         // thread 0 (status also all)
+    bool copy = false;                                       // l1 ball, y inside
     if (bad_input) {
         status = CQK_BAD_INPUT;
     } else if (L1 && abs_sum <= r) {
@@ -319,121 +483,113 @@ __global__ void __launch_bounds__(NT) simplex_kernel(SimplexArgs A) {
                 status = CQK_MAXITER;
                 break;
             }
-            double acc64 = 0.0;
-            df acc32 = df_make(0.0f);
-            long long cm = 0, ct = 0;
-            bool nan_seen = false;
-            const double c = -lam;
+            PassAcc pa;
+            pa.acc64 = 0.0;
+            pa.acc32 = df_make(0.0f);
+            pa.cm = pa.ct = 0u;
+            pa.nan = false;
+            const bool rev = (k & 1) == 0;
+            const bool first = (k == 0);
             if constexpr (sizeof(T) == 8) {
-                const GtThreshold g = make_gt(c);
-                const unsigned long long cb = g.bits;
-                for (int64_t qw = gwarp * 32; qw < nv; qw += nwarps * 32) {
-                    T v[V];
-                    bool ok[V];
-                    load_vec<T>(y, n, qw + lane, aligned, v, ok);
-#pragma unroll
-                    for (int j = 0; j < V; j++) {
-                        unsigned long long b = bits_of((double)v[j]);
-                        if (L1) b &= 0x7FFFFFFFFFFFFFFFull;
-                        const bool sel = ok[j] && gt_bits(b, g);
-                        const bool tie = ok[j] && !sel && (b == cb || ((b | cb) << 1) == 0ull);
-                        if (sel) {
-                            acc64 += __longlong_as_double((long long)b) + lam;
-                            cm++;
-                        }
-                        ct += tie;
-                        nan_seen |= ok[j] && ((b & 0x7FFFFFFFFFFFFFFFull) > 0x7FF0000000000000ull);
-                    }
+                const GtThreshold g = make_gt(-lam);
+                const df Lm = df_make(0.0f);
+                if (g.neg) {
+                    if (first) newton_sweep<T, L1, true, true>(y, n, nv, aligned, rev, g.bits, 0.f, 0.f, lam, Lm, pa);
+                    else newton_sweep<T, L1, true, false>(y, n, nv, aligned, rev, g.bits, 0.f, 0.f, lam, Lm, pa);
+                } else {
+                    if (first) newton_sweep<T, L1, false, true>(y, n, nv, aligned, rev, g.bits, 0.f, 0.f, lam, Lm, pa);
+                    else newton_sweep<T, L1, false, false>(y, n, nv, aligned, rev, g.bits, 0.f, 0.f, lam, Lm, pa);
                 }
             } else {
-                const float rd = f32_rd(c), ru = f32_ru(c);
+                const float rd = f32_rd(-lam), ru = f32_ru(-lam);
                 const df Lm = df_from_f64(lam);
-                for (int64_t qw = gwarp * 32; qw < nv; qw += nwarps * 32) {
-                    T v[V];
-                    bool ok[V];
-                    load_vec<T>(y, n, qw + lane, aligned, v, ok);
-#pragma unroll
-                    for (int j = 0; j < V; j++) {
-                        const float f = L1 ? fabsf((float)v[j]) : (float)v[j];
-                        const bool sel = ok[j] && f > rd;
-                        const bool tie = ok[j] && !sel && f >= ru;
-                        if (sel) {
-                            acc32 = df_add(acc32, df_add_f(Lm, f));
-                            cm++;
-                        }
-                        ct += tie;
-                        nan_seen |= ok[j] && (f != f);
-                    }
-                }
-                acc64 = df_to_f64(acc32);
+                if (first) newton_sweep<T, L1, false, true>(y, n, nv, aligned, rev, 0ull, rd, ru, lam, Lm, pa);
+                else newton_sweep<T, L1, false, false>(y, n, nv, aligned, rev, 0ull, rd, ru, lam, Lm, pa);
+                pa.acc64 = df_to_f64(pa.acc32);
             }
             passes++;
-            if (A.validate && __any_sync(0xffffffffu, nan_seen) && lane == 0) atomicOr(&A.hdr->flags, kFlagBadInput);
-            double pv[3] = {acc64, (double)cm, (double)(cm + ct)};
-            block_sum<3>(pv, sh);
-            write_partials<3>(A.part, par, pv);
+            if (A.validate && first && __any_sync(0xffffffffu, pa.nan) && lane == 0)
+                atomicOr(&A.hdr->flags, kFlagBadInput);
+            write_pass_partials(A.part, par, pa.acc64, pa.cm, pa.ct, sh_d, sh_u);
             if (!grid_barrier(bar, bar_target, err, A.limit_ns, CQK_TIMEOUT)) {
                 if (threadIdx.x == 0) A.info->status = CQK_TIMEOUT;
                 return;
             }
             bar_target += (unsigned)G;
-            double red[3];
-            grid_reduce<3>(A.part, par, -1, red, sh, bc);
+            if (threadIdx.x < 32) {
+                double red[3];
+                warp0_grid_sums(A.part, par, red);
+                if (threadIdx.x == 0) {
+                    int done = 0, bad = 0;
+                    double next = lam;
+                    if (A.validate && first && (__ldcg(&A.hdr->flags) & kFlagBadInput)) {
+                        bad = 1;
+                        done = 1;
+                    } else {
+                        const double phi = red[0], dminus = red[1], dplus = red[2];
+                        const double gk = phi - r;
+                        double step = 0.0;
+                        if (k == 0) {
+                            if (gk == 0.0) {
+                                stop = CQK_STOP_EXACT;
+                                done = 1;
+                            } else if (gk < 0.0) {
+                                lower = lam;
+                                slope = dplus;
+                                step = -gk / dplus;
+                            } else {
+                                upper = lam;
+                                slope = dminus;
+                                step = -gk / dminus;
+                            }
+                        } else if (gk <= 0.0) {
+                            stop = CQK_STOP_BELOW;
+                            done = 1;
+                        } else {
+                            upper = lam;
+                            slope = dminus;
+                            step = -gk / dminus;
+                        }
+                        double fin = lam;
+                        if (!done && upper - lower < A.eps34 * fmax(fabs(upper), fabs(lower))) {
+                            stop = CQK_STOP_BRACKET;
+                            done = 1;
+                        }
+                        if (!done && fabs(step) < A.eps34) {
+                            stop = CQK_STOP_STEP;
+                            done = 1;
+                            if (A.final_step) fin = lam + step;  // the Newton step already computed
+                        }
+                        if (!done) {
+                            next = lam + step;
+                            if (next == lam) {
+                                stop = CQK_STOP_SAME;
+                                done = 1;
+                            }
+                        }
+                        s_final = fin;
+                    }
+                    s_lam = next;
+                    s_done = done;
+                    s_bad = bad;
+                }
+            }
+            __syncthreads();
             par ^= 1;
-            if (A.validate && (__ldcg(&A.hdr->flags) & kFlagBadInput)) {
+            if (s_bad) {
                 bad_input = true;
                 status = CQK_BAD_INPUT;
                 k++;
                 break;
             }
-            const double phi = red[0], dminus = red[1], dplus = red[2];
-            const double gk = phi - r;
-            double step = 0.0;
-            bool done = false;
-            final_lam = lam;
-            if (k == 0) {
-                if (gk == 0.0) {
-                    stop = CQK_STOP_EXACT;
-                    done = true;
-                } else if (gk < 0.0) {
-                    lower = lam;
-                    slope = dplus;
-                    step = -gk / dplus;
-                } else {
-                    upper = lam;
-                    slope = dminus;
-                    step = -gk / dminus;
-                }
-            } else if (gk <= 0.0) {
-                stop = CQK_STOP_BELOW;
-                done = true;
-            } else {
-                upper = lam;
-                slope = dminus;
-                step = -gk / dminus;
-            }
-            if (!done && upper - lower < A.eps34 * fmax(fabs(upper), fabs(lower))) {
-                stop = CQK_STOP_BRACKET;
-                done = true;
-            }
-            if (!done && fabs(step) < A.eps34) {
-                stop = CQK_STOP_STEP;
-                done = true;
-                if (A.final_step) final_lam = lam + step;  // the Newton step already computed
-            }
-            if (!done) {
-                const double next = lam + step;
-                if (next == lam) {
-                    stop = CQK_STOP_SAME;
-                    done = true;
-                } else {
-                    lam = next;
-                }
-            }
-            if (done) {
+            if (s_done) {
+                final_lam = s_final;
                 k++;
                 break;
             }
+            lam = s_lam;
+            final_lam = lam;
+            __syncthreads();  // s_lam is rewritten only after every thread has read it
         }
     }
 
@@ -447,54 +603,69 @@ __global__ void __launch_bounds__(NT) simplex_kernel(SimplexArgs A) {
         const GtThreshold g = make_gt(-lamf);
         const float rd = f32_rd(-lamf);
         const df Lm = df_from_f64(lamf);
-        for (int64_t qw = gwarp * 32; qw < nv; qw += nwarps * 32) {
-            const int64_t q = qw + lane;
-            T v[V];
-            bool ok[V];
-            load_vec<T>(y, n, q, aligned, v, ok);
-            T o[V];
-            bool sel[V];
+        const WarpSweep sw(nv, kStreamU);
+        const bool rev = (k & 1) == 0;  // opposite direction to the last Newton pass
+        for (int64_t it = 0; it < sw.count; it++) {
+            const int64_t base = sw.base(it, rev);
+            T vv[kStreamU][V];
+            bool okk[kStreamU][V];
 #pragma unroll
-            for (int j = 0; j < V; j++) {
-                if (copy) {
-                    o[j] = v[j];
-                    sel[j] = ok[j] && v[j] != T(0);
-                } else if constexpr (sizeof(T) == 8) {
-                    const unsigned long long b = bits_of((double)v[j]);
-                    const unsigned long long ab = L1 ? (b & 0x7FFFFFFFFFFFFFFFull) : b;
-                    sel[j] = ok[j] && gt_bits(ab, g);
-                    double xv = sel[j] ? (__longlong_as_double((long long)ab) + lamf) : 0.0;
-                    if (L1 && (b >> 63)) xv = -xv;
-                    o[j] = (T)xv;
-                } else {
-                    const float f = (float)v[j];
-                    const float af = L1 ? fabsf(f) : f;
-                    sel[j] = ok[j] && af > rd;
-                    float xv = 0.0f;
-                    if (sel[j]) {
-                        const df t = df_add_f(Lm, af);
-                        xv = __fadd_rn(t.hi, t.lo);
+            for (int u = 0; u < kStreamU; u++) load_vec<T>(y, n, base + u * 32 + lane, aligned, vv[u], okk[u]);
+#pragma unroll
+            for (int u = 0; u < kStreamU; u++) {
+                const int64_t qw = base + u * 32;
+                const int64_t q = qw + lane;
+                const T(&v)[V] = vv[u];
+                const bool(&ok)[V] = okk[u];
+                T o[V];
+                bool sel[V];
+                unsigned selv = 0;
+#pragma unroll
+                for (int j = 0; j < V; j++) {
+                    if constexpr (sizeof(T) == 8) {
+                        const unsigned long long b = bits_of((double)v[j]);
+                        const unsigned long long ab = b & 0x7FFFFFFFFFFFFFFFull;
+                        sel[j] = ok[j] && (copy ? ab != 0ull : gt_bits(L1 ? ab : b, g));
+                    } else {
+                        const float f = (float)v[j];
+                        sel[j] = ok[j] && (copy ? f != 0.0f : (L1 ? fabsf(f) : f) > rd);
                     }
-                    if (L1 && f < 0.0f) xv = -xv;
-                    o[j] = (T)xv;
+                    o[j] = copy ? v[j] : T(0);
+                    nz += sel[j];
+                    selv |= (sel[j] && !copy ? 1u : 0u) << j;
                 }
-                if (sel[j]) {
-                    nz++;
-                    if constexpr (sizeof(T) == 8) sx += fabs((double)o[j]);
-                    else sx32 = df_add_f(sx32, fabsf((float)o[j]));
+                // x_i = y_i + lambda (l1: sgn(y_i)(|y_i| + lambda)), one trip per selected element
+                for (unsigned m = selv; m; m &= m - 1) {
+                    const int j = __ffs(m) - 1;
+                    const T vj = pick(v, j);
+                    if constexpr (sizeof(T) == 8) {
+                        const double yv = (double)vj;
+                        double xv = (L1 ? fabs(yv) : yv) + lamf;
+                        if (L1 && yv < 0.0) xv = -xv;
+                        put(o, j, (T)xv);
+                        sx += fabs(xv);
+                    } else {
+                        const float f = (float)vj;
+                        const df t = df_add_f(Lm, L1 ? fabsf(f) : f);
+                        float xv = __fadd_rn(t.hi, t.lo);
+                        if (L1 && f < 0.0f) xv = -xv;
+                        put(o, j, (T)xv);
+                        sx32 = df_add_f(sx32, fabsf(xv));
+                    }
                 }
+                store_vec<T>(x, n, q, aligned, o);
+                if (A.mask) store_mask<V>(A.mask, n, qw, sel);
             }
-            store_vec<T>(x, n, q, aligned, o);
-            if (A.mask) store_mask<V>(A.mask, n, qw, sel);
         }
     }
     if constexpr (sizeof(T) == 4) sx = df_to_f64(sx32);
     double pv[2] = {sx, (double)nz}, tot[2];
     if (last_block_sums<2>(A.part, &A.hdr->ticket, pv, tot, sh) && threadIdx.x == 0) {
         cqk_info inf;
+        const double sumx = copy ? abs_sum : tot[0];  // inside the l1 ball x = y
         inf.lambda = final_lam;
-        inf.residual = tot[0] - r;
-        inf.abs_bx = tot[0];
+        inf.residual = sumx - r;
+        inf.abs_bx = sumx;
         inf.slope = slope;
         inf.lambda0 = lam0;
         inf.nfree = (int64_t)tot[1];
