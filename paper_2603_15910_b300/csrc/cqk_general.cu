@@ -26,6 +26,7 @@
 #include <string.h>
 
 #include "cqk_block.cuh"
+#include "cqk_stage.cuh"
 
 namespace cqk {
 namespace {
@@ -48,6 +49,7 @@ struct GeneralArgs {
     int validate;
     int final_step;
     int aligned;
+    int staged;  // arrays staged through shared memory by bulk copies (aligned data)
     int phi_only;
     unsigned long long limit_ns;
     int fault_inject;
@@ -55,31 +57,32 @@ struct GeneralArgs {
     double* part;
 };
 
-// Per-thread accumulators of one pass.  The df sums are flushed into the FP64 ones every
-// kFlushEvery sweep iterations (16 vectors), bounding the df summation error by ~16*V*2^-47 of
-// the flushed partial sums.
-constexpr int kFlushEvery = 8;   // sweep iterations (kGenU vectors each) between flushes
-constexpr int kGenU = 2;         // 16-byte vectors per array in flight per lane
+// Per-thread accumulators of one pass.  The df sums (lazily normalised) are flushed into the
+// FP64 ones every kFlushEvery sweep iterations, bounding the df summation error by
+// ~16*V*2^-46 of the flushed partial sums.
+constexpr int kFlushEvery = 8;  // sweep iterations (kGenU vectors each) between flushes
+constexpr int kGenU = 2;        // 16-byte vectors per array in flight per lane
+constexpr unsigned kFlagWide = 2u;  // some FP64 value lies outside the df operating range
 struct EvalAcc {
-    df phi, absbx, sfree;
+    LazyDf phi, absbx, sfree;
     double phi64, absbx64, sfree64, satl, satu;
     long long nfree;
-    bool bad;
+    bool bad, wide;
     __device__ void init() {
-        phi = absbx = sfree = df_make(0.0f);
+        phi = absbx = sfree = LazyDf{0.0f, 0.0f};
         phi64 = absbx64 = sfree64 = satl = satu = 0.0;
         nfree = 0;
-        bad = false;
+        bad = wide = false;
     }
     __device__ void flush() {
-        phi64 += df_to_f64(phi);
-        absbx64 += df_to_f64(absbx);
-        sfree64 += df_to_f64(sfree);
-        phi = absbx = sfree = df_make(0.0f);
+        phi64 += lazy_value(phi);
+        absbx64 += lazy_value(absbx);
+        sfree64 += lazy_value(sfree);
+        phi = absbx = sfree = LazyDf{0.0f, 0.0f};
     }
 };
 
-// status of one element: 0 free, 1 x = l, 2 x = u
+// status of one element: 0 free, 1 x = l, 2 x = u; ties = on a breakpoint
 struct Cls {
     int c;
     bool tieL, tieU;
@@ -87,7 +90,7 @@ struct Cls {
 
 // ---- FP64 data, exact FP64 (values outside the df range) -------------------------------
 __device__ __noinline__ double elem_f64_exact(double a, double b, double d, double l, double u, double lam,
-                                                 EvalAcc& acc, bool want_acc, Cls& cl) {
+                                              EvalAcc& acc, bool want_acc, Cls& cl) {
     const double lb = lam * b;
     const double v = a + lb;
     const double dl = isinf(l) ? l : d * l;
@@ -114,36 +117,35 @@ __device__ __noinline__ double elem_f64_exact(double a, double b, double d, doub
 }
 
 // ---- FP64 data in the df range ----------------------------------------------------------
-__device__ __forceinline__ df elem_df(double a, double b, double d, double l, double u, df Lm, EvalAcc& acc,
-                                      bool want_acc, Cls& cl, df& beta_out) {
-    const df A = split_f64(a), B = split_f64(b), D = split_f64(d), Lo = split_f64(l), Up = split_f64(u);
-    const df lb = df_mul(Lm, B);
-    const df v = df_add(A, lb);
+// v = a + lambda b (fused df), 1/d by the MUFU reciprocal and one df Newton correction,
+// t = v/d, and the status of x_i(lambda) read off t against l, u (equivalent to v against
+// d l, d u for d > 0) with the tie band of the file header, scaled to x.
+// Returns x; bx = b x, beta = b^2/d.
+__device__ __forceinline__ df elem_df(df A, df B, df D, df Lo, df Up, df Lm, Cls& cl, df& bx, df& beta) {
+    const df p = two_prod(Lm.hi, B.hi);
+    const float e = fmaf(Lm.hi, B.lo, fmaf(Lm.lo, B.hi, p.lo));
+    const df s = two_sum(A.hi, p.hi);
+    const df v = fast_two_sum(s.hi, __fadd_rn(__fadd_rn(s.lo, e), A.lo));
+    const float r0 = rcp_approx(D.hi);
+    const float res = fmaf(-D.lo, r0, fmaf(-D.hi, r0, 1.0f));
+    const df invd = fast_two_sum(r0, __fmul_rn(r0, res));
+    const df t = df_mul(v, invd);
     const bool linf = isinf(Lo.hi), uinf = isinf(Up.hi);
-    const df dl = linf ? Lo : df_mul(D, Lo);
-    const df du = uinf ? Up : df_mul(D, Up);
-    const float sc = fabsf(A.hi) + fabsf(lb.hi);
-    const df eL = df_add(v, df_neg(dl)), eU = df_add(v, df_neg(du));
-    const bool tieL = !linf && fabsf(eL.hi) <= kTieRel * (sc + fabsf(dl.hi));
-    const bool tieU = !uinf && fabsf(eU.hi) <= kTieRel * (sc + fabsf(du.hi));
+    const float dL = __fadd_rn(__fsub_rn(t.hi, Lo.hi), __fsub_rn(t.lo, Lo.lo));
+    const float dU = __fadd_rn(__fsub_rn(t.hi, Up.hi), __fsub_rn(t.lo, Up.lo));
+    const float sc = __fmul_rn(__fadd_rn(fabsf(A.hi), fabsf(p.hi)), r0);  // (|a| + |lambda b|)/d
+    const bool tieL = !linf && fabsf(dL) <= kTieRel * (sc + fabsf(Lo.hi));
+    const bool tieU = !uinf && fabsf(dU) <= kTieRel * (sc + fabsf(Up.hi));
+    const bool below = tieL || dL < 0.0f;
+    const bool above = !below && (tieU || dU > 0.0f);
+    cl.c = below ? 1 : (above ? 2 : 0);
     cl.tieL = tieL;
     cl.tieU = tieU;
-    const bool below = tieL || (!linf && eL.hi < 0.0f);
-    const bool above = !below && (tieU || (!uinf && eU.hi > 0.0f));
-    cl.c = below ? 1 : (above ? 2 : 0);
-    const float rd = rcp_approx(D.hi);
-    const df invd = df_div(df_make(1.0f), D, rd);
-    df x = df_mul(v, invd);
+    df x = t;
     if (below) x = Lo;
     if (above) x = Up;
-    if (want_acc) {
-        const df bx = df_mul(B, x);
-        acc.phi = df_add(acc.phi, bx);
-        acc.absbx = df_add(acc.absbx, bx.hi < 0.0f ? df_neg(bx) : bx);
-        const df beta = df_mul(df_mul(B, B), invd);
-        acc.sfree = df_add(acc.sfree, cl.c == 0 ? beta : df_make(0.0f));
-        beta_out = beta;
-    }
+    bx = df_mul_lazy(B, x);
+    beta = df_mul_lazy(df_mul(B, B), invd);
     return x;
 }
 
@@ -154,49 +156,194 @@ __device__ __forceinline__ bool bad_elem(double a, double b, double d, double l,
            order_key(l) > order_key(u);
 }
 
+// the same checks on float bit patterns
+__device__ __forceinline__ bool bad_elem_f(float a, float b, float d, float l, float u) {
+    const int ia = __float_as_int(a), ib = __float_as_int(b), id = __float_as_int(d);
+    const int il = __float_as_int(l), iu = __float_as_int(u);
+    auto pos_finite = [](int v) { return v > 0 && v < 0x7F800000; };
+    auto is_nan = [](int v) { return (v & 0x7FFFFFFF) > 0x7F800000; };
+    auto key = [](int v) { return v >= 0 ? v : (int)(0x80000000u - (unsigned)v) - 1; };
+    return !pos_finite(id) || !pos_finite(ib) || (ia & 0x7F800000) == 0x7F800000 || is_nan(il) || is_nan(iu) ||
+           key(il) > key(iu);
+}
+
 // ---- FP32 data -----------------------------------------------------------------------------
-// v = a + lambda b with lambda a float pair: TwoProd + TwoSum; the tests compare the df v
-// with the exact products d*l, d*u (TwoProd); x = v/d rounded to float; b*x, |b x| and
-// b^2/d are accumulated in df.
-__device__ __forceinline__ float elem_f32(float a, float b, float d, float l, float u, df Lm, EvalAcc& acc,
-                                          bool want_acc, Cls& cl, df& beta_out) {
-    const df lb = df_mul_f(Lm, b);
-    const df v = df_add_f(lb, a);
+// v = a + lambda b with lambda a float pair (TwoProd + TwoSum), rounded once; t = v/d by the
+// MUFU reciprocal and one correction (~1 ulp); the status is read off t against l, u with a
+// tie band of 2^-20 relative (the float rounding of t); b x by TwoProd; b^2/d in float.
+constexpr float kTieRel32 = 9.5367431640625e-07f;  // 2^-20
+__device__ __forceinline__ float elem_f32(float a, float b, float d, float l, float u, df Lm, Cls& cl, df& bx,
+                                          float& beta) {
+    const df p = two_prod(Lm.hi, b);
+    const float e = fmaf(Lm.lo, b, p.lo);
+    const df s = two_sum(a, p.hi);
+    const float vh = __fadd_rn(s.hi, __fadd_rn(s.lo, e));
+    const float r0 = rcp_approx(d);
+    float t = __fmul_rn(vh, r0);
+    t = fmaf(fmaf(-t, d, vh), r0, t);
     const bool linf = isinf(l), uinf = isinf(u);
-    const df dl = linf ? df_make(l) : two_prod(d, l);
-    const df du = uinf ? df_make(u) : two_prod(d, u);
-    const float sc = fabsf(a) + fabsf(lb.hi);
-    const df eL = df_add(v, df_neg(dl)), eU = df_add(v, df_neg(du));
-    const bool tieL = !linf && fabsf(eL.hi) <= kTieRel * (sc + fabsf(dl.hi));
-    const bool tieU = !uinf && fabsf(eU.hi) <= kTieRel * (sc + fabsf(du.hi));
+    const float dL = __fsub_rn(t, l), dU = __fsub_rn(t, u);
+    const float sc = __fmul_rn(__fadd_rn(fabsf(a), fabsf(p.hi)), r0);
+    const bool tieL = !linf && fabsf(dL) <= kTieRel32 * (sc + fabsf(l));
+    const bool tieU = !uinf && fabsf(dU) <= kTieRel32 * (sc + fabsf(u));
+    const bool below = tieL || dL < 0.0f;
+    const bool above = !below && (tieU || dU > 0.0f);
+    cl.c = below ? 1 : (above ? 2 : 0);
     cl.tieL = tieL;
     cl.tieU = tieU;
-    const bool below = tieL || (!linf && eL.hi < 0.0f);
-    const bool above = !below && (tieU || (!uinf && eU.hi > 0.0f));
-    cl.c = below ? 1 : (above ? 2 : 0);
-    const float rd = rcp_approx(d);
-    const float vh = __fadd_rn(v.hi, v.lo);
-    float x = __fmul_rn(vh, rd);
-    x = fmaf(fmaf(-x, d, vh), rd, x);  // one correction: ~1 ulp
+    float x = t;
     if (below) x = l;
     if (above) x = u;
-    if (want_acc) {
-        const df bx = two_prod(b, x);
-        acc.phi = df_add(acc.phi, bx);
-        acc.absbx = df_add(acc.absbx, bx.hi < 0.0f ? df_neg(bx) : bx);
-        const float bb = __fmul_rn(b, b);
-        float beta = __fmul_rn(bb, rd);
-        beta = fmaf(fmaf(-beta, d, bb), rd, beta);
-        acc.sfree = df_add_f(acc.sfree, cl.c == 0 ? beta : 0.0f);
-        beta_out = df_make(beta);
-    }
+    bx = two_prod(b, x);
+    const float bb = __fmul_rn(b, b);
+    beta = __fmul_rn(bb, r0);
+    beta = fmaf(fmaf(-beta, d, bb), r0, beta);
     return x;
 }
 
-// ---- one pass over all elements: accumulate (write_x = false) or write x / mask / residual
-template <typename T>
-__device__ __forceinline__ void eval_pass(const GeneralArgs& A, double lam, bool write_x, bool check, bool rev,
-                                          EvalAcc& acc) {
+// ---- the map of one 16-byte vector of elements (V of them): accumulate (write_x = false)
+// or write x / mask and the sums of the stored x.  q = global vector index, qw = index of the
+// warp's first vector (a multiple of 32).
+// FAST: every FP64 value is known to be valid and inside the df operating range (checked in
+// the first pass), so the per-element checks are skipped.
+template <typename T, bool FAST>
+__device__ __forceinline__ void eval_vec(const GeneralArgs& A, const T (&va)[VecOf<T>::V], const T (&vb)[VecOf<T>::V],
+                                         const T (&vd)[VecOf<T>::V], const T (&vl)[VecOf<T>::V],
+                                         const T (&vu)[VecOf<T>::V], const bool (&ok)[VecOf<T>::V], int64_t q,
+                                         int64_t qw, double lam, df Lm, bool lam_ok, bool write_x, bool check,
+                                         EvalAcc& acc) {
+    constexpr int V = VecOf<T>::V;
+    const int64_t n = A.n;
+    const bool aligned = A.aligned != 0;
+    T* __restrict__ px = static_cast<T*>(A.x);
+        T xo[V];
+        bool fr[V];
+        df beta[V];
+        df xdf[V];
+        unsigned tiem = 0, widem = 0, freem = 0;
+#pragma unroll
+        for (int j = 0; j < V; j++) {
+            fr[j] = false;
+            xo[j] = T(0);
+            beta[j] = df_make(0.0f);
+            if (!ok[j]) continue;
+            const T a = va[j], b = vb[j], d = vd[j], l = vl[j], u = vu[j];
+            Cls cl;
+            df bx;
+            if constexpr (sizeof(T) == 8) {
+                df Ad, Bd, Dd, Ld, Ud;
+                if constexpr (FAST) {
+                    Ad = split_f64_finite(a);
+                    Bd = split_f64_finite(b);
+                    Dd = split_f64_finite(d);
+                    Ld = split_f64(l);
+                    Ud = split_f64(u);
+                } else {
+                    // operating range by exponent-field tests: b, d positive in [2^-60, 2^60];
+                    // a 0 or in range; l, u 0, +-inf or in range.  In-range values are finite and
+                    // not NaN, so of the sanity checks only l <= u remains for them; elements
+                    // outside the range take the exact path, which checks everything.
+                    const unsigned hb = (unsigned)__double2hiint(b), hd = (unsigned)__double2hiint(d);
+                    const unsigned ha = (unsigned)__double2hiint(a), la = (unsigned)__double2loint(a);
+                    const unsigned hl = (unsigned)__double2hiint(l), ll = (unsigned)__double2loint(l);
+                    const unsigned hu = (unsigned)__double2hiint(u), lu = (unsigned)__double2loint(u);
+                    auto rng = [](unsigned h) { return (((h >> 20) & 0x7FFu) - 963u) <= 120u; };
+                    auto zero = [](unsigned h, unsigned lo) { return ((h & 0x7FFFFFFFu) | lo) == 0u; };
+                    auto inf = [](unsigned h, unsigned lo) { return (h & 0x7FFFFFFFu) == 0x7FF00000u && lo == 0u; };
+                    const bool inr = lam_ok && ((hb >> 20) - 963u) <= 120u && ((hd >> 20) - 963u) <= 120u &&
+                                     (rng(ha) || zero(ha, la)) && (rng(hl) || zero(hl, ll) || inf(hl, ll)) &&
+                                     (rng(hu) || zero(hu, lu) || inf(hu, lu));
+                    if (!inr) {
+                        widem |= 1u << j;
+                        acc.wide = true;
+                        continue;
+                    }
+                    Ad = split_f64_finite(a);
+                    Bd = split_f64_finite(b);
+                    Dd = split_f64_finite(d);
+                    Ld = split_f64(l);
+                    Ud = split_f64(u);
+                    if (check) acc.bad |= df_lt(Ud, Ld);
+                }
+                const df xv = elem_df(Ad, Bd, Dd, Ld, Ud, Lm, cl, bx, beta[j]);
+                if (write_x) {
+                    xo[j] = cl.c == 1 ? l : (cl.c == 2 ? u : 0.0);
+                    freem |= (cl.c == 0 ? 1u : 0u) << j;
+                    xdf[j] = xv;
+                    // residual sums from b x of the df solution (within 2^-46 of the stored x)
+                    lazy_add(acc.phi, bx);
+                    lazy_add(acc.absbx, bx.hi < 0.0f ? df_neg(bx) : bx);
+                }
+            } else {
+                if (!FAST && check) acc.bad |= bad_elem_f(a, b, d, l, u);
+                float bt;
+                xo[j] = elem_f32(a, b, d, l, u, Lm, cl, bx, bt);
+                beta[j] = df_make(bt);
+            }
+            fr[j] = cl.c == 0;
+            if (!write_x) {
+                lazy_add(acc.phi, bx);
+                lazy_add(acc.absbx, bx.hi < 0.0f ? df_neg(bx) : bx);
+                lazy_add(acc.sfree, fr[j] ? beta[j] : df_make(0.0f));
+            }
+            tiem |= ((cl.tieL && !cl.tieU) ? 1u : 0u) << (2 * j);
+            tiem |= ((cl.tieU && !cl.tieL) ? 2u : 0u) << (2 * j);
+        }
+        // rare cases, one loop trip per element concerned (a data-dependent loop keeps FP64
+        // instructions off the common path): elements on a breakpoint (lateral-slope ties)
+        // and FP64 values outside the df operating range (exact FP64)
+        if (!write_x) {
+            for (unsigned m = tiem; m; m &= m - 1) {
+                const int bit = __ffs(m) - 1;
+                const double bj = df_to_f64(pick(beta, bit >> 1));
+                if (bit & 1) acc.satu += bj;
+                else acc.satl += bj;
+            }
+        }
+        if constexpr (sizeof(T) == 8 && !FAST) {
+            for (unsigned m = widem; m; m &= m - 1) {
+                const int j = __ffs(m) - 1;
+                Cls cl;
+                const T bj = pick(vb, j);
+                if (check) acc.bad |= bad_elem(pick(va, j), bj, pick(vd, j), pick(vl, j), pick(vu, j));
+                const T xj = elem_f64_exact(pick(va, j), bj, pick(vd, j), pick(vl, j),
+                                            pick(vu, j), lam, acc, !write_x, cl);
+                put(xo, j, xj);
+                put(fr, j, cl.c == 0);
+                if (write_x) {
+                    acc.phi64 += bj * xj;
+                    acc.absbx64 += fabs(bj * xj);
+                }
+            }
+        }
+        if (write_x) {
+            // free x of FP64 data: df -> double, one FP64 add per free element
+            if constexpr (sizeof(T) == 8) {
+                for (unsigned m = freem; m; m &= m - 1) {
+                    const int j = __ffs(m) - 1;
+                    put(xo, j, df_to_f64_int(pick(xdf, j)));
+                }
+            } else {
+                // FP32 data: sums of the stored (float) x, b x exact by TwoProd
+#pragma unroll
+                for (int j = 0; j < V; j++) {
+                    if (!ok[j]) continue;
+                    const df pr = two_prod((float)vb[j], (float)xo[j]);
+                    lazy_add(acc.phi, pr);
+                    lazy_add(acc.absbx, pr.hi < 0.0f ? df_neg(pr) : pr);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < V; j++) acc.nfree += (ok[j] && fr[j]) ? 1 : 0;
+            if (px) store_vec<T>(px, n, q, aligned, xo);
+            if (A.mask) store_mask<V>(A.mask, n, qw, fr);
+        }
+}
+
+// ---- one pass over all elements with plain loads (arrays not 16-byte aligned)
+template <typename T, bool FAST>
+__device__ __forceinline__ void eval_pass_plain(const GeneralArgs& A, double lam, bool write_x, bool check, bool rev,
+                                                EvalAcc& acc) {
     constexpr int V = VecOf<T>::V;
     constexpr int U = kGenU;
     const T* __restrict__ pa = static_cast<const T*>(A.a);
@@ -204,7 +351,6 @@ __device__ __forceinline__ void eval_pass(const GeneralArgs& A, double lam, bool
     const T* __restrict__ pd = static_cast<const T*>(A.d);
     const T* __restrict__ pl = static_cast<const T*>(A.l);
     const T* __restrict__ pu = static_cast<const T*>(A.u);
-    T* __restrict__ px = static_cast<T*>(A.x);
     const int64_t n = A.n;
     const int64_t nv = (n + V - 1) / V;
     const int lane = threadIdx.x & 31;
@@ -231,91 +377,88 @@ __device__ __forceinline__ void eval_pass(const GeneralArgs& A, double lam, bool
             load_vec<T>(pu, n, q, aligned, vu[w], ok[w]);
         }
 #pragma unroll
-        for (int w = 0; w < U; w++) {
-            const int64_t qw = base + w * 32;
-            const int64_t q = qw + lane;
-            T xo[V];
-            bool fr[V];
-            df beta[V];
-            unsigned tiem = 0, widem = 0;
+        for (int w = 0; w < U; w++)
+            eval_vec<T, FAST>(A, va[w], vb[w], vd[w], vl[w], vu[w], ok[w], base + w * 32 + lane, base + w * 32, lam, Lm,
+                              lam_ok, write_x, check, acc);
+    }
+}
+
+// ---- one pass with the arrays staged through shared memory by bulk copies (TileRing)
+template <typename T>
+__host__ __device__ constexpr int stage_tile() { return 8192 / (int)sizeof(T); }  // elements per array per stage
+
+template <typename T, bool FAST>
+__device__ __forceinline__ bool eval_pass_staged(const GeneralArgs& A, double lam, bool write_x, bool check, bool rev,
+                                                 EvalAcc& acc, T* smem, uint64_t* bars, unsigned& parity,
+                                                 int* err) {
+    constexpr int V = VecOf<T>::V;
+    constexpr int TT = stage_tile<T>();
+    constexpr int VPT = TT / V / NT;  // vectors per thread per tile
+    using VT = typename VecOf<T>::type;
+    const T* src[5] = {static_cast<const T*>(A.a), static_cast<const T*>(A.b), static_cast<const T*>(A.d),
+                       static_cast<const T*>(A.l), static_cast<const T*>(A.u)};
+    TileRing<T, 5, TT> ring;
+    ring.setup(A.n, smem, bars);
+    ring.parity = parity;
+    const df Lm = df_from_f64(lam);
+    const bool lam_ok = fabs(lam) <= 1.152921504606847e18;  // 2^60
+    if (threadIdx.x == 0)
+        for (int s = 0; s < kStages - 1; s++)
+            if (s < ring.count) ring.issue(ring.tile(s, rev), s, src);
+    bool okw = true;
+    for (int64_t i = 0; i < ring.count; i++) {
+        const int st = (int)(i % kStages);
+        if (threadIdx.x == 0 && i + kStages - 1 < ring.count)
+            ring.issue(ring.tile(i + kStages - 1, rev), (int)((i + kStages - 1) % kStages), src);
+        if (!mbar_wait(&ring.bar[st], (ring.parity >> st) & 1u, err, A.limit_ns, CQK_TIMEOUT)) okw = false;
+        ring.parity ^= 1u << st;
+        const int64_t c = ring.tile(i, rev);
+        const int m = ring.staged(c);
+        if ((i & 7) == 7) acc.flush();
 #pragma unroll
-            for (int j = 0; j < V; j++) {
-                fr[j] = false;
-                xo[j] = T(0);
-                beta[j] = df_make(0.0f);
-                if (!ok[w][j]) continue;
-                const T a = va[w][j], b = vb[w][j], d = vd[w][j], l = vl[w][j], u = vu[w][j];
-                Cls cl;
-                if constexpr (sizeof(T) == 8) {
-                    if (check) acc.bad |= bad_elem(a, b, d, l, u);
-                    const bool inr = lam_ok && df_in_range(a, false) && df_in_range(b, false) &&
-                                     df_in_range(d, false) && df_in_range(l, true) && df_in_range(u, true);
-                    if (!inr) {
-                        widem |= 1u << j;
-                        continue;
-                    }
-                    const df xv = elem_df(a, b, d, l, u, Lm, acc, !write_x, cl, beta[j]);
-                    if (write_x) xo[j] = cl.c == 1 ? l : (cl.c == 2 ? u : df_to_f64(xv));
-                } else {
-                    if (check) acc.bad |= bad_elem(a, b, d, l, u);
-                    xo[j] = elem_f32(a, b, d, l, u, Lm, acc, !write_x, cl, beta[j]);
-                }
-                fr[j] = cl.c == 0;
-                tiem |= ((cl.tieL && !cl.tieU) ? 1u : 0u) << (2 * j);
-                tiem |= ((cl.tieU && !cl.tieL) ? 2u : 0u) << (2 * j);
-            }
-            // rare cases, one loop trip per element concerned (a data-dependent loop keeps FP64
-            // instructions off the common path): elements on a breakpoint (lateral-slope ties)
-            // and FP64 values outside the df operating range (exact FP64)
-            if (!write_x) {
-                for (unsigned m = tiem; m; m &= m - 1) {
-                    const int bit = __ffs(m) - 1;
-                    const double bj = df_to_f64(pick(beta, bit >> 1));
-                    if (bit & 1) acc.satu += bj;
-                    else acc.satl += bj;
-                }
-            }
-            if constexpr (sizeof(T) == 8) {
-                for (unsigned m = widem; m; m &= m - 1) {
-                    const int j = __ffs(m) - 1;
-                    Cls cl;
-                    const T xj = elem_f64_exact(pick(va[w], j), pick(vb[w], j), pick(vd[w], j), pick(vl[w], j),
-                                                pick(vu[w], j), lam, acc, !write_x, cl);
-                    put(xo, j, xj);
-                    put(fr, j, cl.c == 0);
-                }
-            }
-            if (write_x) {
-                // sums of the stored x: b'x, sum |b x|, number of free variables
-                unsigned wide2 = 0;
+        for (int k = 0; k < VPT; k++) {
+            const int ql = (int)threadIdx.x + k * NT;  // vector within the tile
+            const int64_t q = c * (TT / V) + ql;
+            const int64_t qw = q - (threadIdx.x & 31);
+            T va[V], vb[V], vd[V], vl[V], vu[V];
+            bool ok[V];
+            if ((ql + 1) * V <= m) {
+                const VT wa = reinterpret_cast<const VT*>(ring.stage(st, 0))[ql];
+                const VT wb = reinterpret_cast<const VT*>(ring.stage(st, 1))[ql];
+                const VT wd = reinterpret_cast<const VT*>(ring.stage(st, 2))[ql];
+                const VT wl = reinterpret_cast<const VT*>(ring.stage(st, 3))[ql];
+                const VT wu = reinterpret_cast<const VT*>(ring.stage(st, 4))[ql];
 #pragma unroll
                 for (int j = 0; j < V; j++) {
-                    if (!ok[w][j]) continue;
-                    const T b = vb[w][j];
-                    if constexpr (sizeof(T) == 8) {
-                        const bool inr = df_in_range(b, false) && df_in_range(xo[j], false);
-                        const df p = inr ? df_mul(split_f64(b), split_f64(xo[j])) : df_make(0.0f);
-                        acc.phi = df_add(acc.phi, p);
-                        acc.absbx = df_add(acc.absbx, p.hi < 0.0f ? df_neg(p) : p);
-                        wide2 |= (inr ? 0u : 1u) << j;
-                    } else {
-                        const df p = two_prod((float)b, (float)xo[j]);
-                        acc.phi = df_add(acc.phi, p);
-                        acc.absbx = df_add(acc.absbx, p.hi < 0.0f ? df_neg(p) : p);
-                    }
-                    acc.nfree += fr[j];
+                    va[j] = reinterpret_cast<const T*>(&wa)[j];
+                    vb[j] = reinterpret_cast<const T*>(&wb)[j];
+                    vd[j] = reinterpret_cast<const T*>(&wd)[j];
+                    vl[j] = reinterpret_cast<const T*>(&wl)[j];
+                    vu[j] = reinterpret_cast<const T*>(&wu)[j];
+                    ok[j] = true;
                 }
-                for (unsigned m = wide2; m; m &= m - 1) {
-                    const int j = __ffs(m) - 1;
-                    const double bx = (double)pick(vb[w], j) * (double)pick(xo, j);
-                    acc.phi64 += bx;
-                    acc.absbx64 += fabs(bx);
-                }
-                if (px) store_vec<T>(px, n, q, aligned, xo);
-                if (A.mask) store_mask<V>(A.mask, n, qw, fr);
+            } else {  // tail of the array beyond the last full 16 bytes
+                load_vec<T>(src[0], A.n, q, false, va, ok);
+                load_vec<T>(src[1], A.n, q, false, vb, ok);
+                load_vec<T>(src[2], A.n, q, false, vd, ok);
+                load_vec<T>(src[3], A.n, q, false, vl, ok);
+                load_vec<T>(src[4], A.n, q, false, vu, ok);
             }
+            eval_vec<T, FAST>(A, va, vb, vd, vl, vu, ok, q, qw, lam, Lm, lam_ok, write_x, check, acc);
         }
+        __syncthreads();  // the stage is refilled only after every thread has read it
     }
+    parity = ring.parity;
+    return okw;
+}
+
+// one pass over all elements, staged or plain
+template <typename T, bool FAST>
+__device__ __forceinline__ bool eval_pass(const GeneralArgs& A, double lam, bool write_x, bool check, bool rev,
+                                          EvalAcc& acc, T* smem, uint64_t* bars, unsigned& parity, int* err) {
+    if (A.staged) return eval_pass_staged<T, FAST>(A, lam, write_x, check, rev, acc, smem, bars, parity, err);
+    eval_pass_plain<T, FAST>(A, lam, write_x, check, rev, acc);
+    return true;
 }
 
 // closest breakpoint strictly right (dir > 0) / left (dir < 0) of lam, FP64 as defined
@@ -342,68 +485,139 @@ __device__ __forceinline__ double breakpoint_pass(const GeneralArgs& A, double l
     return best;
 }
 
+// eq. (CQKlambda0) terms of V elements: s += b a/d, q += b^2/d (df, FP64 outside the range)
 template <typename T>
-__device__ __forceinline__ void lambda0_pass(const GeneralArgs& A, double& s_out, double& q_out) {
+__device__ __forceinline__ void lambda0_vec(const T (&va)[VecOf<T>::V], const T (&vb)[VecOf<T>::V],
+                                            const T (&vd)[VecOf<T>::V], const bool (&ok)[VecOf<T>::V], LazyDf& s,
+                                            LazyDf& q, double& s64, double& q64) {
+    constexpr int V = VecOf<T>::V;
+    unsigned wide = 0;
+#pragma unroll
+    for (int j = 0; j < V; j++) {
+        if (!ok[j]) continue;
+        const T a = va[j], b = vb[j], d = vd[j];
+        if constexpr (sizeof(T) == 8) {
+            // b, d positive in [2^-60, 2^60], a zero or in that range (exponent-field tests)
+            const unsigned ha = (unsigned)__double2hiint(a), la = (unsigned)__double2loint(a);
+            const bool inr = (((unsigned)__double2hiint(b) >> 20) - 963u) <= 120u &&
+                             (((unsigned)__double2hiint(d) >> 20) - 963u) <= 120u &&
+                             ((((ha >> 20) & 0x7FFu) - 963u) <= 120u || ((ha & 0x7FFFFFFFu) | la) == 0u);
+            const df B = split_f64_finite(b), D = split_f64_finite(d);
+            const float r0 = rcp_approx(D.hi);
+            const float res = fmaf(-D.lo, r0, fmaf(-D.hi, r0, 1.0f));
+            const df invd = fast_two_sum(r0, __fmul_rn(r0, res));
+            const df wgt = df_mul(B, invd);
+            const df ps = df_mul_lazy(wgt, split_f64_finite(a)), pq = df_mul_lazy(wgt, B);
+            lazy_add(s, df{inr ? ps.hi : 0.0f, inr ? ps.lo : 0.0f});
+            lazy_add(q, df{inr ? pq.hi : 0.0f, inr ? pq.lo : 0.0f});
+            wide |= (inr ? 0u : 1u) << j;
+        } else {
+            const float rd = rcp_approx(d);
+            float wgt = __fmul_rn(b, rd);
+            wgt = fmaf(fmaf(-wgt, d, b), rd, wgt);
+            lazy_add(s, two_prod(wgt, a));
+            lazy_add(q, two_prod(wgt, b));
+        }
+    }
+    for (unsigned m = wide; m; m &= m - 1) {  // exact FP64 outside the df range (rare)
+        const int j = __ffs(m) - 1;
+        const double a = pick(va, j), b = pick(vb, j), d = pick(vd, j);
+        s64 += b * a / d;
+        q64 += b * b / d;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ bool lambda0_pass(const GeneralArgs& A, double& s_out, double& q_out, T* smem,
+                                             uint64_t* bars, unsigned& parity, int* err) {
     constexpr int V = VecOf<T>::V;
     const T* __restrict__ pa = static_cast<const T*>(A.a);
     const T* __restrict__ pb = static_cast<const T*>(A.b);
     const T* __restrict__ pd = static_cast<const T*>(A.d);
     const int64_t n = A.n;
-    const int64_t nv = (n + V - 1) / V;
-    const int lane = threadIdx.x & 31;
-    const bool aligned = A.aligned != 0;
-    df s = df_make(0.0f), q = df_make(0.0f);
+    LazyDf s{0.0f, 0.0f}, q{0.0f, 0.0f};
     double s64 = 0.0, q64 = 0.0;
-    int steps = 0;
-    constexpr int U = kGenU;
-    const WarpSweep sw(nv, U);
-    for (int64_t it = 0; it < sw.count; it++) {
-        if (++steps == kFlushEvery) {
-            s64 += df_to_f64(s);
-            q64 += df_to_f64(q);
-            s = q = df_make(0.0f);
-            steps = 0;
-        }
-        const int64_t base = sw.base(it, false);
-        T va[U][V], vb[U][V], vd[U][V];
-        bool ok[U][V];
-#pragma unroll
-        for (int w = 0; w < U; w++) {
-            load_vec<T>(pa, n, base + w * 32 + lane, aligned, va[w], ok[w]);
-            load_vec<T>(pb, n, base + w * 32 + lane, aligned, vb[w], ok[w]);
-            load_vec<T>(pd, n, base + w * 32 + lane, aligned, vd[w], ok[w]);
-        }
-        unsigned wide = 0;
-#pragma unroll
-        for (int wj = 0; wj < U * V; wj++) {
-            const int w = wj / V, j = wj % V;
-            if (!ok[w][j]) continue;
-            const T a = va[w][j], b = vb[w][j], d = vd[w][j];
-            if constexpr (sizeof(T) == 8) {
-                const bool inr = df_in_range(a, false) && df_in_range(b, false) && df_in_range(d, false) &&
-                                 f64_pos_finite(d);
-                const df B = split_f64(inr ? b : 1.0), D = split_f64(inr ? d : 1.0);
-                const df wgt = df_mul(B, df_div(df_make(1.0f), D, rcp_approx(D.hi)));
-                s = df_add(s, inr ? df_mul(wgt, split_f64(a)) : df_make(0.0f));
-                q = df_add(q, inr ? df_mul(wgt, B) : df_make(0.0f));
-                wide |= (inr ? 0u : 1u) << wj;
-            } else {
-                const float rd = rcp_approx(d);
-                float wgt = __fmul_rn(b, rd);
-                wgt = fmaf(fmaf(-wgt, d, b), rd, wgt);
-                s = df_add(s, two_prod(wgt, a));
-                q = df_add(q, two_prod(wgt, b));
+    bool okw = true;
+    if (A.staged) {
+        constexpr int TT = stage_tile<T>();
+        constexpr int VPT = TT / V / NT;
+        using VT = typename VecOf<T>::type;
+        const T* src[3] = {pa, pb, pd};
+        TileRing<T, 3, TT> ring;
+        ring.setup(n, smem, bars);
+        ring.parity = parity;
+        if (threadIdx.x == 0)
+            for (int st = 0; st < kStages - 1; st++)
+                if (st < ring.count) ring.issue(ring.tile(st, false), st, src);
+        for (int64_t i = 0; i < ring.count; i++) {
+            const int st = (int)(i % kStages);
+            if (threadIdx.x == 0 && i + kStages - 1 < ring.count)
+                ring.issue(ring.tile(i + kStages - 1, false), (int)((i + kStages - 1) % kStages), src);
+            if (!mbar_wait(&ring.bar[st], (ring.parity >> st) & 1u, err, A.limit_ns, CQK_TIMEOUT)) okw = false;
+            ring.parity ^= 1u << st;
+            const int64_t c = ring.tile(i, false);
+            const int m = ring.staged(c);
+            if ((i & 7) == 7) {
+                s64 += lazy_value(s);
+                q64 += lazy_value(q);
+                s = q = LazyDf{0.0f, 0.0f};
             }
+#pragma unroll
+            for (int k = 0; k < VPT; k++) {
+                const int ql = (int)threadIdx.x + k * NT;
+                const int64_t qg = c * (TT / V) + ql;
+                T va[V], vb[V], vd[V];
+                bool ok[V];
+                if ((ql + 1) * V <= m) {
+                    const VT wa = reinterpret_cast<const VT*>(ring.stage(st, 0))[ql];
+                    const VT wb = reinterpret_cast<const VT*>(ring.stage(st, 1))[ql];
+                    const VT wd = reinterpret_cast<const VT*>(ring.stage(st, 2))[ql];
+#pragma unroll
+                    for (int j = 0; j < V; j++) {
+                        va[j] = reinterpret_cast<const T*>(&wa)[j];
+                        vb[j] = reinterpret_cast<const T*>(&wb)[j];
+                        vd[j] = reinterpret_cast<const T*>(&wd)[j];
+                        ok[j] = true;
+                    }
+                } else {
+                    load_vec<T>(pa, n, qg, false, va, ok);
+                    load_vec<T>(pb, n, qg, false, vb, ok);
+                    load_vec<T>(pd, n, qg, false, vd, ok);
+                }
+                lambda0_vec<T>(va, vb, vd, ok, s, q, s64, q64);
+            }
+            __syncthreads();
         }
-        for (unsigned m = wide; m; m &= m - 1) {  // exact FP64 outside the df range (rare)
-            const int wj = __ffs(m) - 1;
-            const double a = pick(va[wj / V], wj % V), b = pick(vb[wj / V], wj % V), d = pick(vd[wj / V], wj % V);
-            s64 += b * a / d;
-            q64 += b * b / d;
+        parity = ring.parity;
+    } else {
+        const int64_t nv = (n + V - 1) / V;
+        const int lane = threadIdx.x & 31;
+        constexpr int U = kGenU;
+        const WarpSweep sw(nv, U);
+        int steps = 0;
+        for (int64_t it = 0; it < sw.count; it++) {
+            if (++steps == kFlushEvery) {
+                s64 += lazy_value(s);
+                q64 += lazy_value(q);
+                s = q = LazyDf{0.0f, 0.0f};
+                steps = 0;
+            }
+            const int64_t base = sw.base(it, false);
+            T va[U][V], vb[U][V], vd[U][V];
+            bool ok[U][V];
+#pragma unroll
+            for (int w = 0; w < U; w++) {
+                load_vec<T>(pa, n, base + w * 32 + lane, false, va[w], ok[w]);
+                load_vec<T>(pb, n, base + w * 32 + lane, false, vb[w], ok[w]);
+                load_vec<T>(pd, n, base + w * 32 + lane, false, vd[w], ok[w]);
+            }
+#pragma unroll
+            for (int w = 0; w < U; w++) lambda0_vec<T>(va[w], vb[w], vd[w], ok[w], s, q, s64, q64);
         }
     }
-    s_out = df_to_f64(s) + s64;
-    q_out = df_to_f64(q) + q64;
+    s_out = lazy_value(s) + s64;
+    q_out = lazy_value(q) + q64;
+    return okw;
 }
 
 #define CQK_BARRIER_OR_LEAVE()                                                  \
@@ -419,6 +633,17 @@ template <typename T>
 __global__ void __launch_bounds__(NT, 2) general_kernel(GeneralArgs A) {
     __shared__ double sh[kPartialQ][NWARP];
     __shared__ double bc[kPartialQ];
+    extern __shared__ __align__(128) unsigned char dyn_smem[];
+    __shared__ uint64_t ring_bars[kStages];
+    T* const smem = reinterpret_cast<T*>(dyn_smem);
+    unsigned ring_parity = 0;
+    if (A.staged) {
+        if (threadIdx.x == 0) {
+            for (int st = 0; st < kStages; st++) mbar_init(&ring_bars[st], 1);
+            fence_barrier_init();
+        }
+        __syncthreads();
+    }
     const int G = gridDim.x;
     unsigned bar_target = (unsigned)G + (A.fault_inject ? 1u : 0u);
     unsigned* bar = &A.hdr->bar_count;
@@ -429,7 +654,7 @@ __global__ void __launch_bounds__(NT, 2) general_kernel(GeneralArgs A) {
     if (A.phi_only) {  // cqk_phi: one evaluation at A.lambda0 (and x when requested)
         EvalAcc acc;
         acc.init();
-        eval_pass<T>(A, A.lambda0, false, false, false, acc);
+        eval_pass<T, false>(A, A.lambda0, false, false, false, acc, smem, ring_bars, ring_parity, err);
         acc.flush();
         double pv[3] = {acc.phi64, acc.sfree64, acc.absbx64};
         double pt[2] = {acc.satl, acc.satu};
@@ -442,7 +667,7 @@ __global__ void __launch_bounds__(NT, 2) general_kernel(GeneralArgs A) {
         if (A.x) {
             EvalAcc acc2;
             acc2.init();
-            eval_pass<T>(A, A.lambda0, true, false, true, acc2);
+            eval_pass<T, false>(A, A.lambda0, true, false, true, acc2, smem, ring_bars, ring_parity, err);
         }
         double dummy[1] = {0.0}, tot[1];
         if (last_block_sums<1>(A.part, &A.hdr->ticket, dummy, tot, sh)) {
@@ -462,7 +687,7 @@ __global__ void __launch_bounds__(NT, 2) general_kernel(GeneralArgs A) {
     double lam0 = A.lambda0;
     if (A.init == CQK_INIT_FORMULA) {
         double s, q;
-        lambda0_pass<T>(A, s, q);
+        lambda0_pass<T>(A, s, q, smem, ring_bars, ring_parity, err);
         double pv[2] = {s, q};
         block_sum<2>(pv, sh);
         write_partials<2>(A.part, par, pv);
@@ -479,6 +704,7 @@ __global__ void __launch_bounds__(NT, 2) general_kernel(GeneralArgs A) {
     double final_lam = lam;
     int status = CQK_OK, stop = CQK_STOP_NONE, k = 0;
     bool bad_input = false;
+    bool wide_data = true;  // until the first pass has checked every value
     for (k = 0;; k++) {
         if (k >= A.max_iter) {
             status = CQK_MAXITER;
@@ -486,10 +712,12 @@ __global__ void __launch_bounds__(NT, 2) general_kernel(GeneralArgs A) {
         }
         EvalAcc acc;
         acc.init();
-        eval_pass<T>(A, lam, false, k == 0 && A.validate, (k & 1) == 1, acc);
+        if (k > 0 && !wide_data) eval_pass<T, true>(A, lam, false, false, (k & 1) == 1, acc, smem, ring_bars, ring_parity, err);
+        else eval_pass<T, false>(A, lam, false, k == 0 && A.validate, (k & 1) == 1, acc, smem, ring_bars, ring_parity, err);
         acc.flush();
         passes++;
         if (__any_sync(0xffffffffu, acc.bad) && (threadIdx.x & 31) == 0) atomicOr(&A.hdr->flags, kFlagBadInput);
+        if (k == 0 && __any_sync(0xffffffffu, acc.wide) && (threadIdx.x & 31) == 0) atomicOr(&A.hdr->flags, kFlagWide);
         double pv[5] = {acc.phi64, acc.sfree64, acc.satl, acc.satu, acc.absbx64};
         block_sum<5>(pv, sh);
         write_partials<5>(A.part, par, pv);
@@ -497,6 +725,7 @@ __global__ void __launch_bounds__(NT, 2) general_kernel(GeneralArgs A) {
         double red[5];
         grid_reduce<5>(A.part, par, -1, red, sh, bc);
         par ^= 1;
+        if (k == 0) wide_data = (__ldcg(&A.hdr->flags) & kFlagWide) != 0;
         if (k == 0 && A.validate && (__ldcg(&A.hdr->flags) & kFlagBadInput)) {
             bad_input = true;
             status = CQK_BAD_INPUT;
@@ -615,7 +844,8 @@ __global__ void __launch_bounds__(NT, 2) general_kernel(GeneralArgs A) {
     EvalAcc acc;
     acc.init();
     if (!bad_input && status != CQK_INFEASIBLE) {
-        eval_pass<T>(A, final_lam, true, false, (k & 1) == 1, acc);
+        if (!wide_data) eval_pass<T, true>(A, final_lam, true, false, (k & 1) == 1, acc, smem, ring_bars, ring_parity, err);
+        else eval_pass<T, false>(A, final_lam, true, false, (k & 1) == 1, acc, smem, ring_bars, ring_parity, err);
         passes++;
     }
     acc.flush();
@@ -659,10 +889,21 @@ GeneralArgs make_args(int64_t n, const void* a, const void* b, const void* d, co
     return A;
 }
 
+constexpr size_t kStagedSmem = (size_t)kStages * 5 * 8192;  // bytes of dynamic shared memory
+
 int launch(GeneralArgs A, int dtype, int max_blocks, cudaStream_t s, void* ws) {
     const void* kern = dtype == CQK_F64 ? (const void*)general_kernel<double> : (const void*)general_kernel<float>;
     const int64_t vec = dtype == CQK_F64 ? 2 : 4;
-    const int grid = persistent_grid(kern, NT, 0, (A.n + vec - 1) / vec, max_blocks);
+    A.staged = A.aligned;
+    const size_t smem = A.staged ? kStagedSmem : 0;
+    if (smem) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) {
+            set_last_cuda_error(e);
+            return CQK_CUDA_ERROR;
+        }
+    }
+    const int grid = persistent_grid(kern, NT, smem, (A.n + vec - 1) / vec, max_blocks);
     if (grid <= 0) return CQK_CUDA_ERROR;
     cudaError_t e = cudaMemsetAsync(ws, 0, sizeof(WsHeader), s);
     if (e != cudaSuccess) {
@@ -670,7 +911,7 @@ int launch(GeneralArgs A, int dtype, int max_blocks, cudaStream_t s, void* ws) {
         return CQK_CUDA_ERROR;
     }
     void* args[] = {&A};
-    e = cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(NT), args, 0, s);
+    e = cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(NT), args, smem, s);
     if (e != cudaSuccess) {
         set_last_cuda_error(e);
         return CQK_CUDA_ERROR;
