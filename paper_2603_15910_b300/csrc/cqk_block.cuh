@@ -1,5 +1,11 @@
-// cqk_block.cuh -- streaming loads and deterministic block / grid reductions shared by the
-// persistent kernels of libcqk.
+// cqk_block.cuh -- streaming loads and deterministic reductions shared by the persistent
+// kernels of libcqk.
+//
+// Work is done by a "group" of co-resident blocks on one element range [lo, hi) of arrays
+// that are 16-byte aligned at element 0 (a single solve: one group of all blocks on [0, n);
+// a batch: one group per instance on that instance's range of the concatenated arrays).
+// Vectors are indexed globally: vector q holds elements q*V ... q*V+V-1, so every 128-bit
+// access stays aligned whatever lo is; elements outside [lo, hi) are masked off.
 #pragma once
 
 #include "cqk_device.cuh"
@@ -23,14 +29,33 @@ struct VecOf<float> {
 constexpr int NT = kBlockThreads;
 constexpr int NWARP = NT / 32;
 
-// Load the V elements of vector q (elements q*V ... q*V+V-1); out-of-range elements get
-// ok = false.  One 128-bit load when the arrays are 16-byte aligned and the vector is full.
+struct Span {
+    int64_t lo, hi;
+};
+
+// the vectors [qlo, qhi) that meet the span
+template <int V>
+__device__ __forceinline__ int64_t span_qlo(const Span& s) { return s.lo / V; }
+template <int V>
+__device__ __forceinline__ int64_t span_qhi(const Span& s) { return (s.hi + V - 1) / V; }
+
+// One group of blocks working on one span: block `member` of `g`, its barrier / ticket /
+// flags header and its per-block partial sums [2][kPartialQ][g].
+struct Grp {
+    int member, g;
+    Span sp;
+    WsHeader* hdr;
+    double* part;
+};
+
+// Load the V elements of vector q; elements outside the span get ok = false.  One 128-bit
+// load when the arrays are 16-byte aligned and the vector lies inside the span.
 template <typename T>
-__device__ __forceinline__ void load_vec(const T* __restrict__ p, int64_t n, int64_t q, bool aligned,
+__device__ __forceinline__ void load_vec(const T* __restrict__ p, const Span& sp, int64_t q, bool aligned,
                                          T (&v)[VecOf<T>::V], bool (&ok)[VecOf<T>::V]) {
     constexpr int V = VecOf<T>::V;
     const int64_t e0 = q * V;
-    if (aligned && e0 + V <= n) {
+    if (aligned && e0 >= sp.lo && e0 + V <= sp.hi) {
         using VT = typename VecOf<T>::type;
         VT w = __ldg(reinterpret_cast<const VT*>(p) + q);
         const T* s = reinterpret_cast<const T*>(&w);
@@ -42,19 +67,24 @@ __device__ __forceinline__ void load_vec(const T* __restrict__ p, int64_t n, int
     } else {
 #pragma unroll
         for (int j = 0; j < V; j++) {
-            ok[j] = e0 + j < n;
+            ok[j] = e0 + j >= sp.lo && e0 + j < sp.hi;
             v[j] = ok[j] ? __ldg(p + e0 + j) : T(0);
         }
     }
 }
-
-// Store the V elements of vector q (full vector: one 128-bit store when aligned).
 template <typename T>
-__device__ __forceinline__ void store_vec(T* __restrict__ p, int64_t n, int64_t q, bool aligned,
+__device__ __forceinline__ void load_vec(const T* __restrict__ p, int64_t n, int64_t q, bool aligned,
+                                         T (&v)[VecOf<T>::V], bool (&ok)[VecOf<T>::V]) {
+    load_vec<T>(p, Span{0, n}, q, aligned, v, ok);
+}
+
+// Store the elements of vector q that lie inside the span.
+template <typename T>
+__device__ __forceinline__ void store_vec(T* __restrict__ p, const Span& sp, int64_t q, bool aligned,
                                           const T (&v)[VecOf<T>::V]) {
     constexpr int V = VecOf<T>::V;
     const int64_t e0 = q * V;
-    if (aligned && e0 + V <= n) {
+    if (aligned && e0 >= sp.lo && e0 + V <= sp.hi) {
         using VT = typename VecOf<T>::type;
         VT w;
         T* s = reinterpret_cast<T*>(&w);
@@ -64,14 +94,16 @@ __device__ __forceinline__ void store_vec(T* __restrict__ p, int64_t n, int64_t 
     } else {
 #pragma unroll
         for (int j = 0; j < V; j++)
-            if (e0 + j < n) p[e0 + j] = v[j];
+            if (e0 + j >= sp.lo && e0 + j < sp.hi) p[e0 + j] = v[j];
     }
 }
 
-// Free-mask word of a warp's 32 consecutive vectors (starting at vector qw, a multiple of
-// 32): bit e % 32 of word e / 32 is set iff sel[j] of element e.  Called by all lanes.
+// Free-mask words of a warp's 32 consecutive vectors (starting at vector qw, a multiple of
+// 32): bit e % 32 of word e / 32 is set iff sel of element e.  Words that lie entirely inside
+// the span are stored; a word shared with a neighbouring span is updated atomically on this
+// span's bits only.  Called by all lanes.
 template <int V>
-__device__ __forceinline__ void store_mask(uint32_t* mask, int64_t n, int64_t qw, const bool (&sel)[V]) {
+__device__ __forceinline__ void store_mask(uint32_t* mask, const Span& sp, int64_t qw, const bool (&sel)[V]) {
     const int lane = threadIdx.x & 31;
     unsigned bitsv = 0;
 #pragma unroll
@@ -81,24 +113,33 @@ __device__ __forceinline__ void store_mask(uint32_t* mask, int64_t n, int64_t qw
     for (int o = 1; o < LPW; o <<= 1) bitsv |= __shfl_xor_sync(0xffffffffu, bitsv, o);
     if ((lane % LPW) == 0) {
         const int64_t word = (qw * V) / 32 + lane / LPW;
-        if (word * 32 < n) mask[word] = bitsv;
+        const int64_t w0 = word * 32;
+        if (w0 >= sp.hi || w0 + 32 <= sp.lo) return;
+        if (w0 >= sp.lo && w0 + 32 <= sp.hi) {
+            mask[word] = bitsv;
+        } else {
+            const int64_t a = sp.lo > w0 ? sp.lo - w0 : 0, b = sp.hi < w0 + 32 ? sp.hi - w0 : 32;
+            const unsigned in = (b >= 32 ? 0xFFFFFFFFu : ((1u << b) - 1u)) & ~((1u << a) - 1u);
+            atomicAnd(&mask[word], ~in | bitsv);
+            atomicOr(&mask[word], bitsv & in);
+        }
     }
 }
 
-// Warp-contiguous traversal of nv vectors: iteration i of warp w (of W) covers the vectors
-// [base, base + 32*U) with base = (w + i*W)*32*U, lane L taking base + k*32 + L (k < U), so
-// every load instruction of a warp reads 512 contiguous bytes and each lane has U
-// independent 16-byte loads in flight.  rev = true visits the same iterations in reverse
-// order: a pass that follows a forward pass then starts on the data that the forward pass
-// read last, which is still in L2.
+// Warp-contiguous traversal of the vectors [qlo, qhi) by the warps of a group: iteration i of
+// warp w (of W = g * NWARP) covers the vectors [base, base + 32*U) with
+// base = floor(qlo/32)*32 + (w + i*W)*32*U, lane L taking base + k*32 + L (k < U), so every
+// load instruction of a warp reads 512 contiguous bytes and each lane has U independent
+// 16-byte loads in flight.  rev = true visits the same iterations in reverse order: a pass
+// that follows a forward pass then starts on the data that the forward pass read last,
+// which is still in L2.
 struct WarpSweep {
     int64_t first, step, count;
-    __device__ __forceinline__ WarpSweep(int64_t nv, int U) {
-        const int64_t gwarp = (int64_t)blockIdx.x * NWARP + (threadIdx.x >> 5);
-        const int64_t nwarps = (int64_t)gridDim.x * NWARP;
-        first = gwarp * 32 * U;
-        step = nwarps * 32 * U;
-        count = first < nv ? (nv - first + step - 1) / step : 0;
+    __device__ __forceinline__ WarpSweep(int64_t qlo, int64_t qhi, int U, int member, int g) {
+        const int64_t w = (int64_t)member * NWARP + (threadIdx.x >> 5);
+        first = (qlo / 32) * 32 + w * 32 * U;
+        step = (int64_t)g * NWARP * 32 * U;
+        count = first < qhi ? (qhi - first + step - 1) / step : 0;
     }
     __device__ __forceinline__ int64_t base(int64_t i, bool rev) const { return first + (rev ? count - 1 - i : i) * step; }
 };
@@ -149,19 +190,19 @@ __device__ __forceinline__ void block_sum(double (&v)[NQ], double (*sh)[NWARP]) 
     __syncthreads();
 }
 
-// Reduce the partials of all blocks for pass parity `par` (sums, and a max for q == qmax);
-// every block computes the same values in the same order.  Result in out[] (all threads).
+// Reduce the partials of the group's g blocks for pass parity `par` (sums, and a max for
+// q == qmax); every block computes the same values in the same order.  Result in out[] (all
+// threads).
 template <int NQ>
-__device__ __forceinline__ void grid_reduce(const double* part, int par, int qmax, double (&out)[NQ],
+__device__ __forceinline__ void grid_reduce(const double* part, int g, int par, int qmax, double (&out)[NQ],
                                             double (*sh)[NWARP], double* bc) {
-    const int G = gridDim.x;
     double v[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; q++) v[q] = (q == qmax) ? -INFINITY : 0.0;
-    for (int bIdx = threadIdx.x; bIdx < G; bIdx += NT) {
+    for (int bIdx = threadIdx.x; bIdx < g; bIdx += NT) {
 #pragma unroll
         for (int q = 0; q < NQ; q++) {
-            double t = ld_cg(part + ((size_t)par * kPartialQ + q) * G + bIdx);
+            double t = ld_cg(part + ((size_t)par * kPartialQ + q) * g + bIdx);
             v[q] = (q == qmax) ? fmax(v[q], t) : v[q] + t;
         }
     }
@@ -188,28 +229,26 @@ __device__ __forceinline__ void grid_reduce(const double* part, int par, int qma
 }
 
 template <int NQ>
-__device__ __forceinline__ void write_partials(double* part, int par, const double (&v)[NQ]) {
+__device__ __forceinline__ void write_partials(double* part, int member, int g, int par, const double (&v)[NQ]) {
     if (threadIdx.x == 0) {
-        const int G = gridDim.x;
 #pragma unroll
-        for (int q = 0; q < NQ; q++) part[((size_t)par * kPartialQ + q) * G + blockIdx.x] = v[q];
+        for (int q = 0; q < NQ; q++) part[((size_t)par * kPartialQ + q) * g + member] = v[q];
     }
 }
 
 // Last-block-done reduction of NQ <= 3 sums stored in slots 5..5+NQ of parity 0; returns
-// true in the last block, whose out[] then holds the grid sums (all threads).
+// true in the group's last block, whose out[] then holds the group sums (thread 0).
 template <int NQ>
-__device__ __forceinline__ bool last_block_sums(double* part, unsigned* ticket, double (&v)[NQ], double (&out)[NQ],
-                                                double (*sh)[NWARP]) {
+__device__ __forceinline__ bool last_block_sums(double* part, int member, int g, unsigned* ticket, double (&v)[NQ],
+                                                double (&out)[NQ], double (*sh)[NWARP]) {
     __shared__ unsigned s_last;
-    const int G = gridDim.x;
     block_sum<NQ>(v, sh);
     if (threadIdx.x == 0) {
 #pragma unroll
-        for (int q = 0; q < NQ; q++) part[(size_t)(5 + q) * G + blockIdx.x] = v[q];
+        for (int q = 0; q < NQ; q++) part[(size_t)(5 + q) * g + member] = v[q];
         __threadfence();
         unsigned t = atomicAdd(ticket, 1u);
-        s_last = (t == (unsigned)G - 1) ? 1u : 0u;
+        s_last = (t == (unsigned)g - 1) ? 1u : 0u;
     }
     __syncthreads();
     if (!s_last) return false;
@@ -217,9 +256,9 @@ __device__ __forceinline__ bool last_block_sums(double* part, unsigned* ticket, 
     double w[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; q++) w[q] = 0.0;
-    for (int b = threadIdx.x; b < G; b += NT)
+    for (int b = threadIdx.x; b < g; b += NT)
 #pragma unroll
-        for (int q = 0; q < NQ; q++) w[q] += ld_cg(part + (size_t)(5 + q) * G + b);
+        for (int q = 0; q < NQ; q++) w[q] += ld_cg(part + (size_t)(5 + q) * g + b);
     block_sum<NQ>(w, sh);
 #pragma unroll
     for (int q = 0; q < NQ; q++) out[q] = w[q];

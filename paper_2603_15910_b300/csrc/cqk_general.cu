@@ -211,9 +211,8 @@ __device__ __forceinline__ void eval_vec(const GeneralArgs& A, const T (&va)[Vec
                                          const T (&vd)[VecOf<T>::V], const T (&vl)[VecOf<T>::V],
                                          const T (&vu)[VecOf<T>::V], const bool (&ok)[VecOf<T>::V], int64_t q,
                                          int64_t qw, double lam, df Lm, bool lam_ok, bool write_x, bool check,
-                                         EvalAcc& acc) {
+                                         EvalAcc& acc, const Span& sp) {
     constexpr int V = VecOf<T>::V;
-    const int64_t n = A.n;
     const bool aligned = A.aligned != 0;
     T* __restrict__ px = static_cast<T*>(A.x);
         T xo[V];
@@ -335,15 +334,15 @@ __device__ __forceinline__ void eval_vec(const GeneralArgs& A, const T (&va)[Vec
             }
 #pragma unroll
             for (int j = 0; j < V; j++) acc.nfree += (ok[j] && fr[j]) ? 1 : 0;
-            if (px) store_vec<T>(px, n, q, aligned, xo);
-            if (A.mask) store_mask<V>(A.mask, n, qw, fr);
+            if (px) store_vec<T>(px, sp, q, aligned, xo);
+            if (A.mask) store_mask<V>(A.mask, sp, qw, fr);
         }
 }
 
 // ---- one pass over all elements with plain loads (arrays not 16-byte aligned)
 template <typename T, bool FAST>
-__device__ __forceinline__ void eval_pass_plain(const GeneralArgs& A, double lam, bool write_x, bool check, bool rev,
-                                                EvalAcc& acc) {
+__device__ __forceinline__ void eval_pass_plain(const GeneralArgs& A, const Grp& gp, double lam, bool write_x,
+                                                bool check, bool rev, EvalAcc& acc) {
     constexpr int V = VecOf<T>::V;
     constexpr int U = kGenU;
     const T* __restrict__ pa = static_cast<const T*>(A.a);
@@ -351,13 +350,12 @@ __device__ __forceinline__ void eval_pass_plain(const GeneralArgs& A, double lam
     const T* __restrict__ pd = static_cast<const T*>(A.d);
     const T* __restrict__ pl = static_cast<const T*>(A.l);
     const T* __restrict__ pu = static_cast<const T*>(A.u);
-    const int64_t n = A.n;
-    const int64_t nv = (n + V - 1) / V;
+    const Span sp = gp.sp;
     const int lane = threadIdx.x & 31;
     const bool aligned = A.aligned != 0;
     const df Lm = df_from_f64(lam);
     const bool lam_ok = fabs(lam) <= 1.152921504606847e18;  // 2^60
-    const WarpSweep sw(nv, U);
+    const WarpSweep sw(span_qlo<V>(sp), span_qhi<V>(sp), U, gp.member, gp.g);
     int steps = 0;
     for (int64_t it = 0; it < sw.count; it++) {
         if (++steps == kFlushEvery) {
@@ -370,16 +368,16 @@ __device__ __forceinline__ void eval_pass_plain(const GeneralArgs& A, double lam
 #pragma unroll
         for (int w = 0; w < U; w++) {
             const int64_t q = base + w * 32 + lane;
-            load_vec<T>(pa, n, q, aligned, va[w], ok[w]);
-            load_vec<T>(pb, n, q, aligned, vb[w], ok[w]);
-            load_vec<T>(pd, n, q, aligned, vd[w], ok[w]);
-            load_vec<T>(pl, n, q, aligned, vl[w], ok[w]);
-            load_vec<T>(pu, n, q, aligned, vu[w], ok[w]);
+            load_vec<T>(pa, sp, q, aligned, va[w], ok[w]);
+            load_vec<T>(pb, sp, q, aligned, vb[w], ok[w]);
+            load_vec<T>(pd, sp, q, aligned, vd[w], ok[w]);
+            load_vec<T>(pl, sp, q, aligned, vl[w], ok[w]);
+            load_vec<T>(pu, sp, q, aligned, vu[w], ok[w]);
         }
 #pragma unroll
         for (int w = 0; w < U; w++)
             eval_vec<T, FAST>(A, va[w], vb[w], vd[w], vl[w], vu[w], ok[w], base + w * 32 + lane, base + w * 32, lam, Lm,
-                              lam_ok, write_x, check, acc);
+                              lam_ok, write_x, check, acc, sp);
     }
 }
 
@@ -388,9 +386,9 @@ template <typename T>
 __host__ __device__ constexpr int stage_tile() { return 8192 / (int)sizeof(T); }  // elements per array per stage
 
 template <typename T, bool FAST>
-__device__ __forceinline__ bool eval_pass_staged(const GeneralArgs& A, double lam, bool write_x, bool check, bool rev,
-                                                 EvalAcc& acc, T* smem, uint64_t* bars, unsigned& parity,
-                                                 int* err) {
+__device__ __forceinline__ bool eval_pass_staged(const GeneralArgs& A, const Grp& gp, double lam, bool write_x,
+                                                 bool check, bool rev, EvalAcc& acc, T* smem, uint64_t* bars,
+                                                 unsigned& parity, int* err) {
     constexpr int V = VecOf<T>::V;
     constexpr int TT = stage_tile<T>();
     constexpr int VPT = TT / V / NT;  // vectors per thread per tile
@@ -398,7 +396,8 @@ __device__ __forceinline__ bool eval_pass_staged(const GeneralArgs& A, double la
     const T* src[5] = {static_cast<const T*>(A.a), static_cast<const T*>(A.b), static_cast<const T*>(A.d),
                        static_cast<const T*>(A.l), static_cast<const T*>(A.u)};
     TileRing<T, 5, TT> ring;
-    ring.setup(A.n, smem, bars);
+    const Span sp = gp.sp;
+    ring.setup(sp.lo, sp.hi, smem, bars, gp.member, gp.g);
     ring.parity = parity;
     const df Lm = df_from_f64(lam);
     const bool lam_ok = fabs(lam) <= 1.152921504606847e18;  // 2^60
@@ -413,7 +412,7 @@ __device__ __forceinline__ bool eval_pass_staged(const GeneralArgs& A, double la
         if (!mbar_wait(&ring.bar[st], (ring.parity >> st) & 1u, err, A.limit_ns, CQK_TIMEOUT)) okw = false;
         ring.parity ^= 1u << st;
         const int64_t c = ring.tile(i, rev);
-        const int m = ring.staged(c);
+        const int64_t sb0 = ring.b0(c), sb1 = ring.b1(c);
         if ((i & 7) == 7) acc.flush();
 #pragma unroll
         for (int k = 0; k < VPT; k++) {
@@ -422,7 +421,7 @@ __device__ __forceinline__ bool eval_pass_staged(const GeneralArgs& A, double la
             const int64_t qw = q - (threadIdx.x & 31);
             T va[V], vb[V], vd[V], vl[V], vu[V];
             bool ok[V];
-            if ((ql + 1) * V <= m) {
+            if (q * V >= sb0 && (q + 1) * V <= sb1) {
                 const VT wa = reinterpret_cast<const VT*>(ring.stage(st, 0))[ql];
                 const VT wb = reinterpret_cast<const VT*>(ring.stage(st, 1))[ql];
                 const VT wd = reinterpret_cast<const VT*>(ring.stage(st, 2))[ql];
@@ -438,13 +437,13 @@ __device__ __forceinline__ bool eval_pass_staged(const GeneralArgs& A, double la
                     ok[j] = true;
                 }
             } else {  // tail of the array beyond the last full 16 bytes
-                load_vec<T>(src[0], A.n, q, false, va, ok);
-                load_vec<T>(src[1], A.n, q, false, vb, ok);
-                load_vec<T>(src[2], A.n, q, false, vd, ok);
-                load_vec<T>(src[3], A.n, q, false, vl, ok);
-                load_vec<T>(src[4], A.n, q, false, vu, ok);
+                load_vec<T>(src[0], sp, q, false, va, ok);
+                load_vec<T>(src[1], sp, q, false, vb, ok);
+                load_vec<T>(src[2], sp, q, false, vd, ok);
+                load_vec<T>(src[3], sp, q, false, vl, ok);
+                load_vec<T>(src[4], sp, q, false, vu, ok);
             }
-            eval_vec<T, FAST>(A, va, vb, vd, vl, vu, ok, q, qw, lam, Lm, lam_ok, write_x, check, acc);
+            eval_vec<T, FAST>(A, va, vb, vd, vl, vu, ok, q, qw, lam, Lm, lam_ok, write_x, check, acc, sp);
         }
         __syncthreads();  // the stage is refilled only after every thread has read it
     }
@@ -454,24 +453,25 @@ __device__ __forceinline__ bool eval_pass_staged(const GeneralArgs& A, double la
 
 // one pass over all elements, staged or plain
 template <typename T, bool FAST>
-__device__ __forceinline__ bool eval_pass(const GeneralArgs& A, double lam, bool write_x, bool check, bool rev,
-                                          EvalAcc& acc, T* smem, uint64_t* bars, unsigned& parity, int* err) {
-    if (A.staged) return eval_pass_staged<T, FAST>(A, lam, write_x, check, rev, acc, smem, bars, parity, err);
-    eval_pass_plain<T, FAST>(A, lam, write_x, check, rev, acc);
+__device__ __forceinline__ bool eval_pass(const GeneralArgs& A, const Grp& gp, double lam, bool write_x, bool check,
+                                          bool rev, EvalAcc& acc, T* smem, uint64_t* bars, unsigned& parity,
+                                          int* err) {
+    if (A.staged) return eval_pass_staged<T, FAST>(A, gp, lam, write_x, check, rev, acc, smem, bars, parity, err);
+    eval_pass_plain<T, FAST>(A, gp, lam, write_x, check, rev, acc);
     return true;
 }
 
 // closest breakpoint strictly right (dir > 0) / left (dir < 0) of lam, FP64 as defined
 template <typename T>
-__device__ __forceinline__ double breakpoint_pass(const GeneralArgs& A, double lam, int dir) {
+__device__ __forceinline__ double breakpoint_pass(const GeneralArgs& A, const Grp& gp, double lam, int dir) {
     const T* pa = static_cast<const T*>(A.a);
     const T* pb = static_cast<const T*>(A.b);
     const T* pd = static_cast<const T*>(A.d);
     const T* pl = static_cast<const T*>(A.l);
     const T* pu = static_cast<const T*>(A.u);
     double best = dir > 0 ? INFINITY : -INFINITY;
-    const int64_t stride = (int64_t)gridDim.x * NT;
-    for (int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x; i < A.n; i += stride) {
+    const int64_t stride = (int64_t)gp.g * NT;
+    for (int64_t i = gp.sp.lo + (int64_t)gp.member * NT + threadIdx.x; i < gp.sp.hi; i += stride) {
         const double a = pa[i], b = pb[i], d = pd[i], l = pl[i], u = pu[i];
         const double c0 = (d * l - a) / b, c1 = (d * u - a) / b;
         if (dir > 0) {
@@ -528,13 +528,13 @@ __device__ __forceinline__ void lambda0_vec(const T (&va)[VecOf<T>::V], const T 
 }
 
 template <typename T>
-__device__ __forceinline__ bool lambda0_pass(const GeneralArgs& A, double& s_out, double& q_out, T* smem,
-                                             uint64_t* bars, unsigned& parity, int* err) {
+__device__ __forceinline__ bool lambda0_pass(const GeneralArgs& A, const Grp& gp, double& s_out, double& q_out,
+                                             T* smem, uint64_t* bars, unsigned& parity, int* err) {
     constexpr int V = VecOf<T>::V;
     const T* __restrict__ pa = static_cast<const T*>(A.a);
     const T* __restrict__ pb = static_cast<const T*>(A.b);
     const T* __restrict__ pd = static_cast<const T*>(A.d);
-    const int64_t n = A.n;
+    const Span sp = gp.sp;
     LazyDf s{0.0f, 0.0f}, q{0.0f, 0.0f};
     double s64 = 0.0, q64 = 0.0;
     bool okw = true;
@@ -544,7 +544,7 @@ __device__ __forceinline__ bool lambda0_pass(const GeneralArgs& A, double& s_out
         using VT = typename VecOf<T>::type;
         const T* src[3] = {pa, pb, pd};
         TileRing<T, 3, TT> ring;
-        ring.setup(n, smem, bars);
+        ring.setup(sp.lo, sp.hi, smem, bars, gp.member, gp.g);
         ring.parity = parity;
         if (threadIdx.x == 0)
             for (int st = 0; st < kStages - 1; st++)
@@ -556,7 +556,7 @@ __device__ __forceinline__ bool lambda0_pass(const GeneralArgs& A, double& s_out
             if (!mbar_wait(&ring.bar[st], (ring.parity >> st) & 1u, err, A.limit_ns, CQK_TIMEOUT)) okw = false;
             ring.parity ^= 1u << st;
             const int64_t c = ring.tile(i, false);
-            const int m = ring.staged(c);
+            const int64_t sb0 = ring.b0(c), sb1 = ring.b1(c);
             if ((i & 7) == 7) {
                 s64 += lazy_value(s);
                 q64 += lazy_value(q);
@@ -568,7 +568,7 @@ __device__ __forceinline__ bool lambda0_pass(const GeneralArgs& A, double& s_out
                 const int64_t qg = c * (TT / V) + ql;
                 T va[V], vb[V], vd[V];
                 bool ok[V];
-                if ((ql + 1) * V <= m) {
+                if (qg * V >= sb0 && (qg + 1) * V <= sb1) {
                     const VT wa = reinterpret_cast<const VT*>(ring.stage(st, 0))[ql];
                     const VT wb = reinterpret_cast<const VT*>(ring.stage(st, 1))[ql];
                     const VT wd = reinterpret_cast<const VT*>(ring.stage(st, 2))[ql];
@@ -580,9 +580,9 @@ __device__ __forceinline__ bool lambda0_pass(const GeneralArgs& A, double& s_out
                         ok[j] = true;
                     }
                 } else {
-                    load_vec<T>(pa, n, qg, false, va, ok);
-                    load_vec<T>(pb, n, qg, false, vb, ok);
-                    load_vec<T>(pd, n, qg, false, vd, ok);
+                    load_vec<T>(pa, sp, qg, false, va, ok);
+                    load_vec<T>(pb, sp, qg, false, vb, ok);
+                    load_vec<T>(pd, sp, qg, false, vd, ok);
                 }
                 lambda0_vec<T>(va, vb, vd, ok, s, q, s64, q64);
             }
@@ -590,10 +590,9 @@ __device__ __forceinline__ bool lambda0_pass(const GeneralArgs& A, double& s_out
         }
         parity = ring.parity;
     } else {
-        const int64_t nv = (n + V - 1) / V;
         const int lane = threadIdx.x & 31;
         constexpr int U = kGenU;
-        const WarpSweep sw(nv, U);
+        const WarpSweep sw(span_qlo<V>(sp), span_qhi<V>(sp), U, gp.member, gp.g);
         int steps = 0;
         for (int64_t it = 0; it < sw.count; it++) {
             if (++steps == kFlushEvery) {
@@ -607,9 +606,9 @@ __device__ __forceinline__ bool lambda0_pass(const GeneralArgs& A, double& s_out
             bool ok[U][V];
 #pragma unroll
             for (int w = 0; w < U; w++) {
-                load_vec<T>(pa, n, base + w * 32 + lane, false, va[w], ok[w]);
-                load_vec<T>(pb, n, base + w * 32 + lane, false, vb[w], ok[w]);
-                load_vec<T>(pd, n, base + w * 32 + lane, false, vd[w], ok[w]);
+                load_vec<T>(pa, sp, base + w * 32 + lane, A.aligned != 0, va[w], ok[w]);
+                load_vec<T>(pb, sp, base + w * 32 + lane, A.aligned != 0, vb[w], ok[w]);
+                load_vec<T>(pd, sp, base + w * 32 + lane, A.aligned != 0, vd[w], ok[w]);
             }
 #pragma unroll
             for (int w = 0; w < U; w++) lambda0_vec<T>(va[w], vb[w], vd[w], ok[w], s, q, s64, q64);
@@ -629,32 +628,25 @@ __device__ __forceinline__ bool lambda0_pass(const GeneralArgs& A, double& s_out
         bar_target += (unsigned)G;                                              \
     } while (0)
 
+// ---- one solve (or one phi evaluation) by one group of blocks ------------------------------
+// smem / ring_bars: the block's bulk-copy stages and their mbarriers (initialised by the
+// caller when A.staged); ring_parity: their phase bits, carried across calls.
 template <typename T>
-__global__ void __launch_bounds__(NT, 2) general_kernel(GeneralArgs A) {
+__device__ __forceinline__ void general_solve(const GeneralArgs& A, const Grp& gp, T* smem, uint64_t* ring_bars,
+                                              unsigned& ring_parity) {
     __shared__ double sh[kPartialQ][NWARP];
     __shared__ double bc[kPartialQ];
-    extern __shared__ __align__(128) unsigned char dyn_smem[];
-    __shared__ uint64_t ring_bars[kStages];
-    T* const smem = reinterpret_cast<T*>(dyn_smem);
-    unsigned ring_parity = 0;
-    if (A.staged) {
-        if (threadIdx.x == 0) {
-            for (int st = 0; st < kStages; st++) mbar_init(&ring_bars[st], 1);
-            fence_barrier_init();
-        }
-        __syncthreads();
-    }
-    const int G = gridDim.x;
+    const int G = gp.g;
     unsigned bar_target = (unsigned)G + (A.fault_inject ? 1u : 0u);
-    unsigned* bar = &A.hdr->bar_count;
-    int* err = &A.hdr->error;
+    unsigned* bar = &gp.hdr->bar_count;
+    int* err = &gp.hdr->error;
     const double r = A.r;
     int passes = 0, par = 0;
 
     if (A.phi_only) {  // cqk_phi: one evaluation at A.lambda0 (and x when requested)
         EvalAcc acc;
         acc.init();
-        eval_pass<T, false>(A, A.lambda0, false, false, false, acc, smem, ring_bars, ring_parity, err);
+        eval_pass<T, false>(A, gp, A.lambda0, false, false, false, acc, smem, ring_bars, ring_parity, err);
         acc.flush();
         double pv[3] = {acc.phi64, acc.sfree64, acc.absbx64};
         double pt[2] = {acc.satl, acc.satu};
@@ -662,17 +654,17 @@ __global__ void __launch_bounds__(NT, 2) general_kernel(GeneralArgs A) {
         block_sum<2>(pt, sh);
         if (threadIdx.x == 0) {
             const double w5[5] = {pv[0], pv[1], pv[2], pt[0], pt[1]};
-            write_partials<5>(A.part, 0, w5);
+            write_partials<5>(gp.part, gp.member, G, 0, w5);
         }
         if (A.x) {
             EvalAcc acc2;
             acc2.init();
-            eval_pass<T, false>(A, A.lambda0, true, false, true, acc2, smem, ring_bars, ring_parity, err);
+            eval_pass<T, false>(A, gp, A.lambda0, true, false, true, acc2, smem, ring_bars, ring_parity, err);
         }
         double dummy[1] = {0.0}, tot[1];
-        if (last_block_sums<1>(A.part, &A.hdr->ticket, dummy, tot, sh)) {
+        if (last_block_sums<1>(gp.part, gp.member, G, &gp.hdr->ticket, dummy, tot, sh)) {
             double red[5];
-            grid_reduce<5>(A.part, 0, -1, red, sh, bc);
+            grid_reduce<5>(gp.part, G, 0, -1, red, sh, bc);
             if (threadIdx.x == 0) {
                 A.phi_out[0] = red[0];
                 A.phi_out[1] = red[1] + red[3];
@@ -687,13 +679,13 @@ __global__ void __launch_bounds__(NT, 2) general_kernel(GeneralArgs A) {
     double lam0 = A.lambda0;
     if (A.init == CQK_INIT_FORMULA) {
         double s, q;
-        lambda0_pass<T>(A, s, q, smem, ring_bars, ring_parity, err);
+        lambda0_pass<T>(A, gp, s, q, smem, ring_bars, ring_parity, err);
         double pv[2] = {s, q};
         block_sum<2>(pv, sh);
-        write_partials<2>(A.part, par, pv);
+        write_partials<2>(gp.part, gp.member, G, par, pv);
         CQK_BARRIER_OR_LEAVE();
         double red[2];
-        grid_reduce<2>(A.part, par, -1, red, sh, bc);
+        grid_reduce<2>(gp.part, G, par, -1, red, sh, bc);
         par ^= 1;
         lam0 = (r - red[0]) / red[1];  // eq. (CQKlambda0), J = all variables
         passes++;
@@ -712,21 +704,21 @@ __global__ void __launch_bounds__(NT, 2) general_kernel(GeneralArgs A) {
         }
         EvalAcc acc;
         acc.init();
-        if (k > 0 && !wide_data) eval_pass<T, true>(A, lam, false, false, (k & 1) == 1, acc, smem, ring_bars, ring_parity, err);
-        else eval_pass<T, false>(A, lam, false, k == 0 && A.validate, (k & 1) == 1, acc, smem, ring_bars, ring_parity, err);
+        if (k > 0 && !wide_data) eval_pass<T, true>(A, gp, lam, false, false, (k & 1) == 1, acc, smem, ring_bars, ring_parity, err);
+        else eval_pass<T, false>(A, gp, lam, false, k == 0 && A.validate, (k & 1) == 1, acc, smem, ring_bars, ring_parity, err);
         acc.flush();
         passes++;
-        if (__any_sync(0xffffffffu, acc.bad) && (threadIdx.x & 31) == 0) atomicOr(&A.hdr->flags, kFlagBadInput);
-        if (k == 0 && __any_sync(0xffffffffu, acc.wide) && (threadIdx.x & 31) == 0) atomicOr(&A.hdr->flags, kFlagWide);
+        if (__any_sync(0xffffffffu, acc.bad) && (threadIdx.x & 31) == 0) atomicOr(&gp.hdr->flags, kFlagBadInput);
+        if (k == 0 && __any_sync(0xffffffffu, acc.wide) && (threadIdx.x & 31) == 0) atomicOr(&gp.hdr->flags, kFlagWide);
         double pv[5] = {acc.phi64, acc.sfree64, acc.satl, acc.satu, acc.absbx64};
         block_sum<5>(pv, sh);
-        write_partials<5>(A.part, par, pv);
+        write_partials<5>(gp.part, gp.member, G, par, pv);
         CQK_BARRIER_OR_LEAVE();
         double red[5];
-        grid_reduce<5>(A.part, par, -1, red, sh, bc);
+        grid_reduce<5>(gp.part, G, par, -1, red, sh, bc);
         par ^= 1;
-        if (k == 0) wide_data = (__ldcg(&A.hdr->flags) & kFlagWide) != 0;
-        if (k == 0 && A.validate && (__ldcg(&A.hdr->flags) & kFlagBadInput)) {
+        if (k == 0) wide_data = (__ldcg(&gp.hdr->flags) & kFlagWide) != 0;
+        if (k == 0 && A.validate && (__ldcg(&gp.hdr->flags) & kFlagBadInput)) {
             bad_input = true;
             status = CQK_BAD_INPUT;
             k++;
@@ -801,7 +793,7 @@ __global__ void __launch_bounds__(NT, 2) general_kernel(GeneralArgs A) {
         if (need_bp) {
             // closest breakpoint right of the lower end / left of the upper end (Alg. 1); the
             // block maximum of (-bp) or (bp) keeps one reduction code path
-            double bp = breakpoint_pass<T>(A, need_bp > 0 ? lower : upper, need_bp);
+            double bp = breakpoint_pass<T>(A, gp, need_bp > 0 ? lower : upper, need_bp);
             bp = need_bp > 0 ? -bp : bp;
             bp = warp_max(bp);
             if ((threadIdx.x & 31) == 0) sh[0][threadIdx.x >> 5] = bp;
@@ -810,13 +802,13 @@ __global__ void __launch_bounds__(NT, 2) general_kernel(GeneralArgs A) {
                 double m = -INFINITY;
                 for (int w = 0; w < NWARP; w++) m = fmax(m, sh[0][w]);
                 const double pvb[1] = {m};
-                write_partials<1>(A.part, par, pvb);
+                write_partials<1>(gp.part, gp.member, G, par, pvb);
             }
             __syncthreads();
             passes++;
             CQK_BARRIER_OR_LEAVE();
             double redb[1];
-            grid_reduce<1>(A.part, par, 0, redb, sh, bc);
+            grid_reduce<1>(gp.part, G, par, 0, redb, sh, bc);
             par ^= 1;
             const double m = need_bp > 0 ? -redb[0] : redb[0];
             if (!isfinite(m)) {
@@ -844,13 +836,13 @@ __global__ void __launch_bounds__(NT, 2) general_kernel(GeneralArgs A) {
     EvalAcc acc;
     acc.init();
     if (!bad_input && status != CQK_INFEASIBLE) {
-        if (!wide_data) eval_pass<T, true>(A, final_lam, true, false, (k & 1) == 1, acc, smem, ring_bars, ring_parity, err);
-        else eval_pass<T, false>(A, final_lam, true, false, (k & 1) == 1, acc, smem, ring_bars, ring_parity, err);
+        if (!wide_data) eval_pass<T, true>(A, gp, final_lam, true, false, (k & 1) == 1, acc, smem, ring_bars, ring_parity, err);
+        else eval_pass<T, false>(A, gp, final_lam, true, false, (k & 1) == 1, acc, smem, ring_bars, ring_parity, err);
         passes++;
     }
     acc.flush();
     double pv[3] = {acc.phi64, acc.absbx64, (double)acc.nfree}, tot[3];
-    if (last_block_sums<3>(A.part, &A.hdr->ticket, pv, tot, sh) && threadIdx.x == 0) {
+    if (last_block_sums<3>(gp.part, gp.member, G, &gp.hdr->ticket, pv, tot, sh) && threadIdx.x == 0) {
         cqk_info inf;
         inf.lambda = final_lam;
         inf.residual = tot[0] - r;
@@ -859,7 +851,7 @@ __global__ void __launch_bounds__(NT, 2) general_kernel(GeneralArgs A) {
         inf.lambda0 = lam0;
         inf.nfree = (int64_t)tot[2];
         inf.iters = k;
-        const int e = *(volatile int*)&A.hdr->error;
+        const int e = *(volatile int*)&gp.hdr->error;
         inf.status = e ? e : status;
         inf.passes = passes;
         inf.stop = stop;
@@ -867,6 +859,27 @@ __global__ void __launch_bounds__(NT, 2) general_kernel(GeneralArgs A) {
         inf.tile = 0;
         *A.info = inf;
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT, 2) general_kernel(GeneralArgs A) {
+    extern __shared__ __align__(128) unsigned char dyn_smem[];
+    __shared__ uint64_t ring_bars[kStages];
+    unsigned ring_parity = 0;
+    if (A.staged) {
+        if (threadIdx.x == 0) {
+            for (int st = 0; st < kStages; st++) mbar_init(&ring_bars[st], 1);
+            fence_barrier_init();
+        }
+        __syncthreads();
+    }
+    Grp gp;
+    gp.member = blockIdx.x;
+    gp.g = gridDim.x;
+    gp.sp = Span{0, A.n};
+    gp.hdr = A.hdr;
+    gp.part = A.part;
+    general_solve<T>(A, gp, reinterpret_cast<T*>(dyn_smem), ring_bars, ring_parity);
 }
 
 GeneralArgs make_args(int64_t n, const void* a, const void* b, const void* d, const void* l, const void* u, void* x,

@@ -175,23 +175,23 @@ __device__ __forceinline__ void condat_slab(const T (&vals)[VecOf<T>::V], const 
 }
 
 template <typename T, bool L1>
-__device__ void condat_chunk(const T* __restrict__ y, int64_t n, bool aligned, double r, int64_t w, int64_t W,
+__device__ void condat_chunk(const T* __restrict__ y, const Span& sp, bool aligned, double r, int64_t w, int64_t W,
                              double& S_out, long long& nJ_out) {
     constexpr int V = VecOf<T>::V;
     constexpr int K = condat_k<T>();
     constexpr int TILE = 32 * K * V;
     const int lane = threadIdx.x & 31;
-    const int64_t ntiles = (n + TILE - 1) / TILE;
+    const int64_t t0 = sp.lo / TILE, ntiles = (sp.hi + TILE - 1) / TILE;
     CondatState st;
     st.S = 0.0;
     st.nJ = 0;
     st.rs = -1;
     condat_set_lam<L1>(st, 0.0);
-    for (int64_t t = w; t < ntiles; t += W) {
+    for (int64_t t = t0 + w; t < ntiles; t += W) {
         T vals[K][V];
         bool okv[K][V];
 #pragma unroll
-        for (int k = 0; k < K; k++) load_vec<T>(y, n, t * 32 * K + k * 32 + lane, aligned, vals[k], okv[k]);
+        for (int k = 0; k < K; k++) load_vec<T>(y, sp, t * 32 * K + k * 32 + lane, aligned, vals[k], okv[k]);
 #pragma unroll
         for (int k = 0; k < K; k++)
             condat_slab<T, L1>(vals[k], okv[k], (t * 32 * K + k * 32 + lane) * V, INT64_MAX, true, r, st);
@@ -200,11 +200,11 @@ __device__ void condat_chunk(const T* __restrict__ y, int64_t n, bool aligned, d
     if (st.nJ > 0 && st.rs >= 0) {
         const int64_t tlast = st.rs / TILE;
         const int64_t before = st.rs;
-        for (int64_t t = w; t <= tlast; t += W) {
+        for (int64_t t = t0 + w; t <= tlast; t += W) {
             T vals[K][V];
             bool okv[K][V];
 #pragma unroll
-            for (int k = 0; k < K; k++) load_vec<T>(y, n, t * 32 * K + k * 32 + lane, aligned, vals[k], okv[k]);
+            for (int k = 0; k < K; k++) load_vec<T>(y, sp, t * 32 * K + k * 32 + lane, aligned, vals[k], okv[k]);
 #pragma unroll
             for (int k = 0; k < K; k++)
                 condat_slab<T, L1>(vals[k], okv[k], (t * 32 * K + k * 32 + lane) * V, before, false, r, st);
@@ -227,17 +227,17 @@ struct PassAcc {
 };
 
 template <typename T, bool L1, bool NEG, bool FIRST>
-__device__ __forceinline__ void newton_sweep(const T* __restrict__ y, int64_t n, int64_t nv, bool aligned, bool rev,
-                                             unsigned long long tb, float rd, float ru, double lam, df Lm,
+__device__ __forceinline__ void newton_sweep(const T* __restrict__ y, const Span& sp, const Grp& gp, bool aligned,
+                                             bool rev, unsigned long long tb, float rd, float ru, double lam, df Lm,
                                              PassAcc& pa) {
     constexpr int V = VecOf<T>::V;
     constexpr int U = kStreamU;
     using VT = typename VecOf<T>::type;
     const int lane = threadIdx.x & 31;
-    const WarpSweep sw(nv, U);
+    const WarpSweep sw(span_qlo<V>(sp), span_qhi<V>(sp), U, gp.member, gp.g);
     for (int64_t it = 0; it < sw.count; it++) {
         const int64_t base = sw.base(it, rev);
-        const bool full = aligned && (base + 32 * U) * V <= n;  // warp-uniform
+        const bool full = aligned && base * V >= sp.lo && (base + 32 * U) * V <= sp.hi;  // warp-uniform
         T vv[U][V];
         bool okk[U][V];
         if (full) {
@@ -253,7 +253,7 @@ __device__ __forceinline__ void newton_sweep(const T* __restrict__ y, int64_t n,
             }
         } else {
 #pragma unroll
-            for (int u = 0; u < U; u++) load_vec<T>(y, n, base + u * 32 + lane, aligned, vv[u], okk[u]);
+            for (int u = 0; u < U; u++) load_vec<T>(y, sp, base + u * 32 + lane, aligned, vv[u], okk[u]);
         }
         unsigned selm = 0;
 #pragma unroll
@@ -298,7 +298,7 @@ __device__ __forceinline__ void newton_sweep(const T* __restrict__ y, int64_t n,
 }
 
 // per-block totals of a pass (fixed order) -> partials slot `par`
-__device__ __forceinline__ void write_pass_partials(double* part, int par, double acc, unsigned cm, unsigned ct,
+__device__ __forceinline__ void write_pass_partials(const Grp& gp, int par, double acc, unsigned cm, unsigned ct,
                                                     double* sh_d, unsigned* sh_u) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     acc = warp_sum(acc);
@@ -319,13 +319,12 @@ __device__ __forceinline__ void write_pass_partials(double* part, int par, doubl
             c1 += sh_u[NWARP + w];
         }
         const double pv[3] = {t, (double)c0, (double)(c0 + c1)};
-        write_partials<3>(part, par, pv);
+        write_partials<3>(gp.part, gp.member, gp.g, par, pv);
     }
 }
 
 // grid totals of slot `par` by warp 0 (fixed order); valid in lane 0 of warp 0
-__device__ __forceinline__ void warp0_grid_sums(const double* part, int par, double (&out)[3]) {
-    const int G = gridDim.x;
+__device__ __forceinline__ void warp0_grid_sums(const double* part, int G, int par, double (&out)[3]) {
     const int lane = threadIdx.x & 31;
     double v[3] = {0.0, 0.0, 0.0};
     for (int bI = lane; bI < G; bI += 32)
@@ -335,9 +334,11 @@ __device__ __forceinline__ void warp0_grid_sums(const double* part, int par, dou
     for (int q = 0; q < 3; q++) out[q] = warp_sum(v[q]);
 }
 
-// ---- the persistent kernel ----------------------------------------------------------------
+// ---- one projection by one group of blocks ------------------------------------------------
+// A supplies the arrays, r, the options and the info slot; gp the group (member, size, span,
+// header and partial sums).  The instance is the span [gp.sp.lo, gp.sp.hi) of y and x.
 template <typename T, bool L1>
-__global__ void __launch_bounds__(NT, 2) simplex_kernel(SimplexArgs A) {
+__device__ __forceinline__ void simplex_solve(const SimplexArgs& A, const Grp& gp) {
     constexpr int V = VecOf<T>::V;
     __shared__ double sh[kPartialQ][NWARP];
     __shared__ double bc[kPartialQ];
@@ -347,16 +348,17 @@ __global__ void __launch_bounds__(NT, 2) simplex_kernel(SimplexArgs A) {
     __shared__ double s_lam, s_final;
     __shared__ int s_done, s_bad;
     const T* __restrict__ y = static_cast<const T*>(A.y);
-    const int64_t n = A.n;
-    const int64_t nv = (n + V - 1) / V;
+    const Span sp = gp.sp;
+    const int64_t n = sp.hi - sp.lo;
+    const int64_t qlo = span_qlo<V>(sp), qhi = span_qhi<V>(sp);
     const int lane = threadIdx.x & 31;
-    const int G = gridDim.x;
-    const int64_t gwarp = (int64_t)blockIdx.x * NWARP + (threadIdx.x >> 5);
+    const int G = gp.g;
+    const int64_t gwarp = (int64_t)gp.member * NWARP + (threadIdx.x >> 5);
     const int64_t nwarps = (int64_t)G * NWARP;
     const bool aligned = A.aligned != 0;
     unsigned bar_target = (unsigned)G + (A.fault_inject ? 1u : 0u);
-    unsigned* bar = &A.hdr->bar_count;
-    int* err = &A.hdr->error;
+    unsigned* bar = &gp.hdr->bar_count;
+    int* err = &gp.hdr->error;
     const double r = A.r;
 
     // ------------------------------------------------------------------ pass 0: start
@@ -372,13 +374,13 @@ __global__ void __launch_bounds__(NT, 2) simplex_kernel(SimplexArgs A) {
             double acc_wide = 0.0;  // FP64 values outside the df operating range
             long long mxk = order_key(-INFINITY);
             float mxf = -INFINITY;
-            const WarpSweep sw(nv, kStreamU);
+            const WarpSweep sw(qlo, qhi, kStreamU, gp.member, gp.g);
             for (int64_t it = 0; it < sw.count; it++) {
                 const int64_t base = sw.base(it, false);
                 T vv[kStreamU][V];
                 bool okk[kStreamU][V];
 #pragma unroll
-                for (int u = 0; u < kStreamU; u++) load_vec<T>(y, n, base + u * 32 + lane, aligned, vv[u], okk[u]);
+                for (int u = 0; u < kStreamU; u++) load_vec<T>(y, sp, base + u * 32 + lane, aligned, vv[u], okk[u]);
                 unsigned widem = 0;
 #pragma unroll
                 for (int uj = 0; uj < kStreamU * V; uj++) {
@@ -416,7 +418,7 @@ __global__ void __launch_bounds__(NT, 2) simplex_kernel(SimplexArgs A) {
         if (condat) {
             double Sw = 0.0;
             long long nJw = 0;
-            condat_chunk<T, L1>(y, n, aligned, r, gwarp, nwarps, Sw, nJw);
+            condat_chunk<T, L1>(y, sp, aligned, r, gwarp, nwarps, Sw, nJw);
             q[1] = lane == 0 ? Sw : 0.0;
             q[2] = lane == 0 ? (double)nJw : 0.0;
             passes++;
@@ -429,7 +431,7 @@ __global__ void __launch_bounds__(NT, 2) simplex_kernel(SimplexArgs A) {
             sh[1][wid] = s1;
             sh[2][wid] = s2;
             sh[3][wid] = m;
-            if (badw && A.validate) atomicOr(&A.hdr->flags, kFlagBadInput);
+            if (badw && A.validate) atomicOr(&gp.hdr->flags, kFlagBadInput);
         }
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -441,7 +443,7 @@ __global__ void __launch_bounds__(NT, 2) simplex_kernel(SimplexArgs A) {
                 t3 = fmax(t3, sh[3][w]);
             }
             const double pv[4] = {t0, t1, t2, t3};
-            write_partials<4>(A.part, 0, pv);
+            write_partials<4>(gp.part, gp.member, G, 0, pv);
         }
         __syncthreads();
         if (!grid_barrier(bar, bar_target, err, A.limit_ns, CQK_TIMEOUT)) {
@@ -450,7 +452,7 @@ __global__ void __launch_bounds__(NT, 2) simplex_kernel(SimplexArgs A) {
         }
         bar_target += (unsigned)G;
         double red[4];
-        grid_reduce<4>(A.part, 0, 3, red, sh, bc);
+        grid_reduce<4>(gp.part, G, 0, 3, red, sh, bc);
         abs_sum = red[0];
         if (condat) {
             lam0 = (r - red[1]) / red[2];  // eq. (lambdaJ) on the union of the chunks' J
@@ -462,7 +464,7 @@ __global__ void __launch_bounds__(NT, 2) simplex_kernel(SimplexArgs A) {
             lam0 = fmax((r - red[0]) / (double)n, -red[3]);  // eq. (CQKlambda0) with b = d = 1; Alg. 4 line 1
         }
     }
-    bool bad_input = A.validate && (__ldcg(&A.hdr->flags) & kFlagBadInput);
+    bool bad_input = A.validate && (__ldcg(&gp.hdr->flags) & kFlagBadInput);
 
     // ------------------------------------------------------------------ Newton loop (Alg. 4)
     // thread 0 keeps the bracket and the stopping logic; every thread keeps lambda
@@ -494,23 +496,23 @@ __global__ void __launch_bounds__(NT, 2) simplex_kernel(SimplexArgs A) {
                 const GtThreshold g = make_gt(-lam);
                 const df Lm = df_make(0.0f);
                 if (g.neg) {
-                    if (first) newton_sweep<T, L1, true, true>(y, n, nv, aligned, rev, g.bits, 0.f, 0.f, lam, Lm, pa);
-                    else newton_sweep<T, L1, true, false>(y, n, nv, aligned, rev, g.bits, 0.f, 0.f, lam, Lm, pa);
+                    if (first) newton_sweep<T, L1, true, true>(y, sp, gp, aligned, rev, g.bits, 0.f, 0.f, lam, Lm, pa);
+                    else newton_sweep<T, L1, true, false>(y, sp, gp, aligned, rev, g.bits, 0.f, 0.f, lam, Lm, pa);
                 } else {
-                    if (first) newton_sweep<T, L1, false, true>(y, n, nv, aligned, rev, g.bits, 0.f, 0.f, lam, Lm, pa);
-                    else newton_sweep<T, L1, false, false>(y, n, nv, aligned, rev, g.bits, 0.f, 0.f, lam, Lm, pa);
+                    if (first) newton_sweep<T, L1, false, true>(y, sp, gp, aligned, rev, g.bits, 0.f, 0.f, lam, Lm, pa);
+                    else newton_sweep<T, L1, false, false>(y, sp, gp, aligned, rev, g.bits, 0.f, 0.f, lam, Lm, pa);
                 }
             } else {
                 const float rd = f32_rd(-lam), ru = f32_ru(-lam);
                 const df Lm = df_from_f64(lam);
-                if (first) newton_sweep<T, L1, false, true>(y, n, nv, aligned, rev, 0ull, rd, ru, lam, Lm, pa);
-                else newton_sweep<T, L1, false, false>(y, n, nv, aligned, rev, 0ull, rd, ru, lam, Lm, pa);
+                if (first) newton_sweep<T, L1, false, true>(y, sp, gp, aligned, rev, 0ull, rd, ru, lam, Lm, pa);
+                else newton_sweep<T, L1, false, false>(y, sp, gp, aligned, rev, 0ull, rd, ru, lam, Lm, pa);
                 pa.acc64 = df_to_f64(pa.acc32);
             }
             passes++;
             if (A.validate && first && __any_sync(0xffffffffu, pa.nan) && lane == 0)
-                atomicOr(&A.hdr->flags, kFlagBadInput);
-            write_pass_partials(A.part, par, pa.acc64, pa.cm, pa.ct, sh_d, sh_u);
+                atomicOr(&gp.hdr->flags, kFlagBadInput);
+            write_pass_partials(gp, par, pa.acc64, pa.cm, pa.ct, sh_d, sh_u);
             if (!grid_barrier(bar, bar_target, err, A.limit_ns, CQK_TIMEOUT)) {
                 if (threadIdx.x == 0) A.info->status = CQK_TIMEOUT;
                 return;
@@ -518,11 +520,11 @@ __global__ void __launch_bounds__(NT, 2) simplex_kernel(SimplexArgs A) {
             bar_target += (unsigned)G;
             if (threadIdx.x < 32) {
                 double red[3];
-                warp0_grid_sums(A.part, par, red);
+                warp0_grid_sums(gp.part, G, par, red);
                 if (threadIdx.x == 0) {
                     int done = 0, bad = 0;
                     double next = lam;
-                    if (A.validate && first && (__ldcg(&A.hdr->flags) & kFlagBadInput)) {
+                    if (A.validate && first && (__ldcg(&gp.hdr->flags) & kFlagBadInput)) {
                         bad = 1;
                         done = 1;
                     } else {
@@ -603,14 +605,14 @@ __global__ void __launch_bounds__(NT, 2) simplex_kernel(SimplexArgs A) {
         const GtThreshold g = make_gt(-lamf);
         const float rd = f32_rd(-lamf);
         const df Lm = df_from_f64(lamf);
-        const WarpSweep sw(nv, kStreamU);
+        const WarpSweep sw(qlo, qhi, kStreamU, gp.member, gp.g);
         const bool rev = (k & 1) == 0;  // opposite direction to the last Newton pass
         for (int64_t it = 0; it < sw.count; it++) {
             const int64_t base = sw.base(it, rev);
             T vv[kStreamU][V];
             bool okk[kStreamU][V];
 #pragma unroll
-            for (int u = 0; u < kStreamU; u++) load_vec<T>(y, n, base + u * 32 + lane, aligned, vv[u], okk[u]);
+            for (int u = 0; u < kStreamU; u++) load_vec<T>(y, sp, base + u * 32 + lane, aligned, vv[u], okk[u]);
 #pragma unroll
             for (int u = 0; u < kStreamU; u++) {
                 const int64_t qw = base + u * 32;
@@ -653,14 +655,14 @@ __global__ void __launch_bounds__(NT, 2) simplex_kernel(SimplexArgs A) {
                         sx32 = df_add_f(sx32, fabsf(xv));
                     }
                 }
-                store_vec<T>(x, n, q, aligned, o);
-                if (A.mask) store_mask<V>(A.mask, n, qw, sel);
+                store_vec<T>(x, sp, q, aligned, o);
+                if (A.mask) store_mask<V>(A.mask, sp, qw, sel);
             }
         }
     }
     if constexpr (sizeof(T) == 4) sx = df_to_f64(sx32);
     double pv[2] = {sx, (double)nz}, tot[2];
-    if (last_block_sums<2>(A.part, &A.hdr->ticket, pv, tot, sh) && threadIdx.x == 0) {
+    if (last_block_sums<2>(gp.part, gp.member, G, &gp.hdr->ticket, pv, tot, sh) && threadIdx.x == 0) {
         cqk_info inf;
         const double sumx = copy ? abs_sum : tot[0];  // inside the l1 ball x = y
         inf.lambda = final_lam;
@@ -670,7 +672,7 @@ __global__ void __launch_bounds__(NT, 2) simplex_kernel(SimplexArgs A) {
         inf.lambda0 = lam0;
         inf.nfree = (int64_t)tot[1];
         inf.iters = k;
-        const int e = *(volatile int*)&A.hdr->error;
+        const int e = *(volatile int*)&gp.hdr->error;
         inf.status = e ? e : status;
         inf.passes = passes + (bad_input ? 0 : 1);
         inf.stop = stop;
@@ -678,6 +680,17 @@ __global__ void __launch_bounds__(NT, 2) simplex_kernel(SimplexArgs A) {
         inf.tile = tile;
         *A.info = inf;
     }
+}
+
+template <typename T, bool L1>
+__global__ void __launch_bounds__(NT, 2) simplex_kernel(SimplexArgs A) {
+    Grp gp;
+    gp.member = blockIdx.x;
+    gp.g = gridDim.x;
+    gp.sp = Span{0, A.n};
+    gp.hdr = A.hdr;
+    gp.part = A.part;
+    simplex_solve<T, L1>(A, gp);
 }
 
 }  // namespace

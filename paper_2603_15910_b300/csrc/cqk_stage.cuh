@@ -13,7 +13,7 @@
 // writing into shared memory when the block leaves.
 #pragma once
 
-#include "cqk_device.cuh"
+#include "cqk_block.cuh"
 
 namespace cqk {
 
@@ -68,39 +68,44 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, int* e
     return true;
 }
 
-// The tiles of one block over n elements of NA arrays of T, tile = TT elements.
+// The tiles of one group member over a span of NA arrays of T (16-byte aligned at element
+// 0): tile c holds the global elements [c*TT, (c+1)*TT); the span's tiles are shared out
+// round-robin among the g members.  The bulk copy of tile c delivers the elements
+// [b0, b1) = [c*TT, (c+1)*TT) intersected with the span rounded inwards to 16 bytes; smem
+// position of element e is e - c*TT.  Other elements of the span are read directly.
 template <typename T, int NA, int TT>
 struct TileRing {
     T* buf;              // dynamic shared memory: [kStages][NA][TT]
     uint64_t* bar;       // kStages mbarriers
     unsigned parity;     // bit s: parity of the next completion of stage s
-    int64_t n, ntiles, first, step, count;
+    int64_t slo, shi;    // the span rounded inwards to 16-byte boundaries
+    int64_t first, step, count;
 
-    __device__ __forceinline__ void setup(int64_t n_, T* buf_, uint64_t* bar_) {
+    __device__ __forceinline__ void setup(int64_t lo, int64_t hi, T* buf_, uint64_t* bar_, int member, int g) {
+        constexpr int64_t E = 16 / sizeof(T);
         buf = buf_;
         bar = bar_;
-        n = n_;
-        ntiles = (n + TT - 1) / TT;
-        first = blockIdx.x;
-        step = gridDim.x;
-        count = first < ntiles ? (ntiles - first + step - 1) / step : 0;
+        slo = (lo + E - 1) / E * E;
+        shi = hi / E * E;
+        if (shi < slo) shi = slo;
+        const int64_t c0 = lo / TT, c1 = (hi + TT - 1) / TT;
+        first = c0 + member;
+        step = g;
+        count = first < c1 ? (c1 - first + step - 1) / step : 0;
     }
     __device__ __forceinline__ int64_t tile(int64_t i, bool rev) const { return first + (rev ? count - 1 - i : i) * step; }
     __device__ __forceinline__ T* stage(int s, int a) const { return buf + ((size_t)s * NA + a) * TT; }
-    // number of leading elements of tile c delivered by the bulk copy (a multiple of 16 bytes)
-    __device__ __forceinline__ int staged(int64_t c) const {
-        const int64_t cnt = n - c * TT < TT ? n - c * TT : TT;
-        return (int)((cnt * (int64_t)sizeof(T)) / 16 * 16 / (int64_t)sizeof(T));
-    }
+    __device__ __forceinline__ int64_t b0(int64_t c) const { return c * TT > slo ? c * TT : slo; }
+    __device__ __forceinline__ int64_t b1(int64_t c) const { return (c + 1) * TT < shi ? (c + 1) * TT : shi; }
     // thread 0: start the copies of tile c into stage s
     __device__ __forceinline__ void issue(int64_t c, int s, const T* const* src) const {
-        const int m = staged(c);
-        const uint32_t bytes = (uint32_t)m * sizeof(T);
+        const int64_t lo = b0(c), hi = b1(c);
+        const uint32_t bytes = hi > lo ? (uint32_t)((hi - lo) * (int64_t)sizeof(T)) : 0u;
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive_expect_tx(&bar[s], bytes * NA);
         if (bytes)
 #pragma unroll
-            for (int a = 0; a < NA; a++) bulk_g2s(stage(s, a), src[a] + c * TT, bytes, &bar[s]);
+            for (int a = 0; a < NA; a++) bulk_g2s(stage(s, a) + (lo - c * TT), src[a] + lo, bytes, &bar[s]);
     }
 };
 
