@@ -374,12 +374,13 @@ double cqko_condat_init(const double* y, const int64_t* idx, int64_t p, double r
  * subset I of the variables and lambda_0 follows from eq. (lambdaJ) on the union
  * of the returned J's, using the per-chunk partial sums.
  * The subsets are the chunks of a fixed partition: variable i belongs to chunk
- * (i / tile) mod nchunks and every chunk is scanned in increasing i.
+ * ((i + shift) / tile) mod nchunks and every chunk is scanned in increasing i
+ * (shift places the first tile boundary; 0 for a problem that starts a tile).
  * Outputs: lambda_0, the union's sum and size.
  */
 double cqko_condat_chunks(int64_t n, const double* y, double r, int l1, int64_t tile,
-                          int64_t nchunks, double* usum, int64_t* ucount) {
-    int64_t ntiles = (n + tile - 1) / tile;
+                          int64_t nchunks, int64_t shift, double* usum, int64_t* ucount) {
+    int64_t ntiles = (n + shift + tile - 1) / tile;
     int64_t maxp = ((ntiles + nchunks - 1) / nchunks) * tile;
     int64_t* idx = (int64_t*)malloc(sizeof(int64_t) * (size_t)(maxp > 0 ? maxp : 1));
     int64_t* scratch = (int64_t*)malloc(sizeof(int64_t) * (size_t)(2 * (maxp > 0 ? maxp : 1)));
@@ -388,7 +389,8 @@ double cqko_condat_chunks(int64_t n, const double* y, double r, int l1, int64_t 
     for (int64_t c = 0; c < nchunks; c++) {
         int64_t p = 0;
         for (int64_t t = c; t < ntiles; t += nchunks)
-            for (int64_t i = t * tile; i < (t + 1) * tile && i < n; i++) idx[p++] = i;
+            for (int64_t i = t * tile - shift; i < (t + 1) * tile - shift && i < n; i++)
+                if (i >= 0) idx[p++] = i;
         if (p == 0) continue;
         double js; int64_t jc;
         cqko_condat_init(y, idx, p, r, l1, &js, &jc, scratch, NULL);

@@ -63,7 +63,7 @@ def _load():
         lib.cqko_solve_sort.restype = cint
         lib.cqko_condat_init.argtypes = [d_p, i64_p, i64, dbl, cint, d_p, i64_p, i64_p, d_p]
         lib.cqko_condat_init.restype = dbl
-        lib.cqko_condat_chunks.argtypes = [i64, d_p, dbl, cint, i64, i64, d_p, i64_p]
+        lib.cqko_condat_chunks.argtypes = [i64, d_p, dbl, cint, i64, i64, i64, d_p, i64_p]
         lib.cqko_condat_chunks.restype = dbl
         lib.cqko_condat.argtypes = [i64, d_p, dbl, d_p]
         lib.cqko_condat.restype = dbl
@@ -175,15 +175,15 @@ def condat_init(y, r, idx=None, l1=False, return_trace=False):
     return float(lam), js.value, jc.value
 
 
-def condat_chunks(y, r, tile, nchunks, l1=False):
-    """Parallel lambda_0 of Sec. 4 over the partition chunk(i) = (i // tile) % nchunks.
+def condat_chunks(y, r, tile, nchunks, l1=False, shift=0):
+    """Parallel lambda_0 of Sec. 4 over the partition chunk(i) = ((i + shift) // tile) % nchunks.
 
     Returns (lambda_0, sum over the union of J's, size of the union)."""
     y = _f64(y)
     us = ctypes.c_double()
     uc = ctypes.c_int64()
     lam = _load().cqko_condat_chunks(y.shape[0], _ptr(y), float(r), 1 if l1 else 0, int(tile),
-                                     int(nchunks), ctypes.byref(us), ctypes.byref(uc))
+                                     int(nchunks), int(shift), ctypes.byref(us), ctypes.byref(uc))
     return float(lam), us.value, uc.value
 
 

@@ -98,16 +98,18 @@ def test_alg2_multiplier_never_increases_in_the_scan():
             assert np.all(np.diff(tr) <= 0)
 
 
-def test_alg2_chunk_union_matches_manual_partition():
+@pytest.mark.parametrize("shift", [0, 1, 7, 15])
+def test_alg2_chunk_union_matches_manual_partition(shift):
+    # a problem that starts inside a tile (a batch member) sees its first tile cut short
     y = np.random.default_rng(8).normal(size=1000)
     tile, chunks = 16, 6
     S, C = 0.0, 0
     for c in range(chunks):
-        idx = np.array([i for i in range(1000) if (i // tile) % chunks == c])
+        idx = np.array([i for i in range(1000) if ((i + shift) // tile) % chunks == c])
         _, s, k = oracle.condat_init(y, 1.0, idx=idx)
         S += s
         C += k
-    lam0, S2, C2 = oracle.condat_chunks(y, 1.0, tile, chunks)
+    lam0, S2, C2 = oracle.condat_chunks(y, 1.0, tile, chunks, shift=shift)
     assert C == C2 and math.isclose(S, S2, rel_tol=1e-13)
 
 
