@@ -98,7 +98,12 @@ typedef struct cqk_options {
     int32_t max_blocks;     /* 0 = automatic grid size; otherwise an upper bound                */
     int32_t fault_inject;   /* testing only: 1 = make every device-wide wait unsatisfiable so   */
                             /* that the call ends with CQK_TIMEOUT after spin_limit_us          */
-    int32_t reserved[8];
+    int32_t group_elems;    /* batched calls: an instance of length m is solved by a group of    */
+                            /* min(32, ceil(m / group_elems)) blocks; 0 (default): 1048576 for  */
+                            /* simplex / l1 batches, 65536 for general ones                     */
+    int32_t condat_chunk;   /* CQK_INIT_CONDAT: the partition has min(warps, ceil(n /            */
+                            /* condat_chunk)) chunks; 0 (default): 512                          */
+    int32_t reserved[6];
 } cqk_options;
 
 /* Written on the device by every solve. */
@@ -174,6 +179,50 @@ int cqk_project_simplex(int64_t n, int32_t dtype, const void* y, double r, void*
 int cqk_project_l1(int64_t n, int32_t dtype, const void* y, double r, void* x,
                    uint32_t* free_mask, cqk_info* info_dev, const cqk_options* opt,
                    void* workspace, size_t ws_bytes, void* stream);
+
+/*
+ * A batch of B independent instances in one persistent launch (the paper solves one
+ * instance at a time; the batch is a throughput convenience of this library: every
+ * instance is solved exactly as the single call would, by Alg. 1 or Alg. 4).
+ *   B              number of instances (B = 0: nothing is launched)
+ *   offsets_dev    device array of B + 1 int64: instance k is the element range
+ *                  [offsets_dev[k], offsets_dev[k+1]) of every array (non-decreasing;
+ *                  empty instances allowed; read on the device only, so a decreasing pair
+ *                  is reported as status CQK_BAD_ARG in that instance's info)
+ *   a, b, d, l, u  device arrays of offsets_dev[B] elements; b, d, l, u all NULL selects
+ *                  the simplex batch on y = a (b = d = 1, l = 0, u = +inf), the same as
+ *                  cqk_project_simplex_batched
+ *   r_dev          device array of B doubles: the right-hand side of each instance
+ *   x, free_mask   as for the single calls, over the concatenated elements (mask bit i%32
+ *                  of word i/32 for global element index i)
+ *   info_dev       device array of B cqk_info; instance k's outcome in info_dev[k].
+ *                  An empty instance gets CQK_OK if r == 0, else CQK_INFEASIBLE (general);
+ *                  CQK_INFEASIBLE (simplex); CQK_OK with stop CQK_STOP_INSIDE (l1 ball).
+ *                  An instance whose r is NaN (projections: not in (0, inf)) gets
+ *                  CQK_BAD_ARG and its x is not written.
+ *   workspace      at least cqk_workspace_bytes(n_total, B, dtype) bytes, 256-byte aligned
+ * Instances are handed, longest first, to groups of co-resident blocks (a group of
+ * min(32, ceil(m / group_elems)) blocks for an instance of m elements).  With
+ * CQK_INIT_CONDAT, element offsets_dev[k] + i of instance k lies in chunk
+ * ((i + offsets_dev[k] % tile) / tile) % nchunks, tile and nchunks as in info_dev[k].
+ */
+int cqk_solve_batched(int32_t B, const int64_t* offsets_dev, int32_t dtype, const void* a,
+                      const void* b, const void* d, const void* l, const void* u,
+                      const double* r_dev, void* x, uint32_t* free_mask, cqk_info* info_dev,
+                      const cqk_options* opt, void* workspace, size_t ws_bytes, void* stream);
+
+/* B simplex projections (cqk_project_simplex per instance); arguments as cqk_solve_batched. */
+int cqk_project_simplex_batched(int32_t B, const int64_t* offsets_dev, int32_t dtype,
+                                const void* y, const double* r_dev, void* x,
+                                uint32_t* free_mask, cqk_info* info_dev,
+                                const cqk_options* opt, void* workspace, size_t ws_bytes,
+                                void* stream);
+
+/* B l1-ball projections (cqk_project_l1 per instance); arguments as cqk_solve_batched. */
+int cqk_project_l1_batched(int32_t B, const int64_t* offsets_dev, int32_t dtype, const void* y,
+                           const double* r_dev, void* x, uint32_t* free_mask,
+                           cqk_info* info_dev, const cqk_options* opt, void* workspace,
+                           size_t ws_bytes, void* stream);
 
 /*
  * Allocation-free variant of cqk_project_simplex (the paper has no counterpart: this is a

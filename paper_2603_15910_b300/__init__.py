@@ -15,6 +15,9 @@ from .api import (  # noqa: F401
     library,
     phi,
     project_l1,
+    project_l1_batched,
     project_simplex,
+    project_simplex_batched,
     solve,
+    solve_batched,
 )

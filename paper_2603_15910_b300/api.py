@@ -54,7 +54,9 @@ class _Options(ctypes.Structure):
         ("spin_limit_us", ctypes.c_int64),
         ("max_blocks", ctypes.c_int32),
         ("fault_inject", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 8),
+        ("group_elems", ctypes.c_int32),
+        ("condat_chunk", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 6),
     ]
 
 
@@ -128,6 +130,13 @@ def library():
             f = getattr(lib, name)
             f.argtypes = [i64, i32, vp, dbl, vp, vp, vp, ctypes.POINTER(_Options), vp, sz, vp]
             f.restype = ctypes.c_int
+        lib.cqk_solve_batched.argtypes = [i32, vp, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, ctypes.POINTER(_Options),
+                                          vp, sz, vp]
+        lib.cqk_solve_batched.restype = ctypes.c_int
+        for name in ("cqk_project_simplex_batched", "cqk_project_l1_batched"):
+            f = getattr(lib, name)
+            f.argtypes = [i32, vp, i32, vp, vp, vp, vp, vp, ctypes.POINTER(_Options), vp, sz, vp]
+            f.restype = ctypes.c_int
         lib.cqk_status_string.argtypes = [ctypes.c_int]
         lib.cqk_status_string.restype = ctypes.c_char_p
         lib.cqk_last_cuda_error.argtypes = []
@@ -167,7 +176,7 @@ def stream_handle(stream=None):
 
 
 def make_options(init=None, max_iter=100, lambda0=0.0, validate=True, final_step=None, spin_limit_us=2_000_000,
-                 max_blocks=0, fault_inject=False) -> _Options:
+                 max_blocks=0, fault_inject=False, group_elems=0, condat_chunk=0) -> _Options:
     o = _Options()
     library().cqk_default_options(ctypes.byref(o))
     o.max_iter = int(max_iter)
@@ -179,6 +188,8 @@ def make_options(init=None, max_iter=100, lambda0=0.0, validate=True, final_step
     o.spin_limit_us = int(spin_limit_us)
     o.max_blocks = int(max_blocks)
     o.fault_inject = 1 if fault_inject else 0
+    o.group_elems = int(group_elems)
+    o.condat_chunk = int(condat_chunk)
     return o
 
 
@@ -197,6 +208,11 @@ class Workspace:
     def read_info(self, i: int = 0) -> Info:
         raw = self.info[i * INFO_BYTES:(i + 1) * INFO_BYTES].cpu().numpy().tobytes()
         return Info.from_bytes(raw)
+
+    def read_infos(self, count: int) -> list:
+        """The first `count` infos, in one device-to-host copy."""
+        raw = self.info[:count * INFO_BYTES].cpu().numpy().tobytes()
+        return [Info.from_bytes(raw[i * INFO_BYTES:(i + 1) * INFO_BYTES]) for i in range(count)]
 
 
 def check_rc(rc, what):
@@ -286,3 +302,70 @@ def project_l1(y, r=1.0, *, init=Init.CONDAT, max_iter=100, lambda0=0.0, validat
                want_mask=False, ws: Workspace | None = None, stream=None, sync=True, **kw):
     """Projection of y onto {sum |x_i| <= r} (cqk_project_l1).  Returns (x, info, mask)."""
     return _project("cqk_project_l1", y, r, init, max_iter, lambda0, validate, out, want_mask, ws, stream, sync, kw)
+
+
+def _batch_args(arrays, offsets, r):
+    host, dev, arrays = _on_device(list(arrays))
+    offsets = torch.as_tensor(offsets, dtype=torch.int64).to(dev).contiguous()
+    r = torch.as_tensor(r, dtype=torch.float64).to(dev).contiguous()
+    _check_device(*arrays, offsets, r)
+    B = offsets.numel() - 1
+    if B < 0 or r.numel() != B:
+        raise ValueError("offsets must hold B + 1 entries and r B entries")
+    n = arrays[0].numel()
+    for t in arrays[1:]:
+        if t.dtype != arrays[0].dtype or t.numel() != n:
+            raise ValueError("the arrays must share dtype and length")
+    return host, dev, arrays, offsets, r, B, n
+
+
+def _batch_finish(host, x, mask, ws, B, sync):
+    infos = ws.read_infos(B) if sync else None
+    if host:
+        x = x.cpu()
+        mask = mask.cpu() if mask is not None else None
+    return x, infos, mask
+
+
+def solve_batched(a, b, d, l, u, offsets, r, *, init=Init.FORMULA, max_iter=100, lambda0=0.0, validate=True,
+                  final_step=None, out=None, want_mask=False, ws: Workspace | None = None, stream=None, sync=True,
+                  **kw):
+    """B general CQK instances in one launch (cqk_solve_batched): instance k is the element
+    range offsets[k]:offsets[k+1] of the concatenated a, b, d, l, u, with right-hand side
+    r[k].  Returns (x, infos, mask); infos is a list of B Info (None with sync=False)."""
+    host, dev, (a, b, d, l, u), offsets, r, B, n = _batch_args([a, b, d, l, u], offsets, r)
+    x = out if out is not None else torch.empty_like(a)
+    mask = torch.zeros((n + 31) // 32, dtype=torch.int32, device=dev) if want_mask else None
+    ws = ws or Workspace(n, max(B, 1), a.dtype, dev)
+    opt = make_options(init=init, max_iter=max_iter, lambda0=lambda0, validate=validate, final_step=final_step, **kw)
+    rc = library().cqk_solve_batched(B, ptr(offsets), dtype_code(a.dtype), ptr(a), ptr(b), ptr(d), ptr(l), ptr(u),
+                                     ptr(r), ptr(x), ptr(mask), ptr(ws.info), ctypes.byref(opt), ptr(ws.buf),
+                                     ws.nbytes, stream_handle(stream))
+    check_rc(rc, "cqk_solve_batched")
+    return _batch_finish(host, x, mask, ws, B, sync)
+
+
+def _project_batched(name, y, offsets, r, init, max_iter, lambda0, validate, out, want_mask, ws, stream, sync, kw):
+    host, dev, (y,), offsets, r, B, n = _batch_args([y], offsets, r)
+    x = out if out is not None else torch.empty_like(y)
+    mask = torch.zeros((n + 31) // 32, dtype=torch.int32, device=dev) if want_mask else None
+    ws = ws or Workspace(n, max(B, 1), y.dtype, dev)
+    opt = make_options(init=init, max_iter=max_iter, lambda0=lambda0, validate=validate, **kw)
+    rc = getattr(library(), name)(B, ptr(offsets), dtype_code(y.dtype), ptr(y), ptr(r), ptr(x), ptr(mask),
+                                  ptr(ws.info), ctypes.byref(opt), ptr(ws.buf), ws.nbytes, stream_handle(stream))
+    check_rc(rc, name)
+    return _batch_finish(host, x, mask, ws, B, sync)
+
+
+def project_simplex_batched(y, offsets, r, *, init=Init.CONDAT, max_iter=100, lambda0=0.0, validate=True, out=None,
+                            want_mask=False, ws: Workspace | None = None, stream=None, sync=True, **kw):
+    """B simplex projections in one launch (cqk_project_simplex_batched)."""
+    return _project_batched("cqk_project_simplex_batched", y, offsets, r, init, max_iter, lambda0, validate, out,
+                            want_mask, ws, stream, sync, kw)
+
+
+def project_l1_batched(y, offsets, r, *, init=Init.CONDAT, max_iter=100, lambda0=0.0, validate=True, out=None,
+                       want_mask=False, ws: Workspace | None = None, stream=None, sync=True, **kw):
+    """B l1-ball projections in one launch (cqk_project_l1_batched)."""
+    return _project_batched("cqk_project_l1_batched", y, offsets, r, init, max_iter, lambda0, validate, out,
+                            want_mask, ws, stream, sync, kw)

@@ -24,6 +24,8 @@ Opts resolve_options(const cqk_options* opt, int dtype, int default_init) {
     o.limit_ns = (unsigned long long)(d.spin_limit_us > 0 ? d.spin_limit_us : 2000000) * 1000ull;
     o.max_blocks = d.max_blocks > 0 ? d.max_blocks : 0;
     o.fault_inject = d.fault_inject;
+    o.group_elems = d.group_elems > 0 ? d.group_elems : 0;
+    o.condat_chunk = d.condat_chunk > 0 ? d.condat_chunk : kCondatChunkElems;
     return o;
 }
 
@@ -71,7 +73,8 @@ void cqk_default_options(cqk_options* opt) {
 
 size_t cqk_workspace_bytes(int64_t n_total, int32_t batch, int32_t dtype) {
     if (n_total < 0 || batch < 1 || (dtype != CQK_F64 && dtype != CQK_F32)) return 0;
-    return kSingleWsBytes;
+    const size_t bb = batch_ws_bytes(batch);
+    return bb > kSingleWsBytes ? bb : kSingleWsBytes;
 }
 
 int cqk_solve(int64_t n, int32_t dtype, const void* a, const void* b, const void* d, const void* l, const void* u,
@@ -123,6 +126,49 @@ int cqk_project_simplex(int64_t n, int32_t dtype, const void* y, double r, void*
 int cqk_project_l1(int64_t n, int32_t dtype, const void* y, double r, void* x, uint32_t* free_mask,
                    cqk_info* info_dev, const cqk_options* opt, void* workspace, size_t ws_bytes, void* stream) {
     return project(n, dtype, y, r, x, free_mask, info_dev, opt, workspace, ws_bytes, stream, 1);
+}
+
+static int batched(int32_t B, const int64_t* offsets, int32_t dtype, const void* a, const void* b, const void* d,
+                   const void* l, const void* u, const double* r, void* x, uint32_t* mask, cqk_info* info,
+                   const cqk_options* opt, void* ws, size_t ws_bytes, void* stream, int kind) {
+    // kind: 0 general, 1 simplex, 2 l1 ball
+    if (B < 0 || (dtype != CQK_F64 && dtype != CQK_F32)) return CQK_BAD_ARG;
+    if (B == 0) return CQK_OK;
+    if (!offsets || !a || !r || !x || !info) return CQK_BAD_ARG;
+    if (kind == 0 && (!b || !d || !l || !u)) return CQK_BAD_ARG;
+    if (kind != 0 && x == a) return CQK_BAD_ARG;
+    if (!ws_ok(ws, ws_bytes, batch_ws_bytes(B))) return CQK_BAD_ARG;
+    Opts o = resolve_options(opt, dtype, kind == 0 ? CQK_INIT_FORMULA : CQK_INIT_CONDAT);
+    if (kind == 0) {
+        if (o.init != CQK_INIT_FORMULA && o.init != CQK_INIT_GIVEN) return CQK_BAD_ARG;
+        return launch_general_batched(B, offsets, dtype, a, b, d, l, u, r, x, mask, info, o, ws, (cudaStream_t)stream);
+    }
+    if (o.init != CQK_INIT_FORMULA && o.init != CQK_INIT_CONDAT && o.init != CQK_INIT_GIVEN) return CQK_BAD_ARG;
+    return launch_simplex_batched(B, offsets, dtype, a, r, kind == 2, x, mask, info, o, ws, (cudaStream_t)stream);
+}
+
+int cqk_solve_batched(int32_t B, const int64_t* offsets_dev, int32_t dtype, const void* a, const void* b,
+                      const void* d, const void* l, const void* u, const double* r_dev, void* x, uint32_t* free_mask,
+                      cqk_info* info_dev, const cqk_options* opt, void* workspace, size_t ws_bytes, void* stream) {
+    if (!b && !d && !l && !u)  // simplex batch on y = a (b = d = 1, l = 0, u = +inf)
+        return batched(B, offsets_dev, dtype, a, b, d, l, u, r_dev, x, free_mask, info_dev, opt, workspace, ws_bytes,
+                       stream, 1);
+    return batched(B, offsets_dev, dtype, a, b, d, l, u, r_dev, x, free_mask, info_dev, opt, workspace, ws_bytes, stream,
+                   0);
+}
+
+int cqk_project_simplex_batched(int32_t B, const int64_t* offsets_dev, int32_t dtype, const void* y,
+                                const double* r_dev, void* x, uint32_t* free_mask, cqk_info* info_dev,
+                                const cqk_options* opt, void* workspace, size_t ws_bytes, void* stream) {
+    return batched(B, offsets_dev, dtype, y, nullptr, nullptr, nullptr, nullptr, r_dev, x, free_mask, info_dev, opt,
+                   workspace, ws_bytes, stream, 1);
+}
+
+int cqk_project_l1_batched(int32_t B, const int64_t* offsets_dev, int32_t dtype, const void* y, const double* r_dev,
+                           void* x, uint32_t* free_mask, cqk_info* info_dev, const cqk_options* opt, void* workspace,
+                           size_t ws_bytes, void* stream) {
+    return batched(B, offsets_dev, dtype, y, nullptr, nullptr, nullptr, nullptr, r_dev, x, free_mask, info_dev, opt,
+                   workspace, ws_bytes, stream, 2);
 }
 
 const char* cqk_status_string(int status) {

@@ -48,6 +48,21 @@ struct Grp {
     double* part;
 };
 
+// Barrier of a group at arrival count `target`.  A group of one block needs no device-wide
+// arrival counter: a block barrier around a fence by thread 0 orders the partial sums that
+// thread 0 wrote before it against the reads after it.  `force_grid` keeps the counter
+// (the fault-injection path of the tests).
+__device__ __forceinline__ bool group_barrier(const Grp& gp, unsigned target, unsigned long long limit_ns,
+                                              bool force_grid) {
+    if (gp.g == 1 && !force_grid) {
+        __syncthreads();
+        if (threadIdx.x == 0) __threadfence();
+        __syncthreads();
+        return true;
+    }
+    return grid_barrier(&gp.hdr->bar_count, target, &gp.hdr->error, limit_ns, CQK_TIMEOUT);
+}
+
 // Load the V elements of vector q; elements outside the span get ok = false.  One 128-bit
 // load when the arrays are 16-byte aligned and the vector lies inside the span.
 template <typename T>

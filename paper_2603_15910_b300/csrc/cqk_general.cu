@@ -25,7 +25,7 @@
 // range, exact FP64 per lane otherwise, and FP32 with a df multiplier for FP32 data.
 #include <string.h>
 
-#include "cqk_block.cuh"
+#include "cqk_batch.cuh"
 #include "cqk_stage.cuh"
 
 namespace cqk {
@@ -621,7 +621,7 @@ __device__ __forceinline__ bool lambda0_pass(const GeneralArgs& A, const Grp& gp
 
 #define CQK_BARRIER_OR_LEAVE()                                                  \
     do {                                                                        \
-        if (!grid_barrier(bar, bar_target, err, A.limit_ns, CQK_TIMEOUT)) {     \
+        if (!group_barrier(gp, bar_target, A.limit_ns, A.fault_inject != 0)) {     \
             if (threadIdx.x == 0) A.info->status = CQK_TIMEOUT;                 \
             return;                                                             \
         }                                                                       \
@@ -638,7 +638,6 @@ __device__ __forceinline__ void general_solve(const GeneralArgs& A, const Grp& g
     __shared__ double bc[kPartialQ];
     const int G = gp.g;
     unsigned bar_target = (unsigned)G + (A.fault_inject ? 1u : 0u);
-    unsigned* bar = &gp.hdr->bar_count;
     int* err = &gp.hdr->error;
     const double r = A.r;
     int passes = 0, par = 0;
@@ -882,6 +881,49 @@ __global__ void __launch_bounds__(NT, 2) general_kernel(GeneralArgs A) {
     general_solve<T>(A, gp, reinterpret_cast<T*>(dyn_smem), ring_bars, ring_parity);
 }
 
+// A batch: blocks take (instance, member) slots from the queue until it is empty; the bulk
+// copy stages and their phase bits carry over from one instance to the next.
+struct GeneralBatchArgs {
+    GeneralArgs base;
+    const int64_t* offsets;
+    const double* r;
+    cqk_info* info;
+    int64_t B;
+    BatchRefs R;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(NT, 2) general_batched_kernel(GeneralBatchArgs P) {
+    extern __shared__ __align__(128) unsigned char dyn_smem[];
+    __shared__ uint64_t ring_bars[kStages];
+    unsigned ring_parity = 0;
+    if (P.base.staged) {
+        if (threadIdx.x == 0) {
+            for (int st = 0; st < kStages; st++) mbar_init(&ring_bars[st], 1);
+            fence_barrier_init();
+        }
+        __syncthreads();
+    }
+    while (true) {
+        const Slot sl = next_slot(P.R, P.B);
+        if (sl.inst < 0) break;
+        const Grp gp = slot_group(P.R, P.offsets, sl);
+        GeneralArgs A = P.base;
+        A.r = P.r[sl.inst];
+        A.info = P.info + sl.inst;
+        const int64_t len = gp.sp.hi - gp.sp.lo;
+        if (len <= 0 || A.r != A.r) {
+            // no variable: feasible iff r == 0 (as for a single solve with n = 0)
+            if (sl.member == 0 && threadIdx.x == 0) {
+                if (len < 0 || A.r != A.r) write_plain_info(A.info, CQK_BAD_ARG, CQK_STOP_NONE, A.r);
+                else write_plain_info(A.info, A.r == 0.0 ? CQK_OK : CQK_INFEASIBLE, CQK_STOP_NONE, A.r);
+            }
+            continue;
+        }
+        general_solve<T>(A, gp, reinterpret_cast<T*>(dyn_smem), ring_bars, ring_parity);
+    }
+}
+
 GeneralArgs make_args(int64_t n, const void* a, const void* b, const void* d, const void* l, const void* u, void* x,
                       void* ws, int dtype) {
     GeneralArgs A;
@@ -948,6 +990,54 @@ int launch_general(int64_t n, int dtype, const void* a, const void* b, const voi
     A.limit_ns = o.limit_ns;
     A.fault_inject = o.fault_inject;
     return launch(A, dtype, o.max_blocks, s, ws);
+}
+
+int launch_general_batched(int64_t B, const int64_t* offsets, int dtype, const void* a, const void* b,
+                           const void* d, const void* l, const void* u, const double* r, void* x, uint32_t* mask,
+                           cqk_info* info, const Opts& o, void* ws, cudaStream_t s) {
+    GeneralBatchArgs P;
+    memset(&P, 0, sizeof(P));
+    P.base = make_args(0, a, b, d, l, u, x, ws, dtype);
+    GeneralArgs& A = P.base;
+    A.hdr = nullptr;
+    A.part = nullptr;
+    A.mask = mask;
+    A.init = o.init;
+    A.lambda0 = o.lambda0;
+    A.max_iter = o.max_iter;
+    A.validate = o.validate;
+    A.final_step = o.final_step;
+    A.limit_ns = o.limit_ns;
+    A.fault_inject = o.fault_inject;
+    A.staged = A.aligned;
+    P.offsets = offsets;
+    P.r = r;
+    P.info = info;
+    P.B = B;
+    P.R = BatchRefs::at(ws, B);
+    const void* kern =
+        dtype == CQK_F64 ? (const void*)general_batched_kernel<double> : (const void*)general_batched_kernel<float>;
+    const size_t smem = A.staged ? kStagedSmem : 0;
+    if (smem) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) {
+            set_last_cuda_error(e);
+            return CQK_CUDA_ERROR;
+        }
+    }
+    int grid = persistent_grid(kern, NT, smem, INT64_MAX / 2, o.max_blocks);
+    if (grid <= 0) return CQK_CUDA_ERROR;
+    if ((int64_t)grid > B * kMaxGroup) grid = (int)(B * kMaxGroup);
+    const int64_t per_block = o.group_elems > 0 ? o.group_elems : kGeneralGroupElems;
+    int rc = plan_batch(offsets, B, per_block, grid, ws, s);
+    if (rc != CQK_OK) return rc;
+    void* args[] = {&P};
+    cudaError_t e = cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(NT), args, smem, s);
+    if (e != cudaSuccess) {
+        set_last_cuda_error(e);
+        return CQK_CUDA_ERROR;
+    }
+    return CQK_OK;
 }
 
 int launch_phi(int64_t n, int dtype, const void* a, const void* b, const void* d, const void* l, const void* u,

@@ -40,6 +40,8 @@ struct Opts {
     unsigned long long limit_ns;
     int max_blocks;
     int fault_inject;
+    int64_t group_elems;   // batched calls: one block of an instance's group per this many elements
+    int64_t condat_chunk;  // CQK_INIT_CONDAT: minimum elements per chunk
 };
 
 Opts resolve_options(const cqk_options* opt, int dtype, int default_init);
@@ -52,6 +54,18 @@ int launch_general(int64_t n, int dtype, const void* a, const void* b, const voi
                    void* ws, cudaStream_t s);
 int launch_phi(int64_t n, int dtype, const void* a, const void* b, const void* d, const void* l,
                const void* u, double lambda, void* x, double* out, void* ws, cudaStream_t s);
+
+// batched calls: default elements per block of an instance's group (at most kMaxGroup blocks)
+constexpr int64_t kSimplexGroupElems = 1 << 20;
+constexpr int64_t kGeneralGroupElems = 1 << 16;
+constexpr int64_t kCondatChunkElems = 512;
+size_t batch_ws_bytes(int64_t B);
+int plan_batch(const int64_t* offsets_dev, int64_t B, int64_t per_block, int gmax, void* ws, cudaStream_t s);
+int launch_simplex_batched(int64_t B, const int64_t* offsets, int dtype, const void* y, const double* r, int l1,
+                           void* x, uint32_t* mask, cqk_info* info, const Opts& o, void* ws, cudaStream_t s);
+int launch_general_batched(int64_t B, const int64_t* offsets, int dtype, const void* a, const void* b,
+                           const void* d, const void* l, const void* u, const double* r, void* x, uint32_t* mask,
+                           cqk_info* info, const Opts& o, void* ws, cudaStream_t s);
 
 // number of co-resident blocks for a cooperative kernel, capped by max_blocks and by the work
 int persistent_grid(const void* kernel, int threads, size_t smem, int64_t work_items, int max_blocks);

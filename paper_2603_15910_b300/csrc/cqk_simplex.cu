@@ -21,7 +21,9 @@
 // the threshold for FP32 data); the selected terms y_i + lambda are formed exactly rounded
 // in FP64 (FP64 data, few elements once lambda is near lambda*) or in double-float (FP32
 // data).
-#include "cqk_block.cuh"
+#include <string.h>
+
+#include "cqk_batch.cuh"
 
 namespace cqk {
 namespace {
@@ -48,6 +50,7 @@ struct SimplexArgs {
     int aligned;
     unsigned long long limit_ns;
     int fault_inject;
+    int64_t condat_chunk;  // minimum elements per chunk of the parallel Alg. 2 start
     WsHeader* hdr;
     double* part;  // [2][kPartialQ][gridDim.x]
 };
@@ -111,19 +114,29 @@ __device__ __forceinline__ void condat_slab(const T (&vals)[VecOf<T>::V], const 
     const int lane = threadIdx.x & 31;
     bool pass[V];
     if (first_loop && st.nJ == 0) {
-        // the first element of the chunk starts J unconditionally (first line of Alg. 2)
-        const unsigned any_ok = __ballot_sync(0xffffffffu, okv[0]);
+        // the first element of the chunk (in (lane, j) order; a span may start inside a
+        // vector) starts J unconditionally (first line of Alg. 2)
+        unsigned any_ok = 0, mo[V];
+#pragma unroll
+        for (int j = 0; j < V; j++) {
+            mo[j] = __ballot_sync(0xffffffffu, okv[j]);
+            any_ok |= mo[j];
+        }
         if (!any_ok) return;
         const int L0 = __ffs(any_ok) - 1;
-        double y0 = (double)__shfl_sync(0xffffffffu, vals[0], L0);
+        int j0 = 0;
+#pragma unroll
+        for (int j = V - 1; j >= 0; j--)
+            if ((mo[j] >> L0) & 1u) j0 = j;
+        double y0 = (double)__shfl_sync(0xffffffffu, pick(vals, j0), L0);
         if (L1) y0 = fabs(y0);
         st.S = y0;
         st.nJ = 1;
-        st.rs = __shfl_sync(0xffffffffu, eidx0, L0);
+        st.rs = __shfl_sync(0xffffffffu, eidx0, L0) + j0;
         condat_set_lam<L1>(st, r - y0);
 #pragma unroll
         for (int j = 0; j < V; j++) {
-            const bool after = (lane > L0) || (lane == L0 && j > 0);
+            const bool after = (lane > L0) || (lane == L0 && j > j0);
             pass[j] = okv[j] && after && condat_test<T, L1>(vals[j], st.g, st.rd);
         }
     } else {
@@ -357,8 +370,6 @@ __device__ __forceinline__ void simplex_solve(const SimplexArgs& A, const Grp& g
     const int64_t nwarps = (int64_t)G * NWARP;
     const bool aligned = A.aligned != 0;
     unsigned bar_target = (unsigned)G + (A.fault_inject ? 1u : 0u);
-    unsigned* bar = &gp.hdr->bar_count;
-    int* err = &gp.hdr->error;
     const double r = A.r;
 
     // ------------------------------------------------------------------ pass 0: start
@@ -415,10 +426,13 @@ __device__ __forceinline__ void simplex_solve(const SimplexArgs& A, const Grp& g
             else q[3] = (double)mxf;
             passes++;
         }
+        // chunks of at least condat_chunk elements (the J updates are scalar FP64 work, which
+        // a partition into many small chunks multiplies), at most one per warp
+        const int64_t nchunk = min(nwarps, max((int64_t)1, (n + A.condat_chunk - 1) / A.condat_chunk));
         if (condat) {
             double Sw = 0.0;
             long long nJw = 0;
-            condat_chunk<T, L1>(y, sp, aligned, r, gwarp, nwarps, Sw, nJw);
+            if (gwarp < nchunk) condat_chunk<T, L1>(y, sp, aligned, r, gwarp, nchunk, Sw, nJw);
             q[1] = lane == 0 ? Sw : 0.0;
             q[2] = lane == 0 ? (double)nJw : 0.0;
             passes++;
@@ -446,7 +460,7 @@ __device__ __forceinline__ void simplex_solve(const SimplexArgs& A, const Grp& g
             write_partials<4>(gp.part, gp.member, G, 0, pv);
         }
         __syncthreads();
-        if (!grid_barrier(bar, bar_target, err, A.limit_ns, CQK_TIMEOUT)) {
+        if (!group_barrier(gp, bar_target, A.limit_ns, A.fault_inject != 0)) {
             if (threadIdx.x == 0) A.info->status = CQK_TIMEOUT;
             return;
         }
@@ -456,7 +470,7 @@ __device__ __forceinline__ void simplex_solve(const SimplexArgs& A, const Grp& g
         abs_sum = red[0];
         if (condat) {
             lam0 = (r - red[1]) / red[2];  // eq. (lambdaJ) on the union of the chunks' J
-            nchunks = (int)nwarps;
+            nchunks = (int)nchunk;
             tile = 32 * condat_k<T>() * V;
         } else if (A.init == CQK_INIT_GIVEN) {
             lam0 = fmax(A.lambda0, -red[3]);  // Alg. 4, line 1
@@ -513,7 +527,7 @@ __device__ __forceinline__ void simplex_solve(const SimplexArgs& A, const Grp& g
             if (A.validate && first && __any_sync(0xffffffffu, pa.nan) && lane == 0)
                 atomicOr(&gp.hdr->flags, kFlagBadInput);
             write_pass_partials(gp, par, pa.acc64, pa.cm, pa.ct, sh_d, sh_u);
-            if (!grid_barrier(bar, bar_target, err, A.limit_ns, CQK_TIMEOUT)) {
+            if (!group_barrier(gp, bar_target, A.limit_ns, A.fault_inject != 0)) {
                 if (threadIdx.x == 0) A.info->status = CQK_TIMEOUT;
                 return;
             }
@@ -693,7 +707,86 @@ __global__ void __launch_bounds__(NT, 2) simplex_kernel(SimplexArgs A) {
     simplex_solve<T, L1>(A, gp);
 }
 
+// A batch: blocks take (instance, member) slots from the queue until it is empty; every
+// instance is the span [offsets[i], offsets[i+1]) of y and x, with its own r, info, header
+// and partial sums.
+struct SimplexBatchArgs {
+    SimplexArgs base;
+    const int64_t* offsets;
+    const double* r;
+    cqk_info* info;
+    int64_t B;
+    BatchRefs R;
+};
+
+template <typename T, bool L1>
+__global__ void __launch_bounds__(NT, 2) simplex_batched_kernel(SimplexBatchArgs P) {
+    while (true) {
+        const Slot sl = next_slot(P.R, P.B);
+        if (sl.inst < 0) break;
+        const Grp gp = slot_group(P.R, P.offsets, sl);
+        SimplexArgs A = P.base;
+        A.r = P.r[sl.inst];
+        A.info = P.info + sl.inst;
+        const int64_t len = gp.sp.hi - gp.sp.lo;
+        const bool r_ok = A.r > 0.0 && A.r < INFINITY;
+        if (len <= 0 || !r_ok) {
+            // no element: the simplex {sum x = r > 0} is empty, the l1 ball holds the empty x
+            if (sl.member == 0 && threadIdx.x == 0) {
+                if (len < 0 || !r_ok) write_plain_info(A.info, CQK_BAD_ARG, CQK_STOP_NONE, A.r);
+                else if (L1) write_plain_info(A.info, CQK_OK, CQK_STOP_INSIDE, A.r);
+                else write_plain_info(A.info, CQK_INFEASIBLE, CQK_STOP_NONE, A.r);
+            }
+            continue;
+        }
+        simplex_solve<T, L1>(A, gp);
+    }
+}
+
 }  // namespace
+
+int launch_simplex_batched(int64_t B, const int64_t* offsets, int dtype, const void* y, const double* r, int l1,
+                           void* x, uint32_t* mask, cqk_info* info, const Opts& o, void* ws, cudaStream_t s) {
+    SimplexBatchArgs P;
+    memset(&P, 0, sizeof(P));
+    SimplexArgs& A = P.base;
+    A.y = y;
+    A.x = x;
+    A.mask = mask;
+    A.init = o.init;
+    A.lambda0 = o.lambda0;
+    A.max_iter = o.max_iter;
+    A.eps34 = kEps34F64;
+    A.validate = o.validate;
+    A.final_step = o.final_step;
+    A.limit_ns = o.limit_ns;
+    A.fault_inject = o.fault_inject;
+    A.condat_chunk = o.condat_chunk;
+    A.aligned = ((((uintptr_t)y) | ((uintptr_t)x)) % 16 == 0) ? 1 : 0;
+    P.offsets = offsets;
+    P.r = r;
+    P.info = info;
+    P.B = B;
+    P.R = BatchRefs::at(ws, B);
+    const void* kern;
+    if (dtype == CQK_F64)
+        kern = l1 ? (const void*)simplex_batched_kernel<double, true> : (const void*)simplex_batched_kernel<double, false>;
+    else
+        kern = l1 ? (const void*)simplex_batched_kernel<float, true> : (const void*)simplex_batched_kernel<float, false>;
+    int grid = persistent_grid(kern, NT, 0, INT64_MAX / 2, o.max_blocks);
+    if (grid <= 0) return CQK_CUDA_ERROR;
+    if ((int64_t)grid > B * kMaxGroup) grid = (int)(B * kMaxGroup);
+    const int64_t per_block = o.group_elems > 0 ? o.group_elems : kSimplexGroupElems;
+    int rc = plan_batch(offsets, B, per_block, grid, ws, s);
+    if (rc != CQK_OK) return rc;
+    void* args[] = {&P};
+    cudaError_t e = cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(NT), args, 0, s);
+    if (e != cudaSuccess) {
+        set_last_cuda_error(e);
+        return CQK_CUDA_ERROR;
+    }
+    return CQK_OK;
+}
 
 int launch_simplex(int64_t n, int dtype, const void* y, double r, int l1, void* x, uint32_t* mask,
                    cqk_info* info, const Opts& o, void* ws, cudaStream_t s) {
@@ -712,6 +805,7 @@ int launch_simplex(int64_t n, int dtype, const void* y, double r, int l1, void* 
     A.final_step = o.final_step;
     A.limit_ns = o.limit_ns;
     A.fault_inject = o.fault_inject;
+    A.condat_chunk = o.condat_chunk;
     A.hdr = static_cast<WsHeader*>(ws);
     A.part = reinterpret_cast<double*>(static_cast<char*>(ws) + sizeof(WsHeader));
     A.aligned = ((((uintptr_t)y) | ((uintptr_t)x)) % 16 == 0) ? 1 : 0;
