@@ -225,6 +225,50 @@ int cqk_project_l1_batched(int32_t B, const int64_t* offsets_dev, int32_t dtype,
                            size_t ws_bytes, void* stream);
 
 /*
+ * Adjoint of the solution map (the paper has no backward pass: the formulas below follow
+ * from differentiating its optimality conditions, eq. (xopt) on the free set and
+ * b'x = r).  Given the forward's x, free mask and lambda (info_dev) and an upstream
+ * gradient g, with F the free set, Q = sum_F b_i^2/d_i and mu = sum_F b_i g_i/d_i / Q:
+ *   ga_i = (g_i - mu b_i)/d_i on F, else 0      gd_i = -x_i ga_i
+ *   gb_i = lambda ga_i - mu x_i                 gr   = mu
+ *   gl_i = g_i - mu b_i where x_i sits at l_i, gu_i likewise at u_i, else 0
+ * A variable with l_i = u_i counts as at its lower bound when (a_i + lambda b_i)/d_i <= l_i
+ * (needs a; with a NULL it counts as at the lower bound).
+ *   B, offsets_dev   offsets_dev NULL: one instance of n elements (B must be 1); otherwise
+ *                    B instances as in cqk_solve_batched (n is ignored)
+ *   g, x, b, d       device arrays (required); a nullable; l, u required when free_mask is
+ *                    NULL (F = {l < x < u}) or when gl / gu is requested
+ *   free_mask        nullable: the forward's mask
+ *   info_dev         the forward's info (one per instance): lambda, and for the l1 ball stop
+ *   ga, gb, gd, gl, gu  nullable device outputs (same dtype and length as x)
+ *   gr_dev           nullable device output, one double per instance
+ *   status_dev       nullable device output, one int32 per instance: CQK_OK, CQK_NONDIFF
+ *                    (F empty: mu = 0), CQK_TIMEOUT, or CQK_BAD_ARG (decreasing offsets)
+ *   workspace        cqk_workspace_bytes(n_total, B, dtype) bytes, 256-byte aligned
+ * Two passes over the data: a reduction for (sum_F b g/d, Q) and the map.  FP64 arithmetic.
+ */
+int cqk_backward(int32_t B, const int64_t* offsets_dev, int64_t n, int32_t dtype, const void* g,
+                 const void* x, const void* a, const void* b, const void* d, const void* l,
+                 const void* u, const uint32_t* free_mask, const cqk_info* info_dev, void* ga,
+                 void* gb, void* gd, void* gl, void* gu, double* gr_dev, int32_t* status_dev,
+                 const cqk_options* opt, void* workspace, size_t ws_bytes, void* stream);
+
+/* Simplex projection adjoint: with F = {x > 0} (or the mask), gy_i = g_i - mean_F(g) on F,
+ * else 0; gr = mean_F(g).  Arguments as cqk_backward. */
+int cqk_backward_simplex(int32_t B, const int64_t* offsets_dev, int64_t n, int32_t dtype,
+                         const void* g, const void* x, const uint32_t* free_mask,
+                         const cqk_info* info_dev, void* gy, double* gr_dev, int32_t* status_dev,
+                         const cqk_options* opt, void* workspace, size_t ws_bytes, void* stream);
+
+/* l1-ball projection adjoint (Lemma 3.2): y inside the ball (info stop CQK_STOP_INSIDE):
+ * gy = g, gr = 0; otherwise, with s = sgn(x) and F = {x != 0} (or the mask),
+ * gy_i = g_i - s_i mean_F(s g) on F, else 0; gr = mean_F(s g). */
+int cqk_backward_l1(int32_t B, const int64_t* offsets_dev, int64_t n, int32_t dtype, const void* g,
+                    const void* x, const uint32_t* free_mask, const cqk_info* info_dev, void* gy,
+                    double* gr_dev, int32_t* status_dev, const cqk_options* opt, void* workspace,
+                    size_t ws_bytes, void* stream);
+
+/*
  * Allocation-free variant of cqk_project_simplex (the paper has no counterpart: this is a
  * calling convenience of this library).
  *

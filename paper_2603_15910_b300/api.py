@@ -137,6 +137,13 @@ def library():
             f = getattr(lib, name)
             f.argtypes = [i32, vp, i32, vp, vp, vp, vp, vp, ctypes.POINTER(_Options), vp, sz, vp]
             f.restype = ctypes.c_int
+        lib.cqk_backward.argtypes = [i32, vp, i64, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp,
+                                     ctypes.POINTER(_Options), vp, sz, vp]
+        lib.cqk_backward.restype = ctypes.c_int
+        for name in ("cqk_backward_simplex", "cqk_backward_l1"):
+            f = getattr(lib, name)
+            f.argtypes = [i32, vp, i64, i32, vp, vp, vp, vp, vp, vp, vp, ctypes.POINTER(_Options), vp, sz, vp]
+            f.restype = ctypes.c_int
         lib.cqk_status_string.argtypes = [ctypes.c_int]
         lib.cqk_status_string.restype = ctypes.c_char_p
         lib.cqk_last_cuda_error.argtypes = []
@@ -369,3 +376,41 @@ def project_l1_batched(y, offsets, r, *, init=Init.CONDAT, max_iter=100, lambda0
     """B l1-ball projections in one launch (cqk_project_l1_batched)."""
     return _project_batched("cqk_project_l1_batched", y, offsets, r, init, max_iter, lambda0, validate, out,
                             want_mask, ws, stream, sync, kw)
+
+
+def backward(kind, g, x, info, *, a=None, b=None, d=None, l=None, u=None, mask=None, offsets=None,
+             want=("a", "b", "d", "l", "u"), ws: Workspace | None = None, stream=None, **kw):
+    """Adjoint of a solve (cqk_backward, cqk_backward_simplex, cqk_backward_l1).
+
+    kind: "general", "simplex" or "l1".  g, x (and a, b, d, l, u for "general") are device
+    tensors of one dtype; info is the forward's info buffer (the Workspace.info tensor or a
+    copy of it, one cqk_info per instance); offsets (device int64, B + 1) selects a batch.
+    Returns dict with the requested gradients ("a".."u"; "y" for the projections), "r"
+    (float64 tensor, one per instance) and "status" (int32 tensor).  No host synchronisation."""
+    _check_device(g, x)
+    n = x.numel()
+    B = 1 if offsets is None else offsets.numel() - 1
+    out = {}
+    gr = torch.empty(max(B, 1), dtype=torch.float64, device=x.device)
+    status = torch.empty(max(B, 1), dtype=torch.int32, device=x.device)
+    ws = ws or Workspace(n, max(B, 1), x.dtype, x.device)
+    opt = make_options(**kw)
+    lib = library()
+    if kind == "general":
+        for k in ("a", "b", "d", "l", "u"):
+            out[k] = torch.empty_like(x) if k in want else None
+        rc = lib.cqk_backward(B, ptr(offsets), n, dtype_code(x.dtype), ptr(g), ptr(x), ptr(a), ptr(b), ptr(d), ptr(l),
+                              ptr(u), ptr(mask), ptr(info), ptr(out["a"]), ptr(out["b"]), ptr(out["d"]), ptr(out["l"]),
+                              ptr(out["u"]), ptr(gr), ptr(status), ctypes.byref(opt), ptr(ws.buf), ws.nbytes,
+                              stream_handle(stream))
+        name = "cqk_backward"
+    else:
+        name = "cqk_backward_simplex" if kind == "simplex" else "cqk_backward_l1"
+        out["y"] = torch.empty_like(x)
+        rc = getattr(lib, name)(B, ptr(offsets), n, dtype_code(x.dtype), ptr(g), ptr(x), ptr(mask), ptr(info),
+                                ptr(out["y"]), ptr(gr), ptr(status), ctypes.byref(opt), ptr(ws.buf), ws.nbytes,
+                                stream_handle(stream))
+    check_rc(rc, name)
+    out["r"] = gr
+    out["status"] = status
+    return out

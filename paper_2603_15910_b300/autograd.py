@@ -1,0 +1,106 @@
+"""Differentiable solves: ``torch.autograd.Function`` wrappers whose forward is the library's
+solve (single or batched) and whose backward is the library's adjoint kernel
+(cqk_backward*), reusing the forward's x, free mask and multiplier (the info buffer).
+
+    x = cqk_solve(a, b, d, l, u, r)                       # gradients in a, b, d, l, u, r
+    x = simplex_projection(y, r)                          # gradients in y, r
+    x = l1_projection(y, r)
+    x = simplex_projection(y, r, offsets=off)             # ragged batch; r has one entry per instance
+
+Nothing runs on the CPU: the forward and backward are kernels of libcqk.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import api
+
+
+def _r_tensor(r, B, device):
+    if torch.is_tensor(r):
+        return r
+    return torch.full((B,), float(r), dtype=torch.float64, device=device) if B > 1 else torch.tensor(float(r),
+                                                                                                      dtype=torch.float64)
+
+
+def _r_grad(gr, r):
+    """Per-instance dr (float64, device) shaped and typed like r."""
+    if r.dim() == 0:
+        g = gr[0].reshape(())
+    else:
+        g = gr[: r.numel()].reshape(r.shape)
+    return g.to(device=r.device, dtype=r.dtype)
+
+
+def _forward_info(n, B, dtype, device):
+    ws = api.Workspace(n, max(B, 1), dtype, device)
+    return ws
+
+
+class _Solve(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, a, b, d, l, u, r, offsets, opts):
+        ws = _forward_info(a.numel(), 1 if offsets is None else offsets.numel() - 1, a.dtype, a.device)
+        if offsets is None:
+            x, _, mask = api.solve(a, b, d, l, u, float(r), want_mask=True, ws=ws, sync=False, **opts)
+        else:
+            x, _, mask = api.solve_batched(a, b, d, l, u, offsets, r.to(a.device), want_mask=True, ws=ws,
+                                           sync=False, **opts)
+        ctx.ws = ws
+        ctx.save_for_backward(a, b, d, l, u, r, x, mask, ws.info, offsets if offsets is not None else a.new_empty(0))
+        ctx.batched = offsets is not None
+        return x
+
+    @staticmethod
+    def backward(ctx, gx):
+        a, b, d, l, u, r, x, mask, info, offsets = ctx.saved_tensors
+        want = tuple(k for k, need in zip("abdlu", ctx.needs_input_grad[:5]) if need)
+        out = api.backward("general", gx.contiguous(), x, info, a=a, b=b, d=d, l=l, u=u, mask=mask,
+                           offsets=offsets if ctx.batched else None, want=want, ws=ctx.ws)
+        gr = _r_grad(out["r"], r) if ctx.needs_input_grad[5] else None
+        return out.get("a"), out.get("b"), out.get("d"), out.get("l"), out.get("u"), gr, None, None
+
+
+class _Project(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, y, r, offsets, l1, opts):
+        B = 1 if offsets is None else offsets.numel() - 1
+        ws = _forward_info(y.numel(), B, y.dtype, y.device)
+        if offsets is None:
+            fn = api.project_l1 if l1 else api.project_simplex
+            x, _, mask = fn(y, float(r), want_mask=True, ws=ws, sync=False, **opts)
+        else:
+            fn = api.project_l1_batched if l1 else api.project_simplex_batched
+            x, _, mask = fn(y, offsets, r.to(y.device), want_mask=True, ws=ws, sync=False, **opts)
+        ctx.ws = ws
+        ctx.l1 = l1
+        ctx.batched = offsets is not None
+        ctx.save_for_backward(r, x, mask, ws.info, offsets if offsets is not None else y.new_empty(0))
+        return x
+
+    @staticmethod
+    def backward(ctx, gx):
+        r, x, mask, info, offsets = ctx.saved_tensors
+        out = api.backward("l1" if ctx.l1 else "simplex", gx.contiguous(), x, info, mask=mask,
+                           offsets=offsets if ctx.batched else None, ws=ctx.ws)
+        gr = _r_grad(out["r"], r) if ctx.needs_input_grad[1] else None
+        return out["y"], gr, None, None, None
+
+
+def cqk_solve(a, b, d, l, u, r, offsets=None, **opts):
+    """x*(a, b, d, l, u, r) of (CQK), differentiable in every argument.  With offsets (device
+    int64, B + 1 entries) the arrays hold B instances and r has B entries."""
+    B = 1 if offsets is None else offsets.numel() - 1
+    return _Solve.apply(a, b, d, l, u, _r_tensor(r, B, a.device), offsets, opts)
+
+
+def simplex_projection(y, r=1.0, offsets=None, **opts):
+    """Projection onto {x >= 0, sum x = r}, differentiable in y and r."""
+    B = 1 if offsets is None else offsets.numel() - 1
+    return _Project.apply(y, _r_tensor(r, B, y.device), offsets, False, opts)
+
+
+def l1_projection(y, r=1.0, offsets=None, **opts):
+    """Projection onto {sum |x_i| <= r}, differentiable in y and r."""
+    B = 1 if offsets is None else offsets.numel() - 1
+    return _Project.apply(y, _r_tensor(r, B, y.device), offsets, True, opts)

@@ -171,6 +171,49 @@ int cqk_project_l1_batched(int32_t B, const int64_t* offsets_dev, int32_t dtype,
                    workspace, ws_bytes, stream, 2);
 }
 
+static int backward(int kind, int32_t B, const int64_t* offsets, int64_t n, int32_t dtype, const void* g,
+                    const void* x, const void* a, const void* b, const void* d, const void* l, const void* u,
+                    const uint32_t* mask, const cqk_info* info, void* ga, void* gb, void* gd, void* gl, void* gu,
+                    double* gr, int32_t* status, const cqk_options* opt, void* ws, size_t ws_bytes, void* stream) {
+    if (B < 0 || (dtype != CQK_F64 && dtype != CQK_F32) || !info) return CQK_BAD_ARG;
+    if (!offsets && (B != 1 || n < 0)) return CQK_BAD_ARG;
+    if (B == 0 || (!offsets && n == 0)) return CQK_OK;
+    if (!g || !x) return CQK_BAD_ARG;
+    if (kind == 0 && (!b || !d)) return CQK_BAD_ARG;
+    if (kind == 0 && (!mask || gl || gu) && (!l || !u)) return CQK_BAD_ARG;
+    const size_t need = offsets ? batch_ws_bytes(B) : kSingleWsBytes;
+    if (!ws_ok(ws, ws_bytes, need)) return CQK_BAD_ARG;
+    Opts o = resolve_options(opt, dtype, CQK_INIT_FORMULA);
+    return launch_backward(kind, B, offsets, n, dtype, g, x, a, b, d, l, u, mask, info, ga, gb, gd, gl, gu, gr,
+                           status, o, ws, (cudaStream_t)stream);
+}
+
+int cqk_backward(int32_t B, const int64_t* offsets_dev, int64_t n, int32_t dtype, const void* g, const void* x,
+                 const void* a, const void* b, const void* d, const void* l, const void* u,
+                 const uint32_t* free_mask, const cqk_info* info_dev, void* ga, void* gb, void* gd, void* gl,
+                 void* gu, double* gr_dev, int32_t* status_dev, const cqk_options* opt, void* workspace,
+                 size_t ws_bytes, void* stream) {
+    return backward(0, B, offsets_dev, n, dtype, g, x, a, b, d, l, u, free_mask, info_dev, ga, gb, gd, gl, gu, gr_dev,
+                    status_dev, opt, workspace, ws_bytes, stream);
+}
+
+int cqk_backward_simplex(int32_t B, const int64_t* offsets_dev, int64_t n, int32_t dtype, const void* g,
+                         const void* x, const uint32_t* free_mask, const cqk_info* info_dev, void* gy,
+                         double* gr_dev, int32_t* status_dev, const cqk_options* opt, void* workspace,
+                         size_t ws_bytes, void* stream) {
+    return backward(1, B, offsets_dev, n, dtype, g, x, nullptr, nullptr, nullptr, nullptr, nullptr, free_mask,
+                    info_dev, gy, nullptr, nullptr, nullptr, nullptr, gr_dev, status_dev, opt, workspace, ws_bytes,
+                    stream);
+}
+
+int cqk_backward_l1(int32_t B, const int64_t* offsets_dev, int64_t n, int32_t dtype, const void* g, const void* x,
+                    const uint32_t* free_mask, const cqk_info* info_dev, void* gy, double* gr_dev,
+                    int32_t* status_dev, const cqk_options* opt, void* workspace, size_t ws_bytes, void* stream) {
+    return backward(2, B, offsets_dev, n, dtype, g, x, nullptr, nullptr, nullptr, nullptr, nullptr, free_mask,
+                    info_dev, gy, nullptr, nullptr, nullptr, nullptr, gr_dev, status_dev, opt, workspace, ws_bytes,
+                    stream);
+}
+
 const char* cqk_status_string(int status) {
     switch (status) {
         case CQK_OK: return "ok";

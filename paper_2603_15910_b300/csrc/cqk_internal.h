@@ -59,6 +59,7 @@ int launch_phi(int64_t n, int dtype, const void* a, const void* b, const void* d
 constexpr int64_t kSimplexGroupElems = 1 << 20;
 constexpr int64_t kGeneralGroupElems = 1 << 16;
 constexpr int64_t kCondatChunkElems = 512;
+constexpr int64_t kBackwardGroupElems = 1 << 18;
 size_t batch_ws_bytes(int64_t B);
 int plan_batch(const int64_t* offsets_dev, int64_t B, int64_t per_block, int gmax, void* ws, cudaStream_t s);
 int launch_simplex_batched(int64_t B, const int64_t* offsets, int dtype, const void* y, const double* r, int l1,
@@ -66,6 +67,12 @@ int launch_simplex_batched(int64_t B, const int64_t* offsets, int dtype, const v
 int launch_general_batched(int64_t B, const int64_t* offsets, int dtype, const void* a, const void* b,
                            const void* d, const void* l, const void* u, const double* r, void* x, uint32_t* mask,
                            cqk_info* info, const Opts& o, void* ws, cudaStream_t s);
+
+// backward (kind 0 general, 1 simplex, 2 l1 ball); offsets == nullptr: one instance of n
+int launch_backward(int kind, int64_t B, const int64_t* offsets, int64_t n, int dtype, const void* g, const void* x,
+                    const void* a, const void* b, const void* d, const void* l, const void* u, const uint32_t* mask,
+                    const cqk_info* info, void* ga, void* gb, void* gd, void* gl, void* gu, double* gr,
+                    int32_t* status, const Opts& o, void* ws, cudaStream_t s);
 
 // number of co-resident blocks for a cooperative kernel, capped by max_blocks and by the work
 int persistent_grid(const void* kernel, int threads, size_t smem, int64_t work_items, int max_blocks);
