@@ -181,7 +181,7 @@ __device__ __forceinline__ void put(X (&a)[N], int j, X v) {
         if (t == j) a[t] = v;
 }
 
-__device__ __forceinline__ unsigned long long bits_of(double v) { return (unsigned long long)__double_as_longlong(v); }
+__device__ __forceinline__ unsigned long long bits_of(double v) { return opaque_bits(v); }
 
 // Sum NQ doubles over the block (fixed order); result valid in thread 0.
 template <int NQ>

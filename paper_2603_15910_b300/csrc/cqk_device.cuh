@@ -20,6 +20,26 @@
 namespace cqk {
 
 // ------------------------------------------------------------------------------------------
+// The words of a double as opaque integers.  Bit tests written on __double_as_longlong are
+// recognised by the compiler as floating-point classifications and emitted as FP64
+// instructions, the scarcest unit of this GPU; a move through inline PTX hides the origin of
+// the bits so that the tests below stay on the integer pipe.
+__device__ __forceinline__ unsigned hi_word(double x) {
+    unsigned h;
+    asm("mov.b32 %0, %1;" : "=r"(h) : "r"(__double2hiint(x)));
+    return h;
+}
+__device__ __forceinline__ unsigned lo_word(double x) {
+    unsigned l;
+    asm("mov.b32 %0, %1;" : "=r"(l) : "r"(__double2loint(x)));
+    return l;
+}
+__device__ __forceinline__ unsigned long long opaque_bits(double x) {
+    unsigned long long b;
+    asm("mov.b64 %0, %1;" : "=l"(b) : "l"(__double_as_longlong(x)));
+    return b;
+}
+
 // double-float arithmetic (round to nearest; never contracted: the library is compiled with
 // -fmad=false and fused operations are written as explicit fmaf)
 struct df {
@@ -184,8 +204,8 @@ __device__ __forceinline__ double lazy_value(LazyDf a) { return (double)a.hi + (
 
 // true iff x is 0, +-inf (when allow_inf) or a finite value with 2^-60 <= |x| <= 2^60
 __device__ __forceinline__ bool df_in_range(double x, bool allow_inf) {
-    unsigned hi = (unsigned)__double2hiint(x);
-    unsigned lo = (unsigned)__double2loint(x);
+    unsigned hi = hi_word(x);
+    unsigned lo = lo_word(x);
     unsigned e = (hi >> 20) & 0x7FFu;
     bool zero = ((hi & 0x7FFFFFFFu) | lo) == 0u;
     bool inf = allow_inf && ((hi & 0x7FFFFFFFu) == 0x7FF00000u) && (lo == 0u);
@@ -215,7 +235,7 @@ __device__ __forceinline__ bool gt_bits(unsigned long long ybits, const GtThresh
 // Order-preserving integer key of a double (non-NaN): x < y  <=>  key(x) < key(y) (as signed
 // 64-bit integers; -0 and +0 map to adjacent keys).  Used for max/min without FP64 instructions.
 __device__ __forceinline__ long long order_key(double x) {
-    const long long b = __double_as_longlong(x);
+    const long long b = (long long)opaque_bits(x);
     return b >= 0 ? b : (long long)(0x8000000000000000ull - (unsigned long long)b) - 1;
 }
 __device__ __forceinline__ double from_order_key(long long k) {
@@ -223,16 +243,19 @@ __device__ __forceinline__ double from_order_key(long long k) {
 }
 
 // FP64 classification on the bit pattern (integer pipe).
+__device__ __forceinline__ bool u64_is_nan(unsigned long long b) {
+    const unsigned h = (unsigned)(b >> 32) & 0x7FFFFFFFu, l = (unsigned)b;
+    return (h > 0x7FF00000u) | ((h == 0x7FF00000u) & (l != 0u));
+}
 __device__ __forceinline__ bool f64_is_nan(double x) {
-    return ((unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull) > 0x7FF0000000000000ull;
+    const unsigned h = hi_word(x) & 0x7FFFFFFFu;
+    return (h > 0x7FF00000u) | ((h == 0x7FF00000u) & (lo_word(x) != 0u));
 }
-__device__ __forceinline__ bool f64_is_finite(double x) {
-    return ((unsigned)__double2hiint(x) & 0x7FF00000u) != 0x7FF00000u;
-}
+__device__ __forceinline__ bool f64_is_finite(double x) { return (hi_word(x) & 0x7FF00000u) != 0x7FF00000u; }
 // finite and > 0
 __device__ __forceinline__ bool f64_pos_finite(double x) {
-    const long long b = __double_as_longlong(x);
-    return b > 0 && b < 0x7FF0000000000000ll;
+    const unsigned h = hi_word(x);
+    return ((int)h >= 0) & (h < 0x7FF00000u) & ((h | lo_word(x)) != 0u);
 }
 
 // Largest float <= c: for a float y, y > c  <=>  y > rd(c).

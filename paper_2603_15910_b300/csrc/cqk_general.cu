@@ -242,10 +242,10 @@ __device__ __forceinline__ void eval_vec(const GeneralArgs& A, const T (&va)[Vec
                     // a 0 or in range; l, u 0, +-inf or in range.  In-range values are finite and
                     // not NaN, so of the sanity checks only l <= u remains for them; elements
                     // outside the range take the exact path, which checks everything.
-                    const unsigned hb = (unsigned)__double2hiint(b), hd = (unsigned)__double2hiint(d);
-                    const unsigned ha = (unsigned)__double2hiint(a), la = (unsigned)__double2loint(a);
-                    const unsigned hl = (unsigned)__double2hiint(l), ll = (unsigned)__double2loint(l);
-                    const unsigned hu = (unsigned)__double2hiint(u), lu = (unsigned)__double2loint(u);
+                    const unsigned hb = hi_word(b), hd = hi_word(d);
+                    const unsigned ha = hi_word(a), la = lo_word(a);
+                    const unsigned hl = hi_word(l), ll = lo_word(l);
+                    const unsigned hu = hi_word(u), lu = lo_word(u);
                     auto rng = [](unsigned h) { return (((h >> 20) & 0x7FFu) - 963u) <= 120u; };
                     auto zero = [](unsigned h, unsigned lo) { return ((h & 0x7FFFFFFFu) | lo) == 0u; };
                     auto inf = [](unsigned h, unsigned lo) { return (h & 0x7FFFFFFFu) == 0x7FF00000u && lo == 0u; };
@@ -498,9 +498,8 @@ __device__ __forceinline__ void lambda0_vec(const T (&va)[VecOf<T>::V], const T 
         const T a = va[j], b = vb[j], d = vd[j];
         if constexpr (sizeof(T) == 8) {
             // b, d positive in [2^-60, 2^60], a zero or in that range (exponent-field tests)
-            const unsigned ha = (unsigned)__double2hiint(a), la = (unsigned)__double2loint(a);
-            const bool inr = (((unsigned)__double2hiint(b) >> 20) - 963u) <= 120u &&
-                             (((unsigned)__double2hiint(d) >> 20) - 963u) <= 120u &&
+            const unsigned ha = hi_word(a), la = lo_word(a);
+            const bool inr = ((hi_word(b) >> 20) - 963u) <= 120u && ((hi_word(d) >> 20) - 963u) <= 120u &&
                              ((((ha >> 20) & 0x7FFu) - 963u) <= 120u || ((ha & 0x7FFFFFFFu) | la) == 0u);
             const df B = split_f64_finite(b), D = split_f64_finite(d);
             const float r0 = rcp_approx(D.hi);

@@ -279,7 +279,7 @@ __device__ __forceinline__ void newton_sweep(const T* __restrict__ y, const Span
                 sel = NEG ? (b < tb) : ((long long)b > (long long)tb);
                 if (FIRST) {
                     tie = !sel && (b == tb || ((b | tb) << 1) == 0ull);
-                    nan = (b & 0x7FFFFFFFFFFFFFFFull) > 0x7FF0000000000000ull;
+                    nan = u64_is_nan(b);
                 }
             } else {
                 const float f = L1 ? fabsf((float)vv[u][j]) : (float)vv[u][j];
@@ -302,7 +302,9 @@ __device__ __forceinline__ void newton_sweep(const T* __restrict__ y, const Span
         for (unsigned m = selm; m; m &= m - 1) {
             const T tv = pick2(vv, __ffs(m) - 1);
             if constexpr (sizeof(T) == 8) {
-                pa.acc64 += (L1 ? fabs((double)tv) : (double)tv) + lam;
+                // |y| by clearing the sign bit (an integer operation, not an FP64 one)
+                const double ya = L1 ? __longlong_as_double((long long)(bits_of(tv) & 0x7FFFFFFFFFFFFFFFull)) : (double)tv;
+                pa.acc64 += ya + lam;
             } else {
                 pa.acc32 = df_add(pa.acc32, df_add_f(Lm, L1 ? fabsf((float)tv) : (float)tv));
             }
@@ -381,7 +383,9 @@ __device__ __forceinline__ void simplex_solve(const SimplexArgs& A, const Grp& g
         const bool sum_pass = L1 || !condat;
         bool bad = false;
         if (sum_pass) {
-            df acc = df_make(0.0f);
+            df acc = df_make(0.0f);       // FP32 data
+            LazyDf lz{0.0f, 0.0f};        // FP64 data in the df operating range, flushed into acc64
+            double acc64 = 0.0;
             double acc_wide = 0.0;  // FP64 values outside the df operating range
             long long mxk = order_key(-INFINITY);
             float mxf = -INFINITY;
@@ -398,10 +402,11 @@ __device__ __forceinline__ void simplex_solve(const SimplexArgs& A, const Grp& g
                     const int u = uj / V, j = uj % V;
                     if (!okk[u][j]) continue;
                     if constexpr (sizeof(T) == 8) {
-                        const double t = L1 ? __longlong_as_double(__double_as_longlong(vv[u][j]) & 0x7FFFFFFFFFFFFFFFll)
+                        const double t = L1 ? __longlong_as_double((long long)(bits_of(vv[u][j]) & 0x7FFFFFFFFFFFFFFFull))
                                             : (double)vv[u][j];
                         const bool inr = df_in_range(t, false);
-                        acc = df_add(acc, inr ? split_f64(t) : df_make(0.0f));
+                        const df st = split_f64_finite(t);
+                        lazy_add(lz, df{inr ? st.hi : 0.0f, inr ? st.lo : 0.0f});
                         widem |= (inr ? 0u : 1u) << uj;
                         bad |= f64_is_nan(t);
                         const long long kk = order_key(t);
@@ -419,9 +424,15 @@ __device__ __forceinline__ void simplex_solve(const SimplexArgs& A, const Grp& g
                         const T tv = pick2(vv, __ffs(m) - 1);
                         acc_wide += L1 ? fabs((double)tv) : (double)tv;
                     }
+                    // fold the lazy pair (at most 64 terms) into FP64: one FP64 add per 4 sweeps
+                    if ((it & 3) == 3) {
+                        acc64 += df_to_f64_int(df{lz.hi, lz.lo});
+                        lz = LazyDf{0.0f, 0.0f};
+                    }
                 }
             }
-            q[0] = df_to_f64(acc) + acc_wide;
+            if constexpr (sizeof(T) == 8) acc64 += df_to_f64_int(df{lz.hi, lz.lo});
+            q[0] = df_to_f64(acc) + acc64 + acc_wide;
             if constexpr (sizeof(T) == 8) q[3] = from_order_key(mxk);
             else q[3] = (double)mxf;
             passes++;
@@ -655,11 +666,14 @@ __device__ __forceinline__ void simplex_solve(const SimplexArgs& A, const Grp& g
                     const int j = __ffs(m) - 1;
                     const T vj = pick(v, j);
                     if constexpr (sizeof(T) == 8) {
-                        const double yv = (double)vj;
-                        double xv = (L1 ? fabs(yv) : yv) + lamf;
-                        if (L1 && yv < 0.0) xv = -xv;
+                        // |x_i| = |y_i| + lambda > 0; the l1 ball copies the sign of y_i (bit operations)
+                        const unsigned long long yb = bits_of((double)vj);
+                        const double xm =
+                            (L1 ? __longlong_as_double((long long)(yb & 0x7FFFFFFFFFFFFFFFull)) : (double)vj) + lamf;
+                        const double xv =
+                            L1 ? __longlong_as_double((long long)(bits_of(xm) | (yb & 0x8000000000000000ull))) : xm;
                         put(o, j, (T)xv);
-                        sx += fabs(xv);
+                        sx += xm;
                     } else {
                         const float f = (float)vj;
                         const df t = df_add_f(Lm, L1 ? fabsf(f) : f);
