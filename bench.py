@@ -55,6 +55,41 @@ def measured_peak_hbm():
 
 
 # ------------------------------------------------------------------------------ clocks
+class _NvmlCtypes:
+    """Read-only NVML queries through the driver's libnvidia-ml (SM clock, its maximum and
+    the clock-event reason bits), for images without the pynvml module."""
+
+    NVML_CLOCK_SM = 1
+
+    def __init__(self, bus):
+        import ctypes
+        self.ct = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        rc = self.lib.nvmlInit_v2()
+        if rc != 0:
+            raise RuntimeError(f"nvmlInit_v2 -> {rc}")
+        self.h = ctypes.c_void_p()
+        rc = self.lib.nvmlDeviceGetHandleByPciBusId_v2(bus.encode(), ctypes.byref(self.h))
+        if rc != 0:
+            raise RuntimeError(f"nvmlDeviceGetHandleByPciBusId_v2 -> {rc}")
+        self.reasons_fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+
+    def max_sm(self):
+        v = self.ct.c_uint()
+        rc = self.lib.nvmlDeviceGetMaxClockInfo(self.h, self.NVML_CLOCK_SM, self.ct.byref(v))
+        return v.value if rc == 0 else None
+
+    def sample(self):
+        v = self.ct.c_uint()
+        r = self.ct.c_ulonglong()
+        rc1 = self.lib.nvmlDeviceGetClockInfo(self.h, self.NVML_CLOCK_SM, self.ct.byref(v))
+        rc2 = self.reasons_fn(self.h, self.ct.byref(r))
+        if rc1 != 0 or rc2 != 0:
+            raise RuntimeError(f"nvml query -> {rc1}, {rc2}")
+        return v.value, r.value
+
+
 class ClockSampler:
     """Samples the SM clock and the clock-event reasons of the CUDA device while running:
     NVML addressed by the device's PCI bus id, or `nvidia-smi -lms` when NVML is unusable."""
@@ -73,12 +108,18 @@ class ClockSampler:
         p = torch.cuda.get_device_properties(cuda_index)
         self.bus = f"{p.pci_domain_id:08X}:{p.pci_bus_id:02X}:{p.pci_device_id:02X}.0"
         try:
-            import pynvml
-            pynvml.nvmlInit()
-            self.nv = pynvml
-            self.h = pynvml.nvmlDeviceGetHandleByPciBusId(self.bus.encode())
-            self.max_mhz = pynvml.nvmlDeviceGetMaxClockInfo(self.h, pynvml.NVML_CLOCK_SM)
-            self.source = "nvml"
+            try:
+                import pynvml
+                pynvml.nvmlInit()
+                self.nv = pynvml
+                self.h = pynvml.nvmlDeviceGetHandleByPciBusId(self.bus.encode())
+                self.max_mhz = pynvml.nvmlDeviceGetMaxClockInfo(self.h, pynvml.NVML_CLOCK_SM)
+                self.source = "nvml"
+            except ImportError:
+                self.nv = _NvmlCtypes(self.bus)
+                self.h = None
+                self.max_mhz = self.nv.max_sm()
+                self.source = "nvml (libnvidia-ml via ctypes)"
         except Exception as e:  # noqa: BLE001
             self.nv = None
             self.error = f"nvml: {type(e).__name__}: {e}"
@@ -86,12 +127,16 @@ class ClockSampler:
     def _run(self):
         while not self._stop.is_set():
             try:
-                self.samples.append(self.nv.nvmlDeviceGetClockInfo(self.h, self.nv.NVML_CLOCK_SM))
-                bits = self.nv.nvmlDeviceGetCurrentClocksEventReasons(self.h)
+                if isinstance(self.nv, _NvmlCtypes):
+                    clk, bits = self.nv.sample()
+                else:
+                    clk = self.nv.nvmlDeviceGetClockInfo(self.h, self.nv.NVML_CLOCK_SM)
+                    bits = self.nv.nvmlDeviceGetCurrentClocksEventReasons(self.h)
+                self.samples.append(clk)
                 self._bits(bits)
             except Exception as e:  # noqa: BLE001
                 self.error = f"nvml sample: {type(e).__name__}: {e}"
-            time.sleep(0.02)
+            time.sleep(0.002)
 
     def _bits(self, bits):
         for b, name in self.REASONS.items():
@@ -138,6 +183,35 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------------ our arm
+def kernel_sources_sha256():
+    import glob
+    import hashlib
+    pkg = os.path.join(ROOT, "paper_2603_15910_b300", "csrc")
+    files = sorted(glob.glob(os.path.join(pkg, "*.cu")) + glob.glob(os.path.join(pkg, "*.cuh")) +
+                   glob.glob(os.path.join(pkg, "*.h"))) + [os.path.join(ROOT, "include", "cqk.h")]
+    h = hashlib.sha256()
+    for f in files:
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic(n):
+    """DRAM bytes of the step's two launches from the committed ncu summary, if it was taken on
+    these kernel sources at this size; else None."""
+    path = os.path.join(ROOT, "profiles", "simplex_kernel_f64_n1e8_dram.md")
+    try:
+        with open(path) as f:
+            line = next(ln for ln in f if "traffic_json:" in ln)
+        rec = json.loads(line.split("traffic_json:", 1)[1])
+    except Exception:  # noqa: BLE001
+        return None
+    if n != N_DEFAULT or rec.get("sources_sha256") != kernel_sources_sha256():
+        return None
+    return rec["bytes_per_step"]
+
+
 def algorithmic_bytes_projection(n, elem_bytes, info):
     """Bytes one projection must move: every read pass streams y once, the final pass
     also writes x (info.passes counts the start, Newton and final passes)."""
@@ -219,7 +293,8 @@ def run_ours(args, world, rank, local):
                    "iters_l1": i2.iters, "passes_simplex": i1.passes, "passes_l1": i2.passes,
                    "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (800 MB per vector)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "kernel": "simplex_kernel<double> (simplex + l1 launches)",
+                     "traffic": measured_traffic(n), "traffic_unit": "bytes per step (both launches), ncu",
+                     "kernel": "simplex_kernel<double> (simplex + l1 launches)",
                      "peak_source": peak_kind, "ms_simplex": t_s, "ms_l1": t_l,
                      "algorithmic_bytes": bytes_s + bytes_l, "frac_of_8TBs": achieved / 8000.0},
         "gpu_launches": 2 * K,
@@ -262,6 +337,7 @@ def run_ours(args, world, rank, local):
 
     if args.extras and rank == 0:
         out["variants"] = extras(args, api, W, dev, stream)
+        out["batched"] = batched_extras(api, W, dev, stream)
     if rank == 0 and args.cpu_baseline:
         yc = y[:CPU_SAMPLE].cpu().numpy()
         out["cpu_baseline"] = cpu_baseline(yc)
@@ -319,6 +395,117 @@ def extras(args, api, W, dev, stream):
                                             "status": int(inf.status), "elem_iter_per_s": n * inf.iters / (ms * 1e-3),
                                             "GBps": byt / (ms * 1e-3) / 1e9}
         del p, xg
+        torch.cuda.empty_cache()
+    return res
+
+
+def batched_extras(api, W, dev, stream):
+    """The batched, differentiable workloads: forward + backward of a ragged batch in two
+    launches (captured once in a CUDA graph and replayed) against the same solves issued as
+    one forward and one backward launch per instance.
+      simplex: 4096 instances, lengths log-uniform in [16, 2^20], FP32 y ~ N(0,1), r = 1
+      general: 256 instances, lengths log-uniform in [1e3, 1e6], FP64 uncorrelated box"""
+    import torch
+    res = {}
+    cases = (
+        ("simplex_f32_b4096", lambda: W.batched_simplex(batch=4096, lo=16, hi=1 << 20, seed=0, device=dev,
+                                                        dtype=torch.float32)),
+        ("general_f64_b256", lambda: W.batched_general(batch=256, lo=1000, hi=1000000, seed=0, device=dev,
+                                                       dtype=torch.float64)),
+    )
+    for name, make in cases:
+        d = make()
+        general = "a" in d
+        vec = d["a"] if general else d["y"]
+        n, B = vec.numel(), d["offsets"].numel() - 1
+        off = d["offsets"]
+        r = d["r"].to(dev)
+        g = d["g"]
+        x = torch.empty_like(vec)
+        mask = torch.zeros((n + 31) // 32, dtype=torch.int32, device=dev)
+        ws = api.Workspace(n, B, vec.dtype, dev)
+        grads = {k: torch.empty_like(vec) for k in ("a", "b", "d", "l", "u", "y")}
+        gr = torch.empty(B, dtype=torch.float64, device=dev)
+        st = torch.empty(B, dtype=torch.int32, device=dev)
+        lib = api.library()
+        opt = api.make_options()
+        P = api.ptr
+        code = api.dtype_code(vec.dtype)
+
+        def fwd_bwd(s=None):
+            sh = api.stream_handle(s or stream)
+            if general:
+                rc = lib.cqk_solve_batched(B, P(off), code, P(d["a"]), P(d["b"]), P(d["d"]), P(d["l"]), P(d["u"]),
+                                           P(r), P(x), P(mask), P(ws.info), api.ctypes.byref(opt), P(ws.buf),
+                                           ws.nbytes, sh)
+                api.check_rc(rc, "cqk_solve_batched")
+                rc = lib.cqk_backward(B, P(off), n, code, P(g), P(x), P(d["a"]), P(d["b"]), P(d["d"]), P(d["l"]),
+                                      P(d["u"]), P(mask), P(ws.info), P(grads["a"]), P(grads["b"]), P(grads["d"]),
+                                      P(grads["l"]), P(grads["u"]), P(gr), P(st), api.ctypes.byref(opt),
+                                      P(ws.buf), ws.nbytes, sh)
+                api.check_rc(rc, "cqk_backward")
+            else:
+                rc = lib.cqk_project_simplex_batched(B, P(off), code, P(d["y"]), P(r), P(x), P(mask), P(ws.info),
+                                                     api.ctypes.byref(opt), P(ws.buf), ws.nbytes,
+                                                     sh)
+                api.check_rc(rc, "cqk_project_simplex_batched")
+                rc = lib.cqk_backward_simplex(B, P(off), n, code, P(g), P(x), P(mask), P(ws.info), P(grads["y"]),
+                                              P(gr), P(st), api.ctypes.byref(opt), P(ws.buf), ws.nbytes,
+                                              sh)
+                api.check_rc(rc, "cqk_backward_simplex")
+
+        ms_batched = _time(fwd_bwd, stream)
+        infos = ws.read_infos(B)
+        ok = sum(int(i.status) == 0 for i in infos)
+        graph_ms = None
+        try:
+            gph = torch.cuda.CUDAGraph()
+            cs = torch.cuda.Stream()
+            cs.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(cs):
+                fwd_bwd(cs)
+                torch.cuda.synchronize()
+                with torch.cuda.graph(gph, stream=cs):
+                    fwd_bwd(cs)
+            graph_ms = _time(gph.replay, torch.cuda.current_stream())
+        except Exception as e:  # capture unsupported: report, do not fail the bench
+            graph_ms = f"capture failed: {type(e).__name__}: {e}"
+        # per-instance launches (one forward + one backward per instance), same arrays
+        offs = off.cpu().tolist()
+        rl = d["r"].cpu().tolist()
+        ws1 = api.Workspace(max(offs[k + 1] - offs[k] for k in range(B)), 1, vec.dtype, dev)
+        info1 = ws1.info
+
+        def per_instance():
+            for k in range(B):
+                lo, hi = offs[k], offs[k + 1]
+                m = hi - lo
+                if m == 0:
+                    continue
+                es = vec.element_size()
+                if general:
+                    ap = [P(d[q][lo:hi]) for q in ("a", "b", "d", "l", "u")]
+                    lib.cqk_solve(m, code, *ap, float(rl[k]), P(x[lo:hi]), None, P(info1), api.ctypes.byref(opt),
+                                  P(ws1.buf), ws1.nbytes, api.stream_handle(stream))
+                    lib.cqk_backward(1, None, m, code, P(g[lo:hi]), P(x[lo:hi]), *ap, None, P(info1),
+                                     P(grads["a"][lo:hi]), P(grads["b"][lo:hi]), P(grads["d"][lo:hi]),
+                                     P(grads["l"][lo:hi]), P(grads["u"][lo:hi]), P(gr[k:k + 1]), P(st[k:k + 1]),
+                                     api.ctypes.byref(opt), P(ws1.buf), ws1.nbytes, api.stream_handle(stream))
+                else:
+                    lib.cqk_project_simplex(m, code, P(d["y"][lo:hi]), float(rl[k]), P(x[lo:hi]), None, P(info1),
+                                            api.ctypes.byref(opt), P(ws1.buf), ws1.nbytes, api.stream_handle(stream))
+                    lib.cqk_backward_simplex(1, None, m, code, P(g[lo:hi]), P(x[lo:hi]), None, P(info1),
+                                             P(grads["y"][lo:hi]), P(gr[k:k + 1]), P(st[k:k + 1]),
+                                             api.ctypes.byref(opt), P(ws1.buf), ws1.nbytes, api.stream_handle(stream))
+
+        ms_loop = _time(per_instance, stream, reps=2)
+        res[name] = {"instances": B, "n_total": n, "dtype": str(vec.dtype).replace("torch.", ""),
+                     "ms_fwd_bwd_batched": ms_batched, "ms_fwd_bwd_graph": graph_ms,
+                     "ms_fwd_bwd_per_instance_launches": ms_loop,
+                     "speedup_vs_per_instance": ms_loop / (graph_ms if isinstance(graph_ms, float) else ms_batched),
+                     "instances_ok": ok, "mean_iters": sum(i.iters for i in infos) / B,
+                     "elements_per_s_fwd_bwd": n / ((graph_ms if isinstance(graph_ms, float) else ms_batched) * 1e-3)}
+        del d, x, mask, ws, grads, ws1
         torch.cuda.empty_cache()
     return res
 
