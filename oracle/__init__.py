@@ -29,11 +29,13 @@ from .reference import (  # noqa: F401
     x_of_lambda,
     phi,
     lambda0_formula,
+    lambda0_warm,
     breakpoint_search,
     newton_cqk,
     solve_sort,
     condat_init,
     condat_chunks,
+    condat_chunks_warm,
     condat_project,
     newton_simplex,
     project_simplex_sort,

@@ -25,7 +25,9 @@
  *   cqko_newton         semismooth Newton with secant safeguard      [Alg. 1; stopping criteria of Sec. 4]
  *   cqko_solve_sort     exact solve by sorting breakpoints           [definition: phi(lambda*) = r]
  *   cqko_condat_init    Condat's multiplier initialisation           [Alg. 2]
+ *   cqko_lambda0_warm   eq. (CQKlambda0) over J = {l < xbar < u}      [Sec. 2, start from a primal estimate]
  *   cqko_condat_chunks  Alg. 2 per chunk, union of the J's           [Sec. 4, parallel lambda_0; eq. (lambdaJ)]
+ *   cqko_condat_chunks_warm  the same on I = supp(xbar)              [Sec. 3.3 warm start]
  *   cqko_condat         Condat's projection onto the simplex         [Alg. 3]
  *   cqko_newton_simplex specialised Newton for the simplex           [Alg. 4; Theorem 3.1]
  *   cqko_project_simplex_sort  sort-based simplex projection         [textbook closed form, cited in Sec. 1]
@@ -99,6 +101,26 @@ double cqko_lambda0(int64_t n, const double* a, const double* b, const double* d
         s += (long double)(b[i] * a[i] / d[i]);
         q += (long double)(b[i] * b[i] / d[i]);
     }
+    return (double)(((long double)r - s) / q);
+}
+
+/*
+ * Start from a primal estimate xbar (Sec. 2, after eq. (CQKlambda0)): the same
+ * formula with J = {i : l_i < xbar_i < u_i}, the variables that xbar leaves free;
+ * when that set is empty xbar is discarded and J = {1..n}.
+ */
+double cqko_lambda0_warm(int64_t n, const double* a, const double* b, const double* d,
+                         const double* l, const double* u, const double* xbar, double r) {
+    long double s = 0.0L, q = 0.0L;
+    int64_t m = 0;
+    for (int64_t i = 0; i < n; i++) {
+        if (l[i] < xbar[i] && xbar[i] < u[i]) {
+            s += (long double)(b[i] * a[i] / d[i]);
+            q += (long double)(b[i] * b[i] / d[i]);
+            m++;
+        }
+    }
+    if (m == 0) return cqko_lambda0(n, a, b, d, r);
     return (double)(((long double)r - s) / q);
 }
 
@@ -401,6 +423,43 @@ double cqko_condat_chunks(int64_t n, const double* y, double r, int l1, int64_t 
     free(scratch);
     *usum = (double)S;
     *ucount = C;
+    return (double)(((long double)r - S) / (long double)C);
+}
+
+/*
+ * Warm start of Sec. 3.3: Alg. 2 run on I = supp(xbar) = {i : xbar_i > 0} (l1 ball:
+ * xbar_i != 0), here per chunk of the same partition as cqko_condat_chunks (an element
+ * outside the support is skipped by its chunk's scan).  When no chunk keeps an element
+ * (J_+ empty) the multiplier is max{r/n, -y_1} as the paper sets it (l1 ball: |y_1|).
+ */
+double cqko_condat_chunks_warm(int64_t n, const double* y, const double* xbar, double r, int l1,
+                               int64_t tile, int64_t nchunks, int64_t shift, double* usum,
+                               int64_t* ucount) {
+    int64_t ntiles = (n + shift + tile - 1) / tile;
+    int64_t maxp = ((ntiles + nchunks - 1) / nchunks) * tile;
+    int64_t* idx = (int64_t*)malloc(sizeof(int64_t) * (size_t)(maxp > 0 ? maxp : 1));
+    int64_t* scratch = (int64_t*)malloc(sizeof(int64_t) * (size_t)(2 * (maxp > 0 ? maxp : 1)));
+    long double S = 0.0L;
+    int64_t C = 0;
+    for (int64_t c = 0; c < nchunks; c++) {
+        int64_t p = 0;
+        for (int64_t t = c; t < ntiles; t += nchunks)
+            for (int64_t i = t * tile - shift; i < (t + 1) * tile - shift && i < n; i++)
+                if (i >= 0 && (l1 ? xbar[i] != 0.0 : xbar[i] > 0.0)) idx[p++] = i;
+        if (p == 0) continue;
+        double js; int64_t jc;
+        cqko_condat_init(y, idx, p, r, l1, &js, &jc, scratch, NULL);
+        S += js;
+        C += jc;
+    }
+    free(idx);
+    free(scratch);
+    *usum = (double)S;
+    *ucount = C;
+    if (C == 0) {
+        double y1 = l1 ? fabs(y[0]) : y[0];
+        return fmax(r / (double)n, -y1);
+    }
     return (double)(((long double)r - S) / (long double)C);
 }
 

@@ -65,6 +65,10 @@ def _load():
         lib.cqko_condat_init.restype = dbl
         lib.cqko_condat_chunks.argtypes = [i64, d_p, dbl, cint, i64, i64, i64, d_p, i64_p]
         lib.cqko_condat_chunks.restype = dbl
+        lib.cqko_condat_chunks_warm.argtypes = [i64, d_p, d_p, dbl, cint, i64, i64, i64, d_p, i64_p]
+        lib.cqko_condat_chunks_warm.restype = dbl
+        lib.cqko_lambda0_warm.argtypes = [i64, d_p, d_p, d_p, d_p, d_p, d_p, dbl]
+        lib.cqko_lambda0_warm.restype = dbl
         lib.cqko_condat.argtypes = [i64, d_p, dbl, d_p]
         lib.cqko_condat.restype = dbl
         lib.cqko_newton_simplex.argtypes = [i64, d_p, dbl, cint, dbl, cint, dbl, d_p, i_p, i_p, d_p]
@@ -110,6 +114,14 @@ def lambda0_formula(a, b, d, r):
     """eq. (CQKlambda0) with J = all variables."""
     a, b, d = _f64(a), _f64(b), _f64(d)
     return float(_load().cqko_lambda0(a.shape[0], _ptr(a), _ptr(b), _ptr(d), float(r)))
+
+
+def lambda0_warm(a, b, d, l, u, xbar, r):
+    """eq. (CQKlambda0) with J = {l < xbar < u} (all variables if that set is empty)."""
+    n, a, b, d, l, u = _arrs(a, b, d, l, u)
+    xbar = _f64(xbar)
+    return float(_load().cqko_lambda0_warm(n, _ptr(a), _ptr(b), _ptr(d), _ptr(l), _ptr(u), _ptr(xbar),
+                                           float(r)))
 
 
 def breakpoint_search(lam, direction, a, b, d, l, u):
@@ -184,6 +196,17 @@ def condat_chunks(y, r, tile, nchunks, l1=False, shift=0):
     uc = ctypes.c_int64()
     lam = _load().cqko_condat_chunks(y.shape[0], _ptr(y), float(r), 1 if l1 else 0, int(tile),
                                      int(nchunks), int(shift), ctypes.byref(us), ctypes.byref(uc))
+    return float(lam), us.value, uc.value
+
+
+def condat_chunks_warm(y, xbar, r, tile, nchunks, l1=False, shift=0):
+    """Warm start of Sec. 3.3 over the chunk partition: Alg. 2 per chunk on supp(xbar).
+    Returns (lambda_0, sum over the union of J's, size of the union)."""
+    y, xbar = _f64(y), _f64(xbar)
+    us = ctypes.c_double()
+    uc = ctypes.c_int64()
+    lam = _load().cqko_condat_chunks_warm(y.shape[0], _ptr(y), _ptr(xbar), float(r), 1 if l1 else 0, int(tile),
+                                          int(nchunks), int(shift), ctypes.byref(us), ctypes.byref(uc))
     return float(lam), us.value, uc.value
 
 

@@ -11,7 +11,8 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "cqk_oracle.c")
-PINS = ["tests/test_oracle_general.py", "tests/test_oracle_simplex.py", "tests/test_oracle_grad.py"]
+PINS = ["tests/test_oracle_general.py", "tests/test_oracle_simplex.py", "tests/test_oracle_grad.py",
+        "tests/test_oracle_warm.py"]
 
 # (name, original text, mutated text): each must occur exactly once
 MUTANTS = [
@@ -31,6 +32,10 @@ MUTANTS = [
     ("alg4_stop", "if (g <= 0.0) { *stop = STOPR_BELOW; return ORC_OK; }", "if (g < -1.0) { *stop = STOPR_BELOW; return ORC_OK; }"),
     ("sort_simplex_rho", "if ((long double)s[j] - (cum - r) / (long double)(j + 1) > 0.0L)", "if ((long double)s[j] - (cum + r) / (long double)(j + 1) > 0.0L)"),
     ("alg3_update", "lam = (r - S) / (double)size_after;", "lam = (r + S) / (double)size_after;"),
+    ("warm_free_test", "if (l[i] < xbar[i] && xbar[i] < u[i]) {", "if (l[i] <= xbar[i] && xbar[i] < u[i]) {"),
+    ("warm_support_test", "if (i >= 0 && (l1 ? xbar[i] != 0.0 : xbar[i] > 0.0)) idx[p++] = i;",
+     "if (i >= 0 && (l1 ? xbar[i] != 0.0 : xbar[i] >= 0.0)) idx[p++] = i;"),
+    ("warm_fallback", "return fmax(r / (double)n, -y1);", "return fmax(r / (double)n, y1);"),
 ]
 
 
