@@ -70,6 +70,12 @@ typedef enum {
     CQK_INIT_CONDAT = 1,  /* simplex / l1 only: Alg. 2 run independently on every chunk of a */
                           /* fixed partition, lambda_0 from eq. (lambdaJ) on the union of the */
                           /* J's (Sec. 4); the partition is reported in cqk_info             */
+    CQK_INIT_WARM = 2,    /* from a primal estimate options.xbar (device array of the data's  */
+                          /* dtype and length).  cqk_solve: eq. (CQKlambda0) over J = {l <    */
+                          /* xbar < u}, all variables if J is empty (Sec. 2).  Projections:  */
+                          /* Alg. 2 per chunk (as CQK_INIT_CONDAT) on the support of xbar    */
+                          /* (xbar > 0; l1 ball: xbar != 0) (Sec. 3.3); lambda_0 =           */
+                          /* max{r/n, -y_1} (l1 ball: -|y_1|) when no chunk keeps an element */
     CQK_INIT_GIVEN = 3    /* lambda_0 = options.lambda0                                      */
 } cqk_init;
 
@@ -103,7 +109,8 @@ typedef struct cqk_options {
                             /* simplex / l1 batches, 65536 for general ones                     */
     int32_t condat_chunk;   /* CQK_INIT_CONDAT: the partition has min(warps, ceil(n /            */
                             /* condat_chunk)) chunks; 0 (default): 512                          */
-    int32_t reserved[6];
+    const void* xbar;       /* CQK_INIT_WARM: the primal estimate (device; NULL otherwise)       */
+    int32_t reserved[4];
 } cqk_options;
 
 /* Written on the device by every solve. */

@@ -38,6 +38,7 @@ class Status(enum.IntEnum):
 class Init(enum.IntEnum):
     FORMULA = 0
     CONDAT = 1
+    WARM = 2
     GIVEN = 3
 
 
@@ -56,7 +57,8 @@ class _Options(ctypes.Structure):
         ("fault_inject", ctypes.c_int32),
         ("group_elems", ctypes.c_int32),
         ("condat_chunk", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 6),
+        ("xbar", ctypes.c_void_p),
+        ("reserved", ctypes.c_int32 * 4),
     ]
 
 
@@ -183,7 +185,7 @@ def stream_handle(stream=None):
 
 
 def make_options(init=None, max_iter=100, lambda0=0.0, validate=True, final_step=None, spin_limit_us=2_000_000,
-                 max_blocks=0, fault_inject=False, group_elems=0, condat_chunk=0) -> _Options:
+                 max_blocks=0, fault_inject=False, group_elems=0, condat_chunk=0, xbar=None) -> _Options:
     o = _Options()
     library().cqk_default_options(ctypes.byref(o))
     o.max_iter = int(max_iter)
@@ -197,6 +199,7 @@ def make_options(init=None, max_iter=100, lambda0=0.0, validate=True, final_step
     o.fault_inject = 1 if fault_inject else 0
     o.group_elems = int(group_elems)
     o.condat_chunk = int(condat_chunk)
+    o.xbar = xbar.data_ptr() if xbar is not None else None
     return o
 
 

@@ -5,6 +5,12 @@
 
 #include "cqk_internal.h"
 
+#include <stddef.h>
+
+static_assert(sizeof(cqk_options) == 72, "cqk_options layout is part of the ABI");
+static_assert(offsetof(cqk_options, xbar) == 48, "cqk_options layout is part of the ABI");
+static_assert(sizeof(cqk_info) == 72, "cqk_info layout is part of the ABI");
+
 namespace cqk {
 
 static thread_local int g_last_cuda_error = 0;
@@ -26,6 +32,7 @@ Opts resolve_options(const cqk_options* opt, int dtype, int default_init) {
     o.fault_inject = d.fault_inject;
     o.group_elems = d.group_elems > 0 ? d.group_elems : 0;
     o.condat_chunk = d.condat_chunk > 0 ? d.condat_chunk : kCondatChunkElems;
+    o.xbar = d.xbar;
     return o;
 }
 
@@ -85,7 +92,8 @@ int cqk_solve(int64_t n, int32_t dtype, const void* a, const void* b, const void
     if (!ws_ok(workspace, ws_bytes, kSingleWsBytes)) return CQK_BAD_ARG;
     if (r != r) return CQK_BAD_ARG;
     Opts o = resolve_options(opt, dtype, CQK_INIT_FORMULA);
-    if (o.init != CQK_INIT_FORMULA && o.init != CQK_INIT_GIVEN) return CQK_BAD_ARG;
+    if (o.init != CQK_INIT_FORMULA && o.init != CQK_INIT_GIVEN && o.init != CQK_INIT_WARM) return CQK_BAD_ARG;
+    if (o.init == CQK_INIT_WARM && !o.xbar && n > 0) return CQK_BAD_ARG;
     if (n == 0) {
         cqk_info inf;
         memset(&inf, 0, sizeof(inf));
@@ -114,7 +122,9 @@ static int project(int64_t n, int32_t dtype, const void* y, double r, void* x, u
     if (x == y) return CQK_BAD_ARG;
     if (!ws_ok(ws, ws_bytes, kSingleWsBytes)) return CQK_BAD_ARG;
     Opts o = resolve_options(opt, dtype, CQK_INIT_CONDAT);
-    if (o.init != CQK_INIT_FORMULA && o.init != CQK_INIT_CONDAT && o.init != CQK_INIT_GIVEN) return CQK_BAD_ARG;
+    if (o.init != CQK_INIT_FORMULA && o.init != CQK_INIT_CONDAT && o.init != CQK_INIT_GIVEN && o.init != CQK_INIT_WARM)
+        return CQK_BAD_ARG;
+    if (o.init == CQK_INIT_WARM && !o.xbar) return CQK_BAD_ARG;
     return launch_simplex(n, dtype, y, r, l1, x, mask, info, o, ws, (cudaStream_t)stream);
 }
 
@@ -139,11 +149,13 @@ static int batched(int32_t B, const int64_t* offsets, int32_t dtype, const void*
     if (kind != 0 && x == a) return CQK_BAD_ARG;
     if (!ws_ok(ws, ws_bytes, batch_ws_bytes(B))) return CQK_BAD_ARG;
     Opts o = resolve_options(opt, dtype, kind == 0 ? CQK_INIT_FORMULA : CQK_INIT_CONDAT);
+    if (o.init == CQK_INIT_WARM && !o.xbar) return CQK_BAD_ARG;
     if (kind == 0) {
-        if (o.init != CQK_INIT_FORMULA && o.init != CQK_INIT_GIVEN) return CQK_BAD_ARG;
+        if (o.init != CQK_INIT_FORMULA && o.init != CQK_INIT_GIVEN && o.init != CQK_INIT_WARM) return CQK_BAD_ARG;
         return launch_general_batched(B, offsets, dtype, a, b, d, l, u, r, x, mask, info, o, ws, (cudaStream_t)stream);
     }
-    if (o.init != CQK_INIT_FORMULA && o.init != CQK_INIT_CONDAT && o.init != CQK_INIT_GIVEN) return CQK_BAD_ARG;
+    if (o.init != CQK_INIT_FORMULA && o.init != CQK_INIT_CONDAT && o.init != CQK_INIT_GIVEN && o.init != CQK_INIT_WARM)
+        return CQK_BAD_ARG;
     return launch_simplex_batched(B, offsets, dtype, a, r, kind == 2, x, mask, info, o, ws, (cudaStream_t)stream);
 }
 

@@ -50,6 +50,7 @@ struct GeneralArgs {
     int final_step;
     int aligned;
     int staged;  // arrays staged through shared memory by bulk copies (aligned data)
+    const void* xbar;  // CQK_INIT_WARM: primal estimate
     int phi_only;
     unsigned long long limit_ns;
     int fault_inject;
@@ -618,6 +619,82 @@ __device__ __forceinline__ bool lambda0_pass(const GeneralArgs& A, const Grp& gp
     return okw;
 }
 
+// l < x strictly, as doubles, on order keys (-0 taken as +0; a NaN x is never inside)
+__device__ __forceinline__ long long cmp_key(double v) {
+    const unsigned long long b = opaque_bits(v);
+    return (b << 1) == 0ull ? 0ll : order_key(v);
+}
+template <typename T>
+__device__ __forceinline__ bool strictly_inside(T l, T x, T u) {
+    if constexpr (sizeof(T) == 8) {
+        const long long kx = cmp_key(x);
+        return cmp_key(l) < kx && kx < cmp_key(u) && !f64_is_nan(x);
+    } else {
+        return l < x && x < u;
+    }
+}
+
+// Warm start (Sec. 2): the sums of eq. (CQKlambda0) over J = {l < xbar < u} and over all
+// variables, and |J|, in one pass with plain loads.  out = {s_J, q_J, |J|, s_all, q_all}.
+template <typename T>
+__device__ __forceinline__ void lambda0_warm_pass(const GeneralArgs& A, const Grp& gp, double (&out)[5]) {
+    constexpr int V = VecOf<T>::V;
+    constexpr int U = kGenU;
+    const T* __restrict__ pa = static_cast<const T*>(A.a);
+    const T* __restrict__ pb = static_cast<const T*>(A.b);
+    const T* __restrict__ pd = static_cast<const T*>(A.d);
+    const T* __restrict__ pl = static_cast<const T*>(A.l);
+    const T* __restrict__ pu = static_cast<const T*>(A.u);
+    const T* __restrict__ px = static_cast<const T*>(A.xbar);
+    const Span sp = gp.sp;
+    const int lane = threadIdx.x & 31;
+    const bool aligned = A.aligned != 0;
+    LazyDf sJ{0.0f, 0.0f}, qJ{0.0f, 0.0f}, sA{0.0f, 0.0f}, qA{0.0f, 0.0f};
+    double sJ64 = 0.0, qJ64 = 0.0, sA64 = 0.0, qA64 = 0.0;
+    long long m = 0;
+    const WarpSweep sw(span_qlo<V>(sp), span_qhi<V>(sp), U, gp.member, gp.g);
+    int steps = 0;
+    for (int64_t it = 0; it < sw.count; it++) {
+        if (++steps == kFlushEvery) {
+            sJ64 += lazy_value(sJ);
+            qJ64 += lazy_value(qJ);
+            sA64 += lazy_value(sA);
+            qA64 += lazy_value(qA);
+            sJ = qJ = sA = qA = LazyDf{0.0f, 0.0f};
+            steps = 0;
+        }
+        const int64_t base = sw.base(it, false);
+        T va[U][V], vb[U][V], vd[U][V], vl[U][V], vu[U][V], vx[U][V];
+        bool ok[U][V];
+#pragma unroll
+        for (int w = 0; w < U; w++) {
+            const int64_t q = base + w * 32 + lane;
+            load_vec<T>(pa, sp, q, aligned, va[w], ok[w]);
+            load_vec<T>(pb, sp, q, aligned, vb[w], ok[w]);
+            load_vec<T>(pd, sp, q, aligned, vd[w], ok[w]);
+            load_vec<T>(pl, sp, q, aligned, vl[w], ok[w]);
+            load_vec<T>(pu, sp, q, aligned, vu[w], ok[w]);
+            load_vec<T>(px, sp, q, aligned, vx[w], ok[w]);
+        }
+#pragma unroll
+        for (int w = 0; w < U; w++) {
+            bool inJ[V];
+#pragma unroll
+            for (int j = 0; j < V; j++) {
+                inJ[j] = ok[w][j] && strictly_inside<T>(vl[w][j], vx[w][j], vu[w][j]);
+                m += inJ[j] ? 1 : 0;
+            }
+            lambda0_vec<T>(va[w], vb[w], vd[w], inJ, sJ, qJ, sJ64, qJ64);
+            lambda0_vec<T>(va[w], vb[w], vd[w], ok[w], sA, qA, sA64, qA64);
+        }
+    }
+    out[0] = lazy_value(sJ) + sJ64;
+    out[1] = lazy_value(qJ) + qJ64;
+    out[2] = (double)m;
+    out[3] = lazy_value(sA) + sA64;
+    out[4] = lazy_value(qA) + qA64;
+}
+
 #define CQK_BARRIER_OR_LEAVE()                                                  \
     do {                                                                        \
         if (!group_barrier(gp, bar_target, A.limit_ns, A.fault_inject != 0)) {     \
@@ -686,6 +763,18 @@ __device__ __forceinline__ void general_solve(const GeneralArgs& A, const Grp& g
         grid_reduce<2>(gp.part, G, par, -1, red, sh, bc);
         par ^= 1;
         lam0 = (r - red[0]) / red[1];  // eq. (CQKlambda0), J = all variables
+        passes++;
+    } else if (A.init == CQK_INIT_WARM) {
+        double w[5];
+        lambda0_warm_pass<T>(A, gp, w);
+        block_sum<5>(w, sh);
+        write_partials<5>(gp.part, gp.member, G, par, w);
+        CQK_BARRIER_OR_LEAVE();
+        double red[5];
+        grid_reduce<5>(gp.part, G, par, -1, red, sh, bc);
+        par ^= 1;
+        // eq. (CQKlambda0) over J = {l < xbar < u}; all variables if J is empty (Sec. 2)
+        lam0 = red[2] > 0.0 ? (r - red[0]) / red[1] : (r - red[3]) / red[4];
         passes++;
     }
 
@@ -988,6 +1077,8 @@ int launch_general(int64_t n, int dtype, const void* a, const void* b, const voi
     A.final_step = o.final_step;
     A.limit_ns = o.limit_ns;
     A.fault_inject = o.fault_inject;
+    A.xbar = o.xbar;
+    if (A.init == CQK_INIT_WARM && ((uintptr_t)o.xbar % 16) != 0) A.aligned = 0;  // vector loads need all arrays
     return launch(A, dtype, o.max_blocks, s, ws);
 }
 
@@ -1008,6 +1099,8 @@ int launch_general_batched(int64_t B, const int64_t* offsets, int dtype, const v
     A.final_step = o.final_step;
     A.limit_ns = o.limit_ns;
     A.fault_inject = o.fault_inject;
+    A.xbar = o.xbar;
+    if (A.init == CQK_INIT_WARM && ((uintptr_t)o.xbar % 16) != 0) A.aligned = 0;
     A.staged = A.aligned;
     P.offsets = offsets;
     P.r = r;

@@ -42,6 +42,7 @@ struct Opts {
     int fault_inject;
     int64_t group_elems;   // batched calls: one block of an instance's group per this many elements
     int64_t condat_chunk;  // CQK_INIT_CONDAT: minimum elements per chunk
+    const void* xbar;      // CQK_INIT_WARM: primal estimate
 };
 
 Opts resolve_options(const cqk_options* opt, int dtype, int default_init);

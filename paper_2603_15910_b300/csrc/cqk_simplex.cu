@@ -51,6 +51,7 @@ struct SimplexArgs {
     unsigned long long limit_ns;
     int fault_inject;
     int64_t condat_chunk;  // minimum elements per chunk of the parallel Alg. 2 start
+    const void* xbar;      // CQK_INIT_WARM: primal estimate
     WsHeader* hdr;
     double* part;  // [2][kPartialQ][gridDim.x]
 };
@@ -187,9 +188,23 @@ __device__ __forceinline__ void condat_slab(const T (&vals)[VecOf<T>::V], const 
     }
 }
 
+// xb (nullable): a primal estimate; the chunk then keeps only the elements of its support
+// (x_i > 0; l1 ball: x_i != 0), the warm start of Sec. 3.3.
 template <typename T, bool L1>
-__device__ void condat_chunk(const T* __restrict__ y, const Span& sp, bool aligned, double r, int64_t w, int64_t W,
-                             double& S_out, long long& nJ_out) {
+__device__ __forceinline__ void support_mask(const T* __restrict__ xb, const Span& sp, int64_t q, bool aligned,
+                                             bool (&okv)[VecOf<T>::V]) {
+    if (!xb) return;
+    constexpr int V = VecOf<T>::V;
+    T xv[V];
+    bool xok[V];
+    load_vec<T>(xb, sp, q, aligned, xv, xok);
+#pragma unroll
+    for (int j = 0; j < V; j++) okv[j] = okv[j] && (L1 ? xv[j] != T(0) : xv[j] > T(0));
+}
+
+template <typename T, bool L1>
+__device__ void condat_chunk(const T* __restrict__ y, const T* __restrict__ xb, const Span& sp, bool aligned,
+                             double r, int64_t w, int64_t W, double& S_out, long long& nJ_out) {
     constexpr int V = VecOf<T>::V;
     constexpr int K = condat_k<T>();
     constexpr int TILE = 32 * K * V;
@@ -206,6 +221,8 @@ __device__ void condat_chunk(const T* __restrict__ y, const Span& sp, bool align
 #pragma unroll
         for (int k = 0; k < K; k++) load_vec<T>(y, sp, t * 32 * K + k * 32 + lane, aligned, vals[k], okv[k]);
 #pragma unroll
+        for (int k = 0; k < K; k++) support_mask<T, L1>(xb, sp, t * 32 * K + k * 32 + lane, aligned, okv[k]);
+#pragma unroll
         for (int k = 0; k < K; k++)
             condat_slab<T, L1>(vals[k], okv[k], (t * 32 * K + k * 32 + lane) * V, INT64_MAX, true, r, st);
     }
@@ -218,6 +235,8 @@ __device__ void condat_chunk(const T* __restrict__ y, const Span& sp, bool align
             bool okv[K][V];
 #pragma unroll
             for (int k = 0; k < K; k++) load_vec<T>(y, sp, t * 32 * K + k * 32 + lane, aligned, vals[k], okv[k]);
+#pragma unroll
+            for (int k = 0; k < K; k++) support_mask<T, L1>(xb, sp, t * 32 * K + k * 32 + lane, aligned, okv[k]);
 #pragma unroll
             for (int k = 0; k < K; k++)
                 condat_slab<T, L1>(vals[k], okv[k], (t * 32 * K + k * 32 + lane) * V, before, false, r, st);
@@ -379,7 +398,8 @@ __device__ __forceinline__ void simplex_solve(const SimplexArgs& A, const Grp& g
     int passes = 0, nchunks = 0, tile = 0;
     {
         double q[4] = {0.0, 0.0, 0.0, -INFINITY};  // sum y (l1: |y|), union sum, union size, max y (l1: |y|)
-        const bool condat = A.init == CQK_INIT_CONDAT;
+        const bool warm = A.init == CQK_INIT_WARM;
+        const bool condat = A.init == CQK_INIT_CONDAT || warm;
         const bool sum_pass = L1 || !condat;
         bool bad = false;
         if (sum_pass) {
@@ -443,7 +463,9 @@ __device__ __forceinline__ void simplex_solve(const SimplexArgs& A, const Grp& g
         if (condat) {
             double Sw = 0.0;
             long long nJw = 0;
-            if (gwarp < nchunk) condat_chunk<T, L1>(y, sp, aligned, r, gwarp, nchunk, Sw, nJw);
+            if (gwarp < nchunk)
+                condat_chunk<T, L1>(y, warm ? static_cast<const T*>(A.xbar) : nullptr, sp, aligned, r, gwarp, nchunk,
+                                    Sw, nJw);
             q[1] = lane == 0 ? Sw : 0.0;
             q[2] = lane == 0 ? (double)nJw : 0.0;
             passes++;
@@ -479,8 +501,14 @@ __device__ __forceinline__ void simplex_solve(const SimplexArgs& A, const Grp& g
         double red[4];
         grid_reduce<4>(gp.part, G, 0, 3, red, sh, bc);
         abs_sum = red[0];
-        if (condat) {
+        if (condat && red[2] > 0.0) {
             lam0 = (r - red[1]) / red[2];  // eq. (lambdaJ) on the union of the chunks' J
+            nchunks = (int)nchunk;
+            tile = 32 * condat_k<T>() * V;
+        } else if (condat) {
+            // warm start with an empty J_+ (no element of the estimate's support): Sec. 3.3
+            const double y1 = (double)y[sp.lo];
+            lam0 = fmax(r / (double)n, L1 ? -fabs(y1) : -y1);
             nchunks = (int)nchunk;
             tile = 32 * condat_k<T>() * V;
         } else if (A.init == CQK_INIT_GIVEN) {
@@ -776,7 +804,9 @@ int launch_simplex_batched(int64_t B, const int64_t* offsets, int dtype, const v
     A.limit_ns = o.limit_ns;
     A.fault_inject = o.fault_inject;
     A.condat_chunk = o.condat_chunk;
-    A.aligned = ((((uintptr_t)y) | ((uintptr_t)x)) % 16 == 0) ? 1 : 0;
+    A.xbar = o.xbar;
+    const bool xbar_misaligned = o.init == CQK_INIT_WARM && ((uintptr_t)o.xbar % 16) != 0;
+    A.aligned = ((((uintptr_t)y) | ((uintptr_t)x)) % 16 == 0 && !xbar_misaligned) ? 1 : 0;
     P.offsets = offsets;
     P.r = r;
     P.info = info;
@@ -820,9 +850,11 @@ int launch_simplex(int64_t n, int dtype, const void* y, double r, int l1, void* 
     A.limit_ns = o.limit_ns;
     A.fault_inject = o.fault_inject;
     A.condat_chunk = o.condat_chunk;
+    A.xbar = o.xbar;
+    const bool xbar_misaligned = o.init == CQK_INIT_WARM && ((uintptr_t)o.xbar % 16) != 0;
     A.hdr = static_cast<WsHeader*>(ws);
     A.part = reinterpret_cast<double*>(static_cast<char*>(ws) + sizeof(WsHeader));
-    A.aligned = ((((uintptr_t)y) | ((uintptr_t)x)) % 16 == 0) ? 1 : 0;
+    A.aligned = ((((uintptr_t)y) | ((uintptr_t)x)) % 16 == 0 && !xbar_misaligned) ? 1 : 0;
     const void* kern;
     if (dtype == CQK_F64)
         kern = l1 ? (const void*)simplex_kernel<double, true> : (const void*)simplex_kernel<double, false>;

@@ -44,6 +44,7 @@ def test_host_only_calls():
     o = api.make_options()
     assert o.max_iter == 100 and o.validate == 1 and o.spin_limit_us == 2_000_000 and o.final_step == 1
     assert ctypes.sizeof(api._Info) == 72
+    assert ctypes.sizeof(api._Options) == 72 and api._Options.xbar.offset == 48
 
 
 def test_bad_arguments_are_rejected_before_any_launch():
