@@ -222,10 +222,11 @@ struct GtThreshold {
     bool neg;
 };
 __device__ __forceinline__ GtThreshold make_gt(double c) {
-    if (c == 0.0) c = 0.0;
+    unsigned long long b = opaque_bits(c);
+    if ((b << 1) == 0ull) b = 0ull;  // -0 -> +0
     GtThreshold t;
-    t.bits = (unsigned long long)__double_as_longlong(c);
-    t.neg = c < 0.0;
+    t.bits = b;
+    t.neg = (b >> 63) != 0ull;
     return t;
 }
 __device__ __forceinline__ bool gt_bits(unsigned long long ybits, const GtThreshold& t) {

@@ -8,8 +8,8 @@
 //
 //   pass 0   start:  CQK_INIT_FORMULA  sum y and max y (l1: |y|) -> lambda_0 of
 //                                      eq. (CQKlambda0), clamped by line 1 of Alg. 4
-//                    CQK_INIT_CONDAT   Alg. 2 on every warp's chunk (exact, see
-//                                      condat_chunk); lambda_0 from eq. (lambdaJ) on the
+//                    CQK_INIT_CONDAT   Alg. 2 on every block's chunk (exact, see
+//                                      condat_block); lambda_0 from eq. (lambdaJ) on the
 //                                      union of the J's (Sec. 4)
 //   pass k   phi(lambda_k) = sum_{y_i > -lambda_k} (y_i + lambda_k),
 //            phi'_- = #{y_i > -lambda_k}, phi'_+ = #{y_i >= -lambda_k}
@@ -24,15 +24,13 @@
 #include <string.h>
 
 #include "cqk_batch.cuh"
+#include "cqk_stage.cuh"
 
 namespace cqk {
 namespace {
 
 constexpr int kStreamU = 8;  // 16-byte vectors in flight per lane in the streaming passes
 
-// vectors per lane in one Alg. 2 tile: a tile is 512 elements for FP64 and FP32 data
-template <typename T>
-__host__ __device__ constexpr int condat_k() { return 512 / (32 * VecOf<T>::V); }
 
 struct SimplexArgs {
     int64_t n;
@@ -56,21 +54,83 @@ struct SimplexArgs {
     double* part;  // [2][kPartialQ][gridDim.x]
 };
 
-// ---- Alg. 2 on one warp's chunk -----------------------------------------------------------
-// The chunk of warp w (of W) is the set of tiles t = w, w + W, w + 2W, ...; tile t holds
-// elements [t*TILE, (t+1)*TILE), TILE = 32 * K * V, scanned in increasing index order.
-// Lane L holds vectors t*32*K + k*32 + L (k < K), so the index order in a tile is (k, L, j).
+// ---- sum and max of y (l1: |y|) and the NaN check, accumulated per element -----------------
+// FP64 data: values in the df operating range go to a lazily normalised float pair that is
+// folded into FP64 once per tile or sweep; others are added in FP64 (one trip per element).
+// FP32 data: a double-float sum.  The maximum is kept as an order key (integer pipe).
+struct SumAcc {
+    df acc;
+    LazyDf lz;
+    double acc64, acc_wide;
+    long long mxk;
+    float mxf;
+    bool bad;
+    __device__ void init() {
+        acc = df_make(0.0f);
+        lz = LazyDf{0.0f, 0.0f};
+        acc64 = acc_wide = 0.0;
+        mxk = order_key(-INFINITY);
+        mxf = -INFINITY;
+        bad = false;
+    }
+    __device__ void fold() {
+        acc64 += df_to_f64_int(df{lz.hi, lz.lo});
+        lz = LazyDf{0.0f, 0.0f};
+    }
+    __device__ double sum() const { return df_to_f64(acc) + acc64 + df_to_f64_int(df{lz.hi, lz.lo}) + acc_wide; }
+};
+
+// one element; returns true when an FP64 value lies outside the df range (the caller adds it
+// with sum_wide)
+template <typename T, bool L1>
+__device__ __forceinline__ bool sum_elem(SumAcc& a, T v) {
+    if constexpr (sizeof(T) == 8) {
+        const double t = L1 ? __longlong_as_double((long long)(bits_of(v) & 0x7FFFFFFFFFFFFFFFull)) : (double)v;
+        const bool inr = df_in_range(t, false);
+        const df st = split_f64_finite(t);
+        lazy_add(a.lz, df{inr ? st.hi : 0.0f, inr ? st.lo : 0.0f});
+        a.bad |= f64_is_nan(t);
+        const long long kk = order_key(t);
+        a.mxk = kk > a.mxk ? kk : a.mxk;
+        return !inr;
+    } else {
+        const float t = L1 ? fabsf((float)v) : (float)v;
+        a.acc = df_add_f(a.acc, t);
+        a.bad |= (t != t);
+        a.mxf = fmaxf(a.mxf, t);
+        return false;
+    }
+}
+template <typename T, bool L1>
+__device__ __forceinline__ void sum_wide(SumAcc& a, T v) {
+    a.acc_wide += L1 ? fabs((double)v) : (double)v;
+}
+template <typename T>
+__device__ __forceinline__ double sum_max(const SumAcc& a) {
+    if constexpr (sizeof(T) == 8) return from_order_key(a.mxk);
+    else return (double)a.mxf;
+}
+
+// ---- Alg. 2 on one block's chunk ----------------------------------------------------------
+// The chunk of block m (of W chunk blocks) is the set of tiles c = c0 + m, c0 + m + W, ...;
+// tile c holds elements [c*TILE, (c+1)*TILE) (16 KB), scanned in increasing index order.  The
+// tiles stream into shared memory by bulk copies (kCondatStages stages, bounded waits).
 //
 // Exactness: both branches of the first loop of Alg. 2 lower lambda (adding j with
 // y_j + lambda > 0 gives lambda - (y_j + lambda)/(|J|+1); a restart gives r - y_j, below the
 // rejected lambda_{J u {j}}), so once J is started an element that fails the test fails it
-// for the rest of the scan.  The warp therefore tests a whole slab at once, processes the
-// first passing element in index order with the scalar update (the same FP64 operations as
-// a sequential scan), and re-tests only the later elements of the slab.  The final loop of
-// Alg. 2 over J~ visits, in order, the elements of J~ that pass the test with the current
-// lambda; every element before the last restart that is not in J~ failed the test with a
-// larger lambda and fails it again, so that loop is a re-scan of the chunk prefix before
-// the last restart with the same test.
+// for the rest of the scan.  All threads of the block therefore filter the tile with the
+// threshold of the multiplier current at the start of the tile (a superset of the elements
+// the scan can accept) and warp 0 runs the sequential scan over the passing elements only,
+// in index order: it takes the first passing element with the scalar update (the same FP64
+// operations as a sequential scan), re-tests the later ones, and publishes the new
+// threshold.  Before J is started every element passes (the first element of the chunk
+// starts J unconditionally).  The final loop of Alg. 2 over J~ visits, in order, the elements
+// of J~ that pass the test with the current lambda.  J~ is the set of values accepted before
+// the last restart; warp 0 keeps every accepted value in acceptance (= index) order, so the
+// loop runs over that list.  When J~ outgrows the list, the loop is a re-scan of the chunk
+// prefix before the last restart with the same test instead: every element there that is
+// not in J~ failed the test with a larger lambda and fails it again.
 template <typename T, bool L1>
 __device__ __forceinline__ bool condat_test(T v, const GtThreshold& g, float rd) {
     // exact test "y > c" (l1: "|y| > c") on the bit pattern / against the rounded-down threshold
@@ -88,35 +148,218 @@ __device__ __forceinline__ bool condat_test(T v, const GtThreshold& g, float rd)
 template <bool L1>
 __device__ __forceinline__ double condat_c(double lam) { return L1 ? fmax(0.0, -lam) : -lam; }
 
-// Warp-uniform state of one chunk's scan: lambda_J, sum_J y, |J|, the index of the last
-// restart, and the test threshold derived from lambda (recomputed only when lambda changes,
-// which keeps FP64 instructions off the per-slab path).
-struct CondatState {
-    double lam, S;
-    long long nJ;
-    int64_t rs;
-    GtThreshold g;
-    float rd;
+constexpr int kCondatStages = 5;
+template <typename T>
+__host__ __device__ constexpr int condat_tile() { return 16384 / (int)sizeof(T); }  // elements per tile
+constexpr size_t kCondatSmem = (size_t)kCondatStages * 16384;                      // dynamic shared memory
+constexpr int kJList = 1024;  // accepted values kept for the final loop
+
+struct CondatShared {
+    unsigned msk[NWARP][16];  // filter ballots of each warp, (k, j) -> bit lane
+    double list[kJList];
+    unsigned long long tb;    // the published test threshold
+    int tneg;
+    float trd;
 };
 
-template <bool L1>
-__device__ __forceinline__ void condat_set_lam(CondatState& st, double lam) {
-    st.lam = lam;
-    const double c = condat_c<L1>(lam);
-    st.g = make_gt(c);
-    st.rd = f32_rd(c);
+// ---- the scalar recurrence of Alg. 2 --------------------------------------------------------
+// The scan is one long dependency chain (lambda_{k+1} from lambda_k), and on this GPU every
+// dependent FP64 operation costs ~100 cycles (a chain update with one division measured
+// ~1150 cycles).  The decisions of the scan — y_j + lambda > 0 and the restart test
+// lambda_{J u {j}} < r - y_j — are therefore taken in double-float (FP32 pipe, error below
+// `band`) whenever the margin exceeds the bound, and otherwise from the exact FP64 values of
+// the sequential scan, recomputed from their exact operands: the FP64 sum S of J is kept in
+// the scan's order alongside its double-float copy.  The decisions, hence J, J~, |J| and S,
+// are those of the FP64 scan.
+struct CondatState {
+    double S;  // exact: the FP64 sum of J in scan order
+    df Sd;     // S in double-float
+    long long nJ;
+    int64_t rs;
+    df lam;       // lambda in double-float
+    float band;   // bound on |lam - lambda|
+    float sderr;  // bound on |Sd - S|
+    bool sdok;    // every y of J in the double-float range (Sd meaningful)
+    bool dfok;    // r and every y of J in the double-float range (else decisions are taken in FP64)
+    // lambda = fl(fl(fl(r - eS) - ey) / en) when en > 0, fl(r - ey) when en == 0
+    double eS, ey;
+    long long en;
+    // floats rounded outward around c(lambda): v > chi certainly passes, v <= clo certainly
+    // fails (as doubles); in between the exact FP64 threshold decides
+    float clo, chi;
+    GtThreshold glo, ghi;
+    double* list;
+    int cnt, jt_end;
+};
+
+__device__ __forceinline__ df df_of_count(long long n) {  // exact for n < 2^36, normalised
+    if (n < (1ll << 24)) return df{(float)n, 0.0f};
+    const long long h = n & ~0xFFFll;
+    return df{(float)h, (float)(n - h)};
 }
 
+// lambda_J u {y} = (r - S - y)/(|J| + 1) with S, y the exact operands; lambda = r - y when
+// restart is set (then S is unused)
+template <bool L1>
+__device__ __forceinline__ void condat_bounds(CondatState& st);
+
+template <bool L1>
+__device__ __forceinline__ void condat_lam(CondatState& st, double r, df rd, double S, df Sd, double y, df yd,
+                                           long long n_new, bool restart) {
+    st.eS = S;
+    st.ey = y;
+    st.en = restart ? 0 : n_new;
+    if (restart) {
+        st.lam = df_add(rd, df_neg(yd));
+        st.band = 2.8e-14f * (fabsf(rd.hi) + fabsf(yd.hi)) + 1e-37f;
+    } else {
+        const df num = df_add(df_add(rd, df_neg(Sd)), df_neg(yd));
+        // 1/n as a float pair (n < 2^24 exactly representable; ~2^-46 relative), then one
+        // double-float product: cheaper than a double-float division
+        const float nf = (float)n_new;
+        const float r0 = __frcp_rn(nf);
+        const float e0 = fmaf(-nf, r0, 1.0f);
+        const df inv = fast_two_sum(r0, __fmul_rn(r0, e0));
+        st.lam = df_mul(num, inv);
+        const float scale = 9.1e-13f * (fabsf(rd.hi) + fabsf(Sd.hi) + fabsf(yd.hi)) + 2.0f * st.sderr;
+        st.band = __fmul_ru(scale, __fmul_ru(r0, 1.0000001f)) + 9.1e-13f * fabsf(st.lam.hi) + 1e-37f;
+        if (n_new >= (1ll << 24)) st.band = INFINITY;  // n not exact in a float: FP64 decides
+    }
+    condat_bounds<L1>(st);
+}
+
+// c(lambda) = -lambda (l1: max{0, -lambda}) in double-float
+template <bool L1>
+__device__ __forceinline__ df condat_cdf(df lam) {
+    df c = df_neg(lam);
+    if (L1 && c.hi < 0.0f) c = df{0.0f, 0.0f};
+    return c;
+}
+
+template <bool L1>
+__device__ __forceinline__ void condat_bounds(CondatState& st) {
+    const df c = condat_cdf<L1>(st.lam);
+    float lo = __fsub_rd(__fadd_rd(c.hi, c.lo), st.band);
+    float hi = __fadd_ru(__fadd_ru(c.hi, c.lo), st.band);
+    if (!(st.dfok && st.sdok && lo == lo && hi == hi && fabsf(lo) < 1e30f && fabsf(hi) < 1e30f)) {
+        st.clo = -INFINITY;  // no certain decision: every test goes to FP64
+        st.chi = INFINITY;
+        st.glo = make_gt(-INFINITY);
+        st.ghi = make_gt(INFINITY);
+        return;
+    }
+    st.clo = lo;
+    st.chi = hi;
+    st.glo = make_gt(f32_to_f64_bits(lo));
+    st.ghi = make_gt(f32_to_f64_bits(hi));
+}
+
+// The exact FP64 decisions, out of line: inlined, the compiler evaluates the FP64 division
+// speculatively on every test (measured: ~2400 cycles per test instead of a few).
+template <bool L1>
+__device__ __noinline__ bool condat_exact_gt(unsigned long long vb, double eS, double ey, long long en, double r) {
+    const double le = en == 0 ? r - ey : ((r - eS) - ey) / (double)en;
+    unsigned long long cb = opaque_bits(le) ^ 0x8000000000000000ull;
+    if (L1 && (cb >> 63)) cb = 0ull;
+    return gt_bits(vb, make_gt(__longlong_as_double((long long)cb)));
+}
+__device__ __noinline__ bool condat_exact_accepts(double eS, double ey, long long en, double r, double y) {
+    const double le = en == 0 ? r - ey : ((r - eS) - ey) / (double)en;
+    return le < r - y;
+}
+
+// the test v > c(lambda) of the FP64 scan (v = y_j, l1: |y_j|)
+template <bool L1>
+__device__ __forceinline__ bool condat_gt(double v, const CondatState& st, double r) {
+    const unsigned long long vb = opaque_bits(v);
+    if (gt_bits(vb, st.ghi)) return true;
+    if (!gt_bits(vb, st.glo)) return false;
+    return condat_exact_gt<L1>(vb, st.eS, st.ey, st.en, r);  // rare
+}
+
+// the restart test of Alg. 2: accept y (J <- J u {y}) iff lambda_{J u {y}} < r - y
+__device__ __forceinline__ bool condat_accepts(const CondatState& nx, double r, df rd, double y, df yd) {
+    if (nx.dfok && nx.sdok && df_in_range(y, false)) {
+        const df rmy = df_add(rd, df_neg(yd));
+        const df d = df_add(nx.lam, df_neg(rmy));
+        const float bd = nx.band + 2.8e-14f * (fabsf(rd.hi) + fabsf(yd.hi));
+        if (d.hi < -bd) return true;
+        if (d.hi > bd) return false;
+    }
+    return condat_exact_accepts(nx.eS, nx.ey, nx.en, r, y);  // rare: exact FP64
+}
+
+__device__ __forceinline__ void condat_record(CondatState& st, double v) {
+    if ((threadIdx.x & 31) == 0 && st.cnt < kJList) st.list[st.cnt] = v;
+    st.cnt++;
+}
+
+// one element taken by the first loop of Alg. 2 (J started): add it or restart with it
+template <bool L1>
+__device__ __forceinline__ void condat_take(CondatState& st, double r, df rd, double y, int64_t e) {
+    const df yd = split_f64(y);
+    CondatState nx = st;
+    condat_lam<L1>(nx, r, rd, st.S, st.Sd, y, yd, st.nJ + 1, false);
+    if (condat_accepts(nx, r, rd, y, yd)) {
+        st.lam = nx.lam;
+        st.band = nx.band;
+        st.eS = nx.eS;
+        st.ey = nx.ey;
+        st.en = nx.en;
+        st.clo = nx.clo;
+        st.chi = nx.chi;
+        st.glo = nx.glo;
+        st.ghi = nx.ghi;
+        st.S += y;
+        st.Sd = df_add(st.Sd, yd);
+        st.sderr += 2.8e-14f * (fabsf(st.Sd.hi) + fabsf(yd.hi));
+        st.sdok = st.sdok && df_in_range(y, false);
+        st.nJ += 1;
+    } else {  // restart: J~ <- J~ u J, J <- {j}
+        st.rs = e;
+        st.S = y;
+        st.Sd = yd;
+        st.sderr = 1.5e-14f * fabsf(yd.hi);
+        st.sdok = df_in_range(y, false);
+        st.nJ = 1;
+        condat_lam<L1>(st, r, rd, 0.0, yd, y, yd, 1, true);
+        st.jt_end = st.cnt;
+    }
+    condat_record(st, y);
+}
+
+// the final loop of Alg. 2: J <- J u {y} (no restart test)
+template <bool L1>
+__device__ __forceinline__ void condat_add(CondatState& st, double r, df rd, double y) {
+    const df yd = split_f64(y);
+    condat_lam<L1>(st, r, rd, st.S, st.Sd, y, yd, st.nJ + 1, false);
+    st.S += y;
+    st.Sd = df_add(st.Sd, yd);
+    st.sderr += 2.8e-14f * (fabsf(st.Sd.hi) + fabsf(yd.hi));
+    st.sdok = st.sdok && df_in_range(y, false);
+    st.nJ += 1;
+}
+
+// the block filter's threshold: a float at or below c(lambda) - band (a superset of the
+// elements the scan can accept), as a float (FP32 data) and as double bits (FP64 data)
+__device__ __forceinline__ float condat_filter_rd(const CondatState& st) { return st.clo; }
+
+// Warp 0: the first loop of Alg. 2 over one group of 32 vectors in index order (lane, j);
+// okv marks the elements that passed the block's filter.
 template <typename T, bool L1>
 __device__ __forceinline__ void condat_slab(const T (&vals)[VecOf<T>::V], const bool (&okv)[VecOf<T>::V],
-                                            int64_t eidx0, int64_t before, bool first_loop, double r,
-                                            CondatState& st) {
+                                            int64_t eidx0, double r, df rd, CondatState& st) {
     constexpr int V = VecOf<T>::V;
     const int lane = threadIdx.x & 31;
+    double av[V];
+#pragma unroll
+    for (int j = 0; j < V; j++) {
+        const double dv = (double)vals[j];
+        av[j] = L1 ? __longlong_as_double((long long)(opaque_bits(dv) & 0x7FFFFFFFFFFFFFFFull)) : dv;
+    }
     bool pass[V];
-    if (first_loop && st.nJ == 0) {
-        // the first element of the chunk (in (lane, j) order; a span may start inside a
-        // vector) starts J unconditionally (first line of Alg. 2)
+    if (st.nJ == 0) {
+        // the first element of the chunk starts J unconditionally (first line of Alg. 2)
         unsigned any_ok = 0, mo[V];
 #pragma unroll
         for (int j = 0; j < V; j++) {
@@ -129,21 +372,25 @@ __device__ __forceinline__ void condat_slab(const T (&vals)[VecOf<T>::V], const 
 #pragma unroll
         for (int j = V - 1; j >= 0; j--)
             if ((mo[j] >> L0) & 1u) j0 = j;
-        double y0 = (double)__shfl_sync(0xffffffffu, pick(vals, j0), L0);
-        if (L1) y0 = fabs(y0);
+        const double y0 = __shfl_sync(0xffffffffu, pick(av, j0), L0);
+        const df y0d = split_f64(y0);
         st.S = y0;
+        st.Sd = y0d;
+        st.sderr = 1.5e-14f * fabsf(y0d.hi);
+        st.sdok = df_in_range(y0, false);
         st.nJ = 1;
         st.rs = __shfl_sync(0xffffffffu, eidx0, L0) + j0;
-        condat_set_lam<L1>(st, r - y0);
+        condat_lam<L1>(st, r, rd, 0.0, y0d, y0, y0d, 1, true);
+        st.jt_end = st.cnt;
+        condat_record(st, y0);
 #pragma unroll
         for (int j = 0; j < V; j++) {
             const bool after = (lane > L0) || (lane == L0 && j > j0);
-            pass[j] = okv[j] && after && condat_test<T, L1>(vals[j], st.g, st.rd);
+            pass[j] = okv[j] && after && condat_gt<L1>(av[j], st, r);
         }
     } else {
 #pragma unroll
-        for (int j = 0; j < V; j++)
-            pass[j] = okv[j] && (eidx0 + j < before) && condat_test<T, L1>(vals[j], st.g, st.rd);
+        for (int j = 0; j < V; j++) pass[j] = okv[j] && condat_gt<L1>(av[j], st, r);
     }
     while (true) {
         unsigned m[V];
@@ -159,31 +406,53 @@ __device__ __forceinline__ void condat_slab(const T (&vals)[VecOf<T>::V], const 
 #pragma unroll
         for (int j = V - 1; j >= 0; j--)
             if ((m[j] >> Lf) & 1u) jf = j;
-        double yv = (double)__shfl_sync(0xffffffffu, pick(vals, jf), Lf);
-        if (L1) yv = fabs(yv);
+        const double yv = __shfl_sync(0xffffffffu, pick(av, jf), Lf);
         const int64_t e = __shfl_sync(0xffffffffu, eidx0, Lf) + jf;
-        if (first_loop) {
-            const double lamn = (r - st.S - yv) / (double)(st.nJ + 1);
-            if (lamn < r - yv) {
-                st.S += yv;
-                st.nJ += 1;
-                condat_set_lam<L1>(st, lamn);
-            } else {  // restart: J~ <- J~ u J, J <- {j}
-                st.rs = e;
-                st.S = yv;
-                st.nJ = 1;
-                condat_set_lam<L1>(st, r - yv);
-            }
-        } else {
-            const double lamn = (r - st.S - yv) / (double)(st.nJ + 1);
-            st.S += yv;
-            st.nJ += 1;
-            condat_set_lam<L1>(st, lamn);
-        }
+        condat_take<L1>(st, r, rd, yv, e);
 #pragma unroll
         for (int j = 0; j < V; j++) {
             const bool after = (lane > Lf) || (lane == Lf && j > jf);
-            pass[j] = pass[j] && after && condat_test<T, L1>(vals[j], st.g, st.rd);
+            pass[j] = pass[j] && after && condat_gt<L1>(av[j], st, r);
+        }
+    }
+}
+
+// warp 0, J~ outgrew the list: the final loop of Alg. 2 as a re-scan of one slab (32 vectors)
+// of the chunk prefix before the last restart
+template <typename T, bool L1>
+__device__ __forceinline__ void condat_rescan_slab(const T (&vals)[VecOf<T>::V], const bool (&okv)[VecOf<T>::V],
+                                                   int64_t eidx0, double r, df rd, CondatState& st) {
+    constexpr int V = VecOf<T>::V;
+    const int lane = threadIdx.x & 31;
+    double av[V];
+#pragma unroll
+    for (int j = 0; j < V; j++) {
+        const double dv = (double)vals[j];
+        av[j] = L1 ? __longlong_as_double((long long)(opaque_bits(dv) & 0x7FFFFFFFFFFFFFFFull)) : dv;
+    }
+    bool pass[V];
+#pragma unroll
+    for (int j = 0; j < V; j++) pass[j] = okv[j] && (eidx0 + j < st.rs) && condat_gt<L1>(av[j], st, r);
+    while (true) {
+        unsigned m[V];
+        unsigned any = 0;
+#pragma unroll
+        for (int j = 0; j < V; j++) {
+            m[j] = __ballot_sync(0xffffffffu, pass[j]);
+            any |= m[j];
+        }
+        if (!any) break;
+        const int Lf = __ffs(any) - 1;
+        int jf = 0;
+#pragma unroll
+        for (int j = V - 1; j >= 0; j--)
+            if ((m[j] >> Lf) & 1u) jf = j;
+        const double yv = __shfl_sync(0xffffffffu, pick(av, jf), Lf);
+        condat_add<L1>(st, r, rd, yv);
+#pragma unroll
+        for (int j = 0; j < V; j++) {
+            const bool after = (lane > Lf) || (lane == Lf && j > jf);
+            pass[j] = pass[j] && after && condat_gt<L1>(av[j], st, r);
         }
     }
 }
@@ -202,44 +471,176 @@ __device__ __forceinline__ void support_mask(const T* __restrict__ xb, const Spa
     for (int j = 0; j < V; j++) okv[j] = okv[j] && (L1 ? xv[j] != T(0) : xv[j] > T(0));
 }
 
-template <typename T, bool L1>
-__device__ void condat_chunk(const T* __restrict__ y, const T* __restrict__ xb, const Span& sp, bool aligned,
-                             double r, int64_t w, int64_t W, double& S_out, long long& nJ_out) {
+// the V values of tile vector ql (from the stage when the bulk copy delivered it, else directly)
+template <typename T>
+__device__ __forceinline__ void tile_vec(const T* __restrict__ y, const Span& sp, const T* stage, bool staged,
+                                         int64_t c, int ql, int64_t sb0, int64_t sb1, T (&v)[VecOf<T>::V],
+                                         bool (&ok)[VecOf<T>::V]) {
     constexpr int V = VecOf<T>::V;
-    constexpr int K = condat_k<T>();
-    constexpr int TILE = 32 * K * V;
-    const int lane = threadIdx.x & 31;
-    const int64_t t0 = sp.lo / TILE, ntiles = (sp.hi + TILE - 1) / TILE;
+    constexpr int TT = condat_tile<T>();
+    using VT = typename VecOf<T>::type;
+    const int64_t q = c * (TT / V) + ql;
+    if (staged && q * V >= sb0 && (q + 1) * V <= sb1) {
+        const VT w = reinterpret_cast<const VT*>(stage)[ql];
+#pragma unroll
+        for (int j = 0; j < V; j++) {
+            v[j] = reinterpret_cast<const T*>(&w)[j];
+            ok[j] = true;
+        }
+    } else {
+        load_vec<T>(y, sp, q, false, v, ok);
+    }
+}
+
+// Alg. 2 on the chunk of block `member` of `nchunk` (blocks with member >= nchunk have none).
+// Called by all threads; (S_out, nJ_out) = (sum_J y, |J|) valid in thread 0.  With SUM the
+// same pass also accumulates the sum and maximum of y (l1: |y|) into sacc (the chunks of all
+// blocks cover the span once; blocks without a chunk add nothing).
+//
+// Per tile: every thread tests its KC vectors against the published threshold and the warps
+// store their ballots; a block vote skips the rest of the tile when nothing passed (the usual
+// case once lambda is close); otherwise warp 0 walks the passing elements in index order
+// (k, warp, lane, j), re-reading their values from the stage, with the exact scan.
+template <typename T, bool L1, bool SUM>
+__device__ void condat_block(const T* __restrict__ y, const T* __restrict__ xb, const Span& sp, bool aligned,
+                             double r, int member, int nchunk, T* smem, uint64_t* bars, unsigned& parity, int* err,
+                             unsigned long long limit_ns, SumAcc& sacc, double& S_out, long long& nJ_out) {
+    constexpr int V = VecOf<T>::V;
+    constexpr int TT = condat_tile<T>();
+    constexpr int KC = TT / V / NT;
+    static_assert(KC * V * NT == TT && KC * V <= 16, "tile layout");
+    __shared__ CondatShared s;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     CondatState st;
     st.S = 0.0;
+    st.Sd = df{0.0f, 0.0f};
     st.nJ = 0;
     st.rs = -1;
-    condat_set_lam<L1>(st, 0.0);
-    for (int64_t t = t0 + w; t < ntiles; t += W) {
-        T vals[K][V];
-        bool okv[K][V];
-#pragma unroll
-        for (int k = 0; k < K; k++) load_vec<T>(y, sp, t * 32 * K + k * 32 + lane, aligned, vals[k], okv[k]);
-#pragma unroll
-        for (int k = 0; k < K; k++) support_mask<T, L1>(xb, sp, t * 32 * K + k * 32 + lane, aligned, okv[k]);
-#pragma unroll
-        for (int k = 0; k < K; k++)
-            condat_slab<T, L1>(vals[k], okv[k], (t * 32 * K + k * 32 + lane) * V, INT64_MAX, true, r, st);
+    st.lam = df{0.0f, 0.0f};
+    st.band = 0.0f;
+    st.sderr = 0.0f;
+    st.sdok = true;
+    st.dfok = df_in_range(r, false) && r != 0.0;
+    st.eS = st.ey = 0.0;
+    st.en = 0;
+    st.clo = -INFINITY;
+    st.chi = INFINITY;
+    st.glo = make_gt(-INFINITY);
+    st.ghi = make_gt(INFINITY);
+    st.list = s.list;
+    st.cnt = 0;
+    st.jt_end = 0;
+    const df rdf = split_f64(r);
+    if (threadIdx.x == 0) {  // before J starts every element passes the filter
+        const GtThreshold g0 = make_gt(-INFINITY);
+        s.tb = g0.bits;
+        s.tneg = 1;
+        s.trd = -INFINITY;
     }
-    // final loop of Alg. 2: re-scan the chunk prefix before the last restart
-    if (st.nJ > 0 && st.rs >= 0) {
-        const int64_t tlast = st.rs / TILE;
-        const int64_t before = st.rs;
-        for (int64_t t = t0 + w; t <= tlast; t += W) {
-            T vals[K][V];
-            bool okv[K][V];
+    TileRing<T, 1, TT> ring;
+    ring.setup(sp.lo, sp.hi, smem, bars, member, nchunk);
+    if (member >= nchunk) ring.count = 0;
+    ring.parity = parity;
+    const bool staged = aligned;
+    const T* src[1] = {y};
+    __syncthreads();
+    if (staged && threadIdx.x == 0)
+        for (int k = 0; k < kCondatStages - 1; k++)
+            if (k < ring.count) ring.issue(ring.tile(k, false), k, src);
+    for (int64_t i = 0; i < ring.count; i++) {
+        const int stg = (int)(i % kCondatStages);
+        if (staged) {
+            if (threadIdx.x == 0 && i + kCondatStages - 1 < ring.count)
+                ring.issue(ring.tile(i + kCondatStages - 1, false), (int)((i + kCondatStages - 1) % kCondatStages), src);
+            mbar_wait(&ring.bar[stg], (ring.parity >> stg) & 1u, err, limit_ns, CQK_TIMEOUT);
+            ring.parity ^= 1u << stg;
+        }
+        const int64_t c = ring.tile(i, false);
+        const int64_t sb0 = staged ? ring.b0(c) : 0, sb1 = staged ? ring.b1(c) : 0;
+        const T* stage = ring.stage(stg, 0);
+        const GtThreshold g{s.tb, s.tneg != 0};
+        const float rd = s.trd;
+        bool anyp = false;
 #pragma unroll
-            for (int k = 0; k < K; k++) load_vec<T>(y, sp, t * 32 * K + k * 32 + lane, aligned, vals[k], okv[k]);
+        for (int k = 0; k < KC; k++) {
+            const int ql = k * NT + (int)threadIdx.x;
+            T v[V];
+            bool ok[V];
+            tile_vec<T>(y, sp, stage, staged, c, ql, sb0, sb1, v, ok);
+            if constexpr (SUM) {
+                unsigned widem = 0;
 #pragma unroll
-            for (int k = 0; k < K; k++) support_mask<T, L1>(xb, sp, t * 32 * K + k * 32 + lane, aligned, okv[k]);
+                for (int j = 0; j < V; j++)
+                    if (ok[j] && sum_elem<T, L1>(sacc, v[j])) widem |= 1u << j;
+                for (unsigned m = widem; m; m &= m - 1) sum_wide<T, L1>(sacc, pick(v, __ffs(m) - 1));
+            }
+            support_mask<T, L1>(xb, sp, c * (TT / V) + ql, aligned, ok);
 #pragma unroll
-            for (int k = 0; k < K; k++)
-                condat_slab<T, L1>(vals[k], okv[k], (t * 32 * K + k * 32 + lane) * V, before, false, r, st);
+            for (int j = 0; j < V; j++) {
+                const bool p = ok[j] && condat_test<T, L1>(v[j], g, rd);
+                const unsigned bal = __ballot_sync(0xffffffffu, p);
+                if (lane == 0) s.msk[wid][k * V + j] = bal;
+                anyp |= p;
+            }
+        }
+        if constexpr (SUM && sizeof(T) == 8) sacc.fold();
+        // a tile with no survivor needs no scan (the vote is also the barrier after which the
+        // stage may be refilled and the ballots rewritten)
+        if (!__syncthreads_or(anyp)) continue;
+        if (wid == 0) {
+            // lane g looks at group g = (k, w) of 32 vectors; the groups are visited in order
+            static_assert(KC * NWARP <= 32, "one lane per group");
+            unsigned gany = 0;
+            if (lane < KC * NWARP)
+#pragma unroll
+                for (int j = 0; j < V; j++) gany |= s.msk[lane % NWARP][(lane / NWARP) * V + j];
+            for (unsigned groups = __ballot_sync(0xffffffffu, gany != 0u); groups; groups &= groups - 1) {
+                const int gi = __ffs(groups) - 1;
+                const int k = gi / NWARP, w = gi % NWARP;
+                unsigned mj[V];
+#pragma unroll
+                for (int j = 0; j < V; j++) mj[j] = s.msk[w][k * V + j];
+                {
+                    const int ql = k * NT + w * 32 + lane;
+                    T v[V];
+                    bool ok[V];
+                    tile_vec<T>(y, sp, stage, staged, c, ql, sb0, sb1, v, ok);
+#pragma unroll
+                    for (int j = 0; j < V; j++) ok[j] = ((mj[j] >> lane) & 1u) != 0u;
+                    condat_slab<T, L1>(v, ok, (c * (TT / V) + ql) * V, r, rdf, st);
+                }
+            }
+            if (lane == 0 && st.nJ > 0) {
+                const float fr = condat_filter_rd(st);
+                const GtThreshold gf = st.glo;
+                s.tb = gf.bits;
+                s.tneg = gf.neg ? 1 : 0;
+                s.trd = fr;
+            }
+        }
+        __syncthreads();
+    }
+    parity = ring.parity;
+    // final loop of Alg. 2 over J~ (warp 0)
+    if (wid == 0 && st.nJ > 0) {
+        if (st.jt_end <= kJList) {
+            __syncwarp();
+            for (int e = 0; e < st.jt_end; e++) {
+                const double val = st.list[e];
+                if (condat_gt<L1>(val, st, r)) condat_add<L1>(st, r, rdf, val);
+            }
+        } else if (st.rs >= 0) {
+            const int64_t c0 = sp.lo / TT;
+            for (int64_t c = c0 + member; c * TT <= st.rs; c += nchunk) {
+                for (int sl = 0; sl < TT / V / 32; sl++) {
+                    const int64_t q = c * (TT / V) + sl * 32 + lane;
+                    T vals[V];
+                    bool okv[V];
+                    load_vec<T>(y, sp, q, aligned, vals, okv);
+                    support_mask<T, L1>(xb, sp, q, aligned, okv);
+                    condat_rescan_slab<T, L1>(vals, okv, q * V, r, rdf, st);
+                }
+            }
         }
     }
     S_out = st.S;
@@ -372,7 +773,8 @@ __device__ __forceinline__ void warp0_grid_sums(const double* part, int G, int p
 // A supplies the arrays, r, the options and the info slot; gp the group (member, size, span,
 // header and partial sums).  The instance is the span [gp.sp.lo, gp.sp.hi) of y and x.
 template <typename T, bool L1>
-__device__ __forceinline__ void simplex_solve(const SimplexArgs& A, const Grp& gp) {
+__device__ __forceinline__ void simplex_solve(const SimplexArgs& A, const Grp& gp, T* smem, uint64_t* bars,
+                                              unsigned& ring_parity) {
     constexpr int V = VecOf<T>::V;
     __shared__ double sh[kPartialQ][NWARP];
     __shared__ double bc[kPartialQ];
@@ -387,8 +789,6 @@ __device__ __forceinline__ void simplex_solve(const SimplexArgs& A, const Grp& g
     const int64_t qlo = span_qlo<V>(sp), qhi = span_qhi<V>(sp);
     const int lane = threadIdx.x & 31;
     const int G = gp.g;
-    const int64_t gwarp = (int64_t)gp.member * NWARP + (threadIdx.x >> 5);
-    const int64_t nwarps = (int64_t)G * NWARP;
     const bool aligned = A.aligned != 0;
     unsigned bar_target = (unsigned)G + (A.fault_inject ? 1u : 0u);
     const double r = A.r;
@@ -400,15 +800,13 @@ __device__ __forceinline__ void simplex_solve(const SimplexArgs& A, const Grp& g
         double q[4] = {0.0, 0.0, 0.0, -INFINITY};  // sum y (l1: |y|), union sum, union size, max y (l1: |y|)
         const bool warm = A.init == CQK_INIT_WARM;
         const bool condat = A.init == CQK_INIT_CONDAT || warm;
-        const bool sum_pass = L1 || !condat;
+        // the l1 ball needs sum |y| (inside test) and the formula start sum y and max y; with
+        // the Alg. 2 start the l1 sums ride on the Alg. 2 pass
+        const bool sum_pass = !condat;
         bool bad = false;
+        SumAcc sacc;
+        sacc.init();
         if (sum_pass) {
-            df acc = df_make(0.0f);       // FP32 data
-            LazyDf lz{0.0f, 0.0f};        // FP64 data in the df operating range, flushed into acc64
-            double acc64 = 0.0;
-            double acc_wide = 0.0;  // FP64 values outside the df operating range
-            long long mxk = order_key(-INFINITY);
-            float mxf = -INFINITY;
             const WarpSweep sw(qlo, qhi, kStreamU, gp.member, gp.g);
             for (int64_t it = 0; it < sw.count; it++) {
                 const int64_t base = sw.base(it, false);
@@ -420,56 +818,33 @@ __device__ __forceinline__ void simplex_solve(const SimplexArgs& A, const Grp& g
 #pragma unroll
                 for (int uj = 0; uj < kStreamU * V; uj++) {
                     const int u = uj / V, j = uj % V;
-                    if (!okk[u][j]) continue;
-                    if constexpr (sizeof(T) == 8) {
-                        const double t = L1 ? __longlong_as_double((long long)(bits_of(vv[u][j]) & 0x7FFFFFFFFFFFFFFFull))
-                                            : (double)vv[u][j];
-                        const bool inr = df_in_range(t, false);
-                        const df st = split_f64_finite(t);
-                        lazy_add(lz, df{inr ? st.hi : 0.0f, inr ? st.lo : 0.0f});
-                        widem |= (inr ? 0u : 1u) << uj;
-                        bad |= f64_is_nan(t);
-                        const long long kk = order_key(t);
-                        mxk = kk > mxk ? kk : mxk;
-                    } else {
-                        const float t = L1 ? fabsf((float)vv[u][j]) : (float)vv[u][j];
-                        acc = df_add_f(acc, t);
-                        bad |= (t != t);
-                        mxf = fmaxf(mxf, t);
-                    }
+                    if (okk[u][j] && sum_elem<T, L1>(sacc, vv[u][j])) widem |= 1u << uj;
                 }
                 if constexpr (sizeof(T) == 8) {
                     // values outside the df operating range: exact FP64, one trip per element
-                    for (unsigned m = widem; m; m &= m - 1) {
-                        const T tv = pick2(vv, __ffs(m) - 1);
-                        acc_wide += L1 ? fabs((double)tv) : (double)tv;
-                    }
+                    for (unsigned m = widem; m; m &= m - 1) sum_wide<T, L1>(sacc, pick2(vv, __ffs(m) - 1));
                     // fold the lazy pair (at most 64 terms) into FP64: one FP64 add per 4 sweeps
-                    if ((it & 3) == 3) {
-                        acc64 += df_to_f64_int(df{lz.hi, lz.lo});
-                        lz = LazyDf{0.0f, 0.0f};
-                    }
+                    if ((it & 3) == 3) sacc.fold();
                 }
             }
-            if constexpr (sizeof(T) == 8) acc64 += df_to_f64_int(df{lz.hi, lz.lo});
-            q[0] = df_to_f64(acc) + acc64 + acc_wide;
-            if constexpr (sizeof(T) == 8) q[3] = from_order_key(mxk);
-            else q[3] = (double)mxf;
             passes++;
         }
         // chunks of at least condat_chunk elements (the J updates are scalar FP64 work, which
-        // a partition into many small chunks multiplies), at most one per warp
-        const int64_t nchunk = min(nwarps, max((int64_t)1, (n + A.condat_chunk - 1) / A.condat_chunk));
+        // a partition into many small chunks multiplies, and larger chunks give a better
+        // lambda_0), at most one per block
+        const int nchunk = (int)min((int64_t)G, max((int64_t)1, (n + A.condat_chunk - 1) / A.condat_chunk));
         if (condat) {
             double Sw = 0.0;
             long long nJw = 0;
-            if (gwarp < nchunk)
-                condat_chunk<T, L1>(y, warm ? static_cast<const T*>(A.xbar) : nullptr, sp, aligned, r, gwarp, nchunk,
-                                    Sw, nJw);
-            q[1] = lane == 0 ? Sw : 0.0;
-            q[2] = lane == 0 ? (double)nJw : 0.0;
+            condat_block<T, L1, L1>(y, warm ? static_cast<const T*>(A.xbar) : nullptr, sp, aligned, r, gp.member,
+                                    nchunk, smem, bars, ring_parity, &gp.hdr->error, A.limit_ns, sacc, Sw, nJw);
+            q[1] = threadIdx.x == 0 ? Sw : 0.0;
+            q[2] = threadIdx.x == 0 ? (double)nJw : 0.0;
             passes++;
         }
+        bad = sacc.bad;
+        q[0] = sacc.sum();
+        q[3] = sum_max<T>(sacc);
         const int wid = threadIdx.x >> 5;
         const double s0 = warp_sum(q[0]), s1 = warp_sum(q[1]), s2 = warp_sum(q[2]), m = warp_max(q[3]);
         const unsigned badw = __ballot_sync(0xffffffffu, bad);
@@ -504,13 +879,13 @@ __device__ __forceinline__ void simplex_solve(const SimplexArgs& A, const Grp& g
         if (condat && red[2] > 0.0) {
             lam0 = (r - red[1]) / red[2];  // eq. (lambdaJ) on the union of the chunks' J
             nchunks = (int)nchunk;
-            tile = 32 * condat_k<T>() * V;
+            tile = condat_tile<T>();
         } else if (condat) {
             // warm start with an empty J_+ (no element of the estimate's support): Sec. 3.3
             const double y1 = (double)y[sp.lo];
             lam0 = fmax(r / (double)n, L1 ? -fabs(y1) : -y1);
             nchunks = (int)nchunk;
-            tile = 32 * condat_k<T>() * V;
+            tile = condat_tile<T>();
         } else if (A.init == CQK_INIT_GIVEN) {
             lam0 = fmax(A.lambda0, -red[3]);  // Alg. 4, line 1
         } else {
@@ -738,15 +1113,29 @@ __device__ __forceinline__ void simplex_solve(const SimplexArgs& A, const Grp& g
     }
 }
 
+// the bulk-copy stages of the Alg. 2 start: kCondatSmem bytes of dynamic shared memory and
+// their mbarriers, initialised once per block
+__device__ __forceinline__ void init_condat_bars(uint64_t* bars) {
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < kCondatStages; k++) mbar_init(&bars[k], 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+}
+
 template <typename T, bool L1>
 __global__ void __launch_bounds__(NT, 2) simplex_kernel(SimplexArgs A) {
+    extern __shared__ __align__(128) unsigned char dyn_smem[];
+    __shared__ uint64_t bars[kCondatStages];
+    unsigned parity = 0;
+    init_condat_bars(bars);
     Grp gp;
     gp.member = blockIdx.x;
     gp.g = gridDim.x;
     gp.sp = Span{0, A.n};
     gp.hdr = A.hdr;
     gp.part = A.part;
-    simplex_solve<T, L1>(A, gp);
+    simplex_solve<T, L1>(A, gp, reinterpret_cast<T*>(dyn_smem), bars, parity);
 }
 
 // A batch: blocks take (instance, member) slots from the queue until it is empty; every
@@ -763,6 +1152,10 @@ struct SimplexBatchArgs {
 
 template <typename T, bool L1>
 __global__ void __launch_bounds__(NT, 2) simplex_batched_kernel(SimplexBatchArgs P) {
+    extern __shared__ __align__(128) unsigned char dyn_smem[];
+    __shared__ uint64_t bars[kCondatStages];
+    unsigned parity = 0;
+    init_condat_bars(bars);
     while (true) {
         const Slot sl = next_slot(P.R, P.B);
         if (sl.inst < 0) break;
@@ -781,7 +1174,7 @@ __global__ void __launch_bounds__(NT, 2) simplex_batched_kernel(SimplexBatchArgs
             }
             continue;
         }
-        simplex_solve<T, L1>(A, gp);
+        simplex_solve<T, L1>(A, gp, reinterpret_cast<T*>(dyn_smem), bars, parity);
     }
 }
 
@@ -817,14 +1210,19 @@ int launch_simplex_batched(int64_t B, const int64_t* offsets, int dtype, const v
         kern = l1 ? (const void*)simplex_batched_kernel<double, true> : (const void*)simplex_batched_kernel<double, false>;
     else
         kern = l1 ? (const void*)simplex_batched_kernel<float, true> : (const void*)simplex_batched_kernel<float, false>;
-    int grid = persistent_grid(kern, NT, 0, INT64_MAX / 2, o.max_blocks);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCondatSmem);
+    if (e != cudaSuccess) {
+        set_last_cuda_error(e);
+        return CQK_CUDA_ERROR;
+    }
+    int grid = persistent_grid(kern, NT, kCondatSmem, INT64_MAX / 2, o.max_blocks);
     if (grid <= 0) return CQK_CUDA_ERROR;
     if ((int64_t)grid > B * kMaxGroup) grid = (int)(B * kMaxGroup);
     const int64_t per_block = o.group_elems > 0 ? o.group_elems : kSimplexGroupElems;
     int rc = plan_batch(offsets, B, per_block, grid, ws, s);
     if (rc != CQK_OK) return rc;
     void* args[] = {&P};
-    cudaError_t e = cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(NT), args, 0, s);
+    e = cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(NT), args, kCondatSmem, s);
     if (e != cudaSuccess) {
         set_last_cuda_error(e);
         return CQK_CUDA_ERROR;
@@ -861,15 +1259,20 @@ int launch_simplex(int64_t n, int dtype, const void* y, double r, int l1, void* 
     else
         kern = l1 ? (const void*)simplex_kernel<float, true> : (const void*)simplex_kernel<float, false>;
     const int64_t vec = dtype == CQK_F64 ? 2 : 4;
-    const int grid = persistent_grid(kern, NT, 0, (n + vec - 1) / vec, o.max_blocks);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCondatSmem);
+    if (e != cudaSuccess) {
+        set_last_cuda_error(e);
+        return CQK_CUDA_ERROR;
+    }
+    const int grid = persistent_grid(kern, NT, kCondatSmem, (n + vec - 1) / vec, o.max_blocks);
     if (grid <= 0) return CQK_CUDA_ERROR;
-    cudaError_t e = cudaMemsetAsync(ws, 0, sizeof(WsHeader), s);
+    e = cudaMemsetAsync(ws, 0, sizeof(WsHeader), s);
     if (e != cudaSuccess) {
         set_last_cuda_error(e);
         return CQK_CUDA_ERROR;
     }
     void* args[] = {&A};
-    e = cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(NT), args, 0, s);
+    e = cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(NT), args, kCondatSmem, s);
     if (e != cudaSuccess) {
         set_last_cuda_error(e);
         return CQK_CUDA_ERROR;

@@ -1,0 +1,61 @@
+"""GPU parity of the parallel Alg. 2 start (CQK_INIT_CONDAT) on inputs that put the scan's
+tests on a knife edge: integer-valued y (y_j + lambda = 0 and lambda_{J u {j}} = r - y_j hold
+exactly, so the double-float shortcut must defer to FP64), magnitudes outside the
+double-float range, and a large r.  lambda_0 must equal the oracle's chunked Alg. 2."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2603_15910_b300 import api
+from helpers import assert_x_close, np64
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+
+
+def _check(y, r, l1, dtype=torch.float64):
+    yt = torch.from_numpy(y).to(dtype)
+    y64 = np64(yt)
+    fn = api.project_l1 if l1 else api.project_simplex
+    x, info, _ = fn(yt.to(DEV), r, init=api.Init.CONDAT)
+    assert info.status == api.Status.OK, info
+    if l1:
+        lam, xstar, inside = oracle.project_l1(y64, r)
+        if inside:
+            return
+    else:
+        lam, xstar = oracle.project_simplex_sort(y64, r)
+    assert_x_close(np64(x), xstar, dtype)
+    l0, S, C = oracle.condat_chunks(y64, r, info.tile, info.nchunks, l1=l1)
+    assert math.isclose(info.lambda0, l0, rel_tol=1e-13, abs_tol=1e-300), (info.lambda0, l0, info)
+
+
+@pytest.mark.parametrize("l1", [False, True])
+@pytest.mark.parametrize("seed", range(4))
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_condat_integer_ties(seed, l1, dtype):
+    rng = np.random.default_rng(seed)
+    n = [1000, 70000, 1_000_000, 3][seed]
+    y = rng.integers(-3, 4, size=n).astype(np.float64)
+    _check(y, float(rng.integers(1, 6)), l1, dtype)
+
+
+@pytest.mark.parametrize("l1", [False, True])
+def test_condat_outside_the_double_float_range(l1):
+    rng = np.random.default_rng(5)
+    y = rng.normal(size=200_000)
+    y[::7] *= 1e-70
+    y[3::11] *= 1e70
+    _check(y, 1.0, l1)
+    _check(rng.normal(size=50_000) * 1e-80, 1e-79, l1)
+
+
+@pytest.mark.parametrize("l1", [False, True])
+def test_condat_large_radius_and_scale(l1):
+    rng = np.random.default_rng(6)
+    y = rng.normal(size=300_000) * 1e30
+    _check(y, 3e31, l1)
+    _check(rng.uniform(size=300_000), 50.0, l1)
