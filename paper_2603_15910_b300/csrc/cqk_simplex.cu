@@ -505,6 +505,7 @@ template <typename T, bool L1, bool SUM>
 __device__ void condat_block(const T* __restrict__ y, const T* __restrict__ xb, const Span& sp, bool aligned,
                              double r, int member, int nchunk, T* smem, uint64_t* bars, unsigned& parity, int* err,
                              unsigned long long limit_ns, SumAcc& sacc, double& S_out, long long& nJ_out) {
+    // (without SUM the NaN check of the data rides on this pass, into sacc.bad)
     constexpr int V = VecOf<T>::V;
     constexpr int TT = condat_tile<T>();
     constexpr int KC = TT / V / NT;
@@ -573,6 +574,12 @@ __device__ void condat_block(const T* __restrict__ y, const T* __restrict__ xb, 
                 for (int j = 0; j < V; j++)
                     if (ok[j] && sum_elem<T, L1>(sacc, v[j])) widem |= 1u << j;
                 for (unsigned m = widem; m; m &= m - 1) sum_wide<T, L1>(sacc, pick(v, __ffs(m) - 1));
+            } else {
+#pragma unroll
+                for (int j = 0; j < V; j++) {
+                    if constexpr (sizeof(T) == 8) sacc.bad |= ok[j] && u64_is_nan(bits_of((double)v[j]));
+                    else sacc.bad |= ok[j] && (v[j] != v[j]);
+                }
             }
             support_mask<T, L1>(xb, sp, c * (TT / V) + ql, aligned, ok);
 #pragma unroll
@@ -769,6 +776,35 @@ __device__ __forceinline__ void warp0_grid_sums(const double* part, int G, int p
     for (int q = 0; q < 3; q++) out[q] = warp_sum(v[q]);
 }
 
+// one pass over the group's span accumulating the sum and maximum of y (l1: |y|) and the NaN
+// check (every thread of the group)
+template <typename T, bool L1>
+__device__ __forceinline__ void sum_sweep(const T* __restrict__ y, const Span& sp, const Grp& gp, bool aligned,
+                                          SumAcc& sacc) {
+    constexpr int V = VecOf<T>::V;
+    const int lane = threadIdx.x & 31;
+    const WarpSweep sw(span_qlo<V>(sp), span_qhi<V>(sp), kStreamU, gp.member, gp.g);
+    for (int64_t it = 0; it < sw.count; it++) {
+        const int64_t base = sw.base(it, false);
+        T vv[kStreamU][V];
+        bool okk[kStreamU][V];
+#pragma unroll
+        for (int u = 0; u < kStreamU; u++) load_vec<T>(y, sp, base + u * 32 + lane, aligned, vv[u], okk[u]);
+        unsigned widem = 0;
+#pragma unroll
+        for (int uj = 0; uj < kStreamU * V; uj++) {
+            const int u = uj / V, j = uj % V;
+            if (okk[u][j] && sum_elem<T, L1>(sacc, vv[u][j])) widem |= 1u << uj;
+        }
+        if constexpr (sizeof(T) == 8) {
+            // values outside the df operating range: exact FP64, one trip per element
+            for (unsigned m = widem; m; m &= m - 1) sum_wide<T, L1>(sacc, pick2(vv, __ffs(m) - 1));
+            // fold the lazy pair (at most 64 terms) into FP64: one FP64 add per 4 sweeps
+            if ((it & 3) == 3) sacc.fold();
+        }
+    }
+}
+
 // ---- one projection by one group of blocks ------------------------------------------------
 // A supplies the arrays, r, the options and the info slot; gp the group (member, size, span,
 // header and partial sums).  The instance is the span [gp.sp.lo, gp.sp.hi) of y and x.
@@ -782,7 +818,7 @@ __device__ __forceinline__ void simplex_solve(const SimplexArgs& A, const Grp& g
     __shared__ unsigned sh_u[2 * NWARP];
     // loop state written by thread 0 after each update, read by all threads
     __shared__ double s_lam, s_final;
-    __shared__ int s_done, s_bad;
+    __shared__ int s_done, s_bad, s_redo;
     const T* __restrict__ y = static_cast<const T*>(A.y);
     const Span sp = gp.sp;
     const int64_t n = sp.hi - sp.lo;
@@ -796,37 +832,20 @@ __device__ __forceinline__ void simplex_solve(const SimplexArgs& A, const Grp& g
     // ------------------------------------------------------------------ pass 0: start
     double lam0 = 0.0, abs_sum = 0.0;
     int passes = 0, nchunks = 0, tile = 0;
+    bool condat_start = false;  // lambda_0 from the Alg. 2 union (>= lambda*)
+    int par0 = 1;               // partial-sum slot of the first Newton pass
     {
         double q[4] = {0.0, 0.0, 0.0, -INFINITY};  // sum y (l1: |y|), union sum, union size, max y (l1: |y|)
         const bool warm = A.init == CQK_INIT_WARM;
         const bool condat = A.init == CQK_INIT_CONDAT || warm;
-        // the l1 ball needs sum |y| (inside test) and the formula start sum y and max y; with
-        // the Alg. 2 start the l1 sums ride on the Alg. 2 pass
+        // the formula and given starts need sum y and max y (l1: |y|), which also serve the l1
+        // ball's inside test; after an Alg. 2 start the l1 ball sums |y| only when needed (below)
         const bool sum_pass = !condat;
         bool bad = false;
         SumAcc sacc;
         sacc.init();
         if (sum_pass) {
-            const WarpSweep sw(qlo, qhi, kStreamU, gp.member, gp.g);
-            for (int64_t it = 0; it < sw.count; it++) {
-                const int64_t base = sw.base(it, false);
-                T vv[kStreamU][V];
-                bool okk[kStreamU][V];
-#pragma unroll
-                for (int u = 0; u < kStreamU; u++) load_vec<T>(y, sp, base + u * 32 + lane, aligned, vv[u], okk[u]);
-                unsigned widem = 0;
-#pragma unroll
-                for (int uj = 0; uj < kStreamU * V; uj++) {
-                    const int u = uj / V, j = uj % V;
-                    if (okk[u][j] && sum_elem<T, L1>(sacc, vv[u][j])) widem |= 1u << uj;
-                }
-                if constexpr (sizeof(T) == 8) {
-                    // values outside the df operating range: exact FP64, one trip per element
-                    for (unsigned m = widem; m; m &= m - 1) sum_wide<T, L1>(sacc, pick2(vv, __ffs(m) - 1));
-                    // fold the lazy pair (at most 64 terms) into FP64: one FP64 add per 4 sweeps
-                    if ((it & 3) == 3) sacc.fold();
-                }
-            }
+            sum_sweep<T, L1>(y, sp, gp, aligned, sacc);
             passes++;
         }
         // chunks of at least condat_chunk elements (the J updates are scalar FP64 work, which
@@ -836,8 +855,8 @@ __device__ __forceinline__ void simplex_solve(const SimplexArgs& A, const Grp& g
         if (condat) {
             double Sw = 0.0;
             long long nJw = 0;
-            condat_block<T, L1, L1>(y, warm ? static_cast<const T*>(A.xbar) : nullptr, sp, aligned, r, gp.member,
-                                    nchunk, smem, bars, ring_parity, &gp.hdr->error, A.limit_ns, sacc, Sw, nJw);
+            condat_block<T, L1, false>(y, warm ? static_cast<const T*>(A.xbar) : nullptr, sp, aligned, r, gp.member,
+                                       nchunk, smem, bars, ring_parity, &gp.hdr->error, A.limit_ns, sacc, Sw, nJw);
             q[1] = threadIdx.x == 0 ? Sw : 0.0;
             q[2] = threadIdx.x == 0 ? (double)nJw : 0.0;
             passes++;
@@ -878,6 +897,7 @@ __device__ __forceinline__ void simplex_solve(const SimplexArgs& A, const Grp& g
         abs_sum = red[0];
         if (condat && red[2] > 0.0) {
             lam0 = (r - red[1]) / red[2];  // eq. (lambdaJ) on the union of the chunks' J
+            condat_start = true;
             nchunks = (int)nchunk;
             tile = condat_tile<T>();
         } else if (condat) {
@@ -890,6 +910,33 @@ __device__ __forceinline__ void simplex_solve(const SimplexArgs& A, const Grp& g
             lam0 = fmax(A.lambda0, -red[3]);  // Alg. 4, line 1
         } else {
             lam0 = fmax((r - red[0]) / (double)n, -red[3]);  // eq. (CQKlambda0) with b = d = 1; Alg. 4 line 1
+        }
+        // The l1 ball's inside test needs sum |y|, except when the Alg. 2 start already proves
+        // sum |y| > r: lambda_0 >= lambda* (eq. (lambdaJ)), and lambda* >= 0 whenever sum |y| <= r
+        // (then phi(0) = sum |y| <= r).  lambda_0 = (r - S)/C < 0 is taken as proven only when
+        // r - S is negative beyond the rounding of S.
+        if (L1 && condat) {
+            const bool outside = condat_start && (r - red[1]) < -1e-13 * (fabs(r) + fabs(red[1]));
+            if (outside) {
+                abs_sum = INFINITY;
+            } else {
+                SumAcc s2;
+                s2.init();
+                sum_sweep<T, L1>(y, sp, gp, aligned, s2);
+                passes++;
+                double pv[1] = {s2.sum()};
+                block_sum<1>(pv, sh);
+                write_partials<1>(gp.part, gp.member, G, 1, pv);
+                if (!group_barrier(gp, bar_target, A.limit_ns, A.fault_inject != 0)) {
+                    if (threadIdx.x == 0) A.info->status = CQK_TIMEOUT;
+                    return;
+                }
+                bar_target += (unsigned)G;
+                double red1[1];
+                grid_reduce<1>(gp.part, G, 1, -1, red1, sh, bc);
+                abs_sum = red1[0];
+                par0 = 0;  // slot 1 holds this reduction: the Newton loop starts on slot 0
+            }
         }
     }
     bool bad_input = A.validate && (__ldcg(&gp.hdr->flags) & kFlagBadInput);
@@ -907,7 +954,10 @@ __device__ __forceinline__ void simplex_solve(const SimplexArgs& A, const Grp& g
         stop = CQK_STOP_INSIDE;
         lam = final_lam = 0.0;
     } else {
-        int par = 1;
+        int par = par0;
+        // ties (phi'_+) are needed only when the first step goes right; from the Alg. 2 start
+        // (lambda_0 >= lambda*) it goes left, and the pass is redone with ties if it does not
+        bool ties = !condat_start;
         for (k = 0;; k++) {
             if (k >= A.max_iter) {
                 status = CQK_MAXITER;
@@ -919,7 +969,7 @@ __device__ __forceinline__ void simplex_solve(const SimplexArgs& A, const Grp& g
             pa.cm = pa.ct = 0u;
             pa.nan = false;
             const bool rev = (k & 1) == 0;
-            const bool first = (k == 0);
+            const bool first = (k == 0) && ties;
             if constexpr (sizeof(T) == 8) {
                 const GtThreshold g = make_gt(-lam);
                 const df Lm = df_make(0.0f);
@@ -950,11 +1000,13 @@ __device__ __forceinline__ void simplex_solve(const SimplexArgs& A, const Grp& g
                 double red[3];
                 warp0_grid_sums(gp.part, G, par, red);
                 if (threadIdx.x == 0) {
-                    int done = 0, bad = 0;
+                    int done = 0, bad = 0, redo = 0;
                     double next = lam;
                     if (A.validate && first && (__ldcg(&gp.hdr->flags) & kFlagBadInput)) {
                         bad = 1;
                         done = 1;
+                    } else if (k == 0 && !first && red[0] - r < 0.0) {
+                        redo = 1;  // phi(lambda_0) < r: the step needs phi'_+, count the ties
                     } else {
                         const double phi = red[0], dminus = red[1], dplus = red[2];
                         const double gk = phi - r;
@@ -1002,10 +1054,17 @@ __device__ __forceinline__ void simplex_solve(const SimplexArgs& A, const Grp& g
                     s_lam = next;
                     s_done = done;
                     s_bad = bad;
+                    s_redo = redo;
                 }
             }
             __syncthreads();
             par ^= 1;
+            if (s_redo) {
+                ties = true;
+                k--;
+                __syncthreads();
+                continue;
+            }
             if (s_bad) {
                 bad_input = true;
                 status = CQK_BAD_INPUT;
