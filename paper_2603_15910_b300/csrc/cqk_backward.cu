@@ -83,6 +83,61 @@ __device__ __forceinline__ void store_or(void* p, const Span& sp, int64_t q, boo
     if (p) store_vec<T>(static_cast<T*>(p), sp, q, aligned, v);
 }
 
+// ---- per-element arithmetic -----------------------------------------------------------------
+// Double-float (FP32 pipe, ~2^-44 relative) for FP64 data in the df operating range and for
+// FP32 data; FP64 values outside the range take an exact FP64 path per element (out of line,
+// so that it costs nothing when unused).  FP64 results are formed from the double-float ones on
+// the integer pipe (df_to_f64_bits): the kernel issues no FP64 instruction per element.
+
+template <typename T>
+__device__ __forceinline__ df to_df(T v) {
+    if constexpr (sizeof(T) == 8) return split_f64_finite((double)v);
+    else return df_make((float)v);
+}
+template <typename T>
+__device__ __forceinline__ T from_df(df v) {
+    if constexpr (sizeof(T) == 8) return df_to_f64_bits(v);
+    else return __fadd_rn(v.hi, v.lo);
+}
+// 1/d as a float pair (d > 0)
+__device__ __forceinline__ df inv_df(df D) {
+    const float r0 = rcp_approx(D.hi);
+    const float res = fmaf(-D.lo, r0, fmaf(-D.hi, r0, 1.0f));
+    return fast_two_sum(r0, __fmul_rn(r0, res));
+}
+template <typename T>
+__device__ __forceinline__ bool in_df_range(T v) {
+    if constexpr (sizeof(T) == 8) return df_in_range((double)v, false);
+    else return true;
+}
+
+// exact FP64 fallbacks (values outside the df range)
+__device__ __noinline__ void bwd_sum_exact(double g, double x, double b, double d, int kind, double& S, double& Q) {
+    if (kind == kBwdGeneral) {
+        const double w = b / d;
+        S += w * g;
+        Q += w * b;
+    } else {
+        S += (kind == kBwdL1 && x < 0.0) ? -g : g;
+        Q += 1.0;
+    }
+}
+__device__ __noinline__ void bwd_map_exact(double g, double x, double b, double d, bool fr, bool lower, double mu,
+                                           double lam, int kind, double* out) {
+    // out: ga (or gy), gb, gd, gl, gu
+    if (kind == kBwdGeneral) {
+        const double res = g - mu * b;
+        const double daj = fr ? res / d : 0.0;
+        out[0] = daj;
+        out[1] = lam * daj - mu * x;
+        out[2] = -x * daj;
+        out[3] = !fr && lower ? res : 0.0;
+        out[4] = !fr && !lower ? res : 0.0;
+    } else {
+        out[0] = fr ? g - ((kind == kBwdL1 && x < 0.0) ? -mu : mu) : 0.0;
+    }
+}
+
 // one instance by one group
 template <typename T, int KIND>
 __device__ __forceinline__ void bwd_instance(const BwdArgs& A, const Grp& gp, int64_t inst) {
@@ -100,9 +155,16 @@ __device__ __forceinline__ void bwd_instance(const BwdArgs& A, const Grp& gp, in
     const WarpSweep sw(span_qlo<V>(sp), span_qhi<V>(sp), U, gp.member, gp.g);
 
     // ---- pass 1: sum_F b g/d and Q = sum_F b^2/d (simplex / l1: sum_F (s) g and |F|)
-    double S = 0.0, Q = 0.0;
+    LazyDf Sl{0.0f, 0.0f}, Ql{0.0f, 0.0f};
+    double S64 = 0.0, Q64 = 0.0;
+    long long nF = 0;
     if (!inside) {
         for (int64_t it = 0; it < sw.count; it++) {
+            if ((it & 7) == 7) {
+                S64 += lazy_value(Sl);
+                Q64 += lazy_value(Ql);
+                Sl = Ql = LazyDf{0.0f, 0.0f};
+            }
             const int64_t base = sw.base(it, false);
             T vg[U][V], vx[U][V], vb[U][V], vd[U][V], vl[U][V], vu[U][V];
             bool ok[U][V];
@@ -124,26 +186,40 @@ __device__ __forceinline__ void bwd_instance(const BwdArgs& A, const Grp& gp, in
             for (int w = 0; w < U; w++) {
                 const int64_t q = base + w * 32 + lane;
                 const unsigned fb = free_bits<T, KIND>(A, sp, q, vx[w], vl[w], vu[w]);
+                unsigned widem = 0;
 #pragma unroll
                 for (int j = 0; j < V; j++) {
                     if (!ok[w][j] || !((fb >> j) & 1u)) continue;
-                    const double gj = (double)vg[w][j];
-                    if (KIND == kBwdGeneral) {
-                        const double wj = (double)vb[w][j] / (double)vd[w][j];
-                        S += wj * gj;
-                        Q += wj * (double)vb[w][j];
-                    } else if (KIND == kBwdSimplex) {
-                        S += gj;
-                        Q += 1.0;
-                    } else {
-                        S += vx[w][j] > T(0) ? gj : -gj;
-                        Q += 1.0;
+                    bool inr = in_df_range<T>(vg[w][j]);
+                    if (KIND == kBwdGeneral) inr = inr && in_df_range<T>(vb[w][j]) && in_df_range<T>(vd[w][j]);
+                    if (!inr) {
+                        widem |= 1u << j;
+                        continue;
                     }
+                    const df G = to_df<T>(vg[w][j]);
+                    if (KIND == kBwdGeneral) {
+                        const df B = to_df<T>(vb[w][j]);
+                        const df W = df_mul(B, inv_df(to_df<T>(vd[w][j])));
+                        lazy_add(Sl, df_mul_lazy(W, G));
+                        lazy_add(Ql, df_mul_lazy(W, B));
+                    } else if (KIND == kBwdSimplex) {
+                        lazy_add(Sl, G);
+                        nF++;
+                    } else {
+                        lazy_add(Sl, vx[w][j] > T(0) ? G : df_neg(G));
+                        nF++;
+                    }
+                }
+                for (unsigned m = widem; m; m &= m - 1) {
+                    const int j = __ffs(m) - 1;
+                    bwd_sum_exact((double)pick(vg[w], j), (double)pick(vx[w], j),
+                                  KIND == kBwdGeneral ? (double)pick(vb[w], j) : 1.0,
+                                  KIND == kBwdGeneral ? (double)pick(vd[w], j) : 1.0, KIND, S64, Q64);
                 }
             }
         }
     }
-    double pv[2] = {S, Q};
+    double pv[2] = {lazy_value(Sl) + S64, KIND == kBwdGeneral ? lazy_value(Ql) + Q64 : (double)nF + Q64};
     block_sum<2>(pv, sh);
     write_partials<2>(gp.part, gp.member, gp.g, 0, pv);
     const unsigned target = (unsigned)gp.g + (A.fault_inject ? 1u : 0u);
@@ -155,6 +231,8 @@ __device__ __forceinline__ void bwd_instance(const BwdArgs& A, const Grp& gp, in
     grid_reduce<2>(gp.part, gp.g, 0, -1, red, sh, bc);
     const bool nondiff = !inside && !(red[1] > 0.0);
     const double mu = (inside || nondiff) ? 0.0 : red[0] / red[1];
+    const df M = df_from_f64(mu), Lm = df_from_f64(lam);
+    const bool par_ok = fabs(mu) <= 1.152921504606847e18 && fabs(lam) <= 1.152921504606847e18;  // 2^60
 
     // ---- pass 2: the gradients
     for (int64_t it = 0; it < sw.count; it++) {
@@ -180,32 +258,74 @@ __device__ __forceinline__ void bwd_instance(const BwdArgs& A, const Grp& gp, in
             const int64_t q = base + w * 32 + lane;
             const unsigned fb = inside ? ((1u << V) - 1u) : free_bits<T, KIND>(A, sp, q, vx[w], vl[w], vu[w]);
             T oa[V], ob[V], od[V], ol[V], ou[V];
+            unsigned widem = 0;
 #pragma unroll
             for (int j = 0; j < V; j++) {
                 const bool fr = (fb >> j) & 1u;
-                const double gj = (double)vg[w][j], xj = (double)vx[w][j];
+                oa[j] = ob[j] = od[j] = ol[j] = ou[j] = T(0);
+                if (!ok[w][j]) continue;
+                if (KIND == kBwdL1 && inside) {
+                    oa[j] = vg[w][j];
+                    continue;
+                }
+                bool inr = par_ok && in_df_range<T>(vg[w][j]) && in_df_range<T>(vx[w][j]);
+                if (KIND == kBwdGeneral) inr = inr && in_df_range<T>(vb[w][j]) && in_df_range<T>(vd[w][j]);
+                if (!inr) {
+                    widem |= 1u << j;
+                    continue;
+                }
+                const df G = to_df<T>(vg[w][j]);
                 if (KIND == kBwdGeneral) {
-                    const double bj = (double)vb[w][j], dj = (double)vd[w][j];
-                    const double res = gj - mu * bj;
-                    const double daj = fr ? res / dj : 0.0;
-                    oa[j] = (T)daj;
-                    od[j] = (T)(-xj * daj);
-                    ob[j] = (T)(lam * daj - mu * xj);
-                    bool lower = false;
-                    if (!fr && need_lu && ok[w][j]) {
-                        lower = vx[w][j] == vl[w][j];
-                        if (lower && vl[w][j] == vu[w][j] && A.a) {
-                            // a fixed variable (l = u) is at its lower bound when (a + lambda b)/d <= l
-                            const double aj = (double)static_cast<const T*>(A.a)[q * V + j];
-                            lower = (aj + lam * bj) / dj <= (double)vl[w][j];
+                    const df B = to_df<T>(vb[w][j]), X = to_df<T>(vx[w][j]);
+                    const df res = df_add(G, df_neg(df_mul(M, B)));
+                    const df mx = df_mul(M, X);
+                    if (fr) {
+                        const df ga = df_mul(res, inv_df(to_df<T>(vd[w][j])));
+                        oa[j] = from_df<T>(ga);
+                        od[j] = from_df<T>(df_neg(df_mul(X, ga)));
+                        ob[j] = from_df<T>(df_add(df_mul(Lm, ga), df_neg(mx)));
+                    } else {
+                        ob[j] = from_df<T>(df_neg(mx));
+                        bool lower = false;
+                        if (need_lu) {
+                            lower = vx[w][j] == vl[w][j];
+                            if (lower && vl[w][j] == vu[w][j] && A.a) {
+                                // a fixed variable (l = u) is at its lower bound when (a + lambda b)/d <= l
+                                const double aj = (double)static_cast<const T*>(A.a)[q * V + j];
+                                lower = (aj + lam * (double)vb[w][j]) / (double)vd[w][j] <= (double)vl[w][j];
+                            }
                         }
+                        const T rv = from_df<T>(res);
+                        ol[j] = lower ? rv : T(0);
+                        ou[j] = lower ? T(0) : rv;
                     }
-                    ol[j] = (T)(!fr && lower ? res : 0.0);
-                    ou[j] = (T)(!fr && !lower ? res : 0.0);
-                } else if (KIND == kBwdSimplex) {
-                    oa[j] = (T)(fr ? gj - mu : 0.0);
-                } else {
-                    oa[j] = (T)(inside ? gj : (fr ? gj - (vx[w][j] > T(0) ? mu : -mu) : 0.0));
+                } else if (fr) {
+                    const bool neg = KIND == kBwdL1 && vx[w][j] < T(0);
+                    oa[j] = from_df<T>(df_add(G, neg ? M : df_neg(M)));
+                }
+            }
+            for (unsigned m = widem; m; m &= m - 1) {
+                const int j = __ffs(m) - 1;
+                const bool fr = (fb >> j) & 1u;
+                const T xj = pick(vx[w], j);
+                bool lower = false;
+                if (KIND == kBwdGeneral && !fr && need_lu) {
+                    const T lj = pick(vl[w], j), uj = pick(vu[w], j);
+                    lower = xj == lj;
+                    if (lower && lj == uj && A.a) {
+                        const double aj = (double)static_cast<const T*>(A.a)[q * V + j];
+                        lower = (aj + lam * (double)pick(vb[w], j)) / (double)pick(vd[w], j) <= (double)lj;
+                    }
+                }
+                double o5[5];
+                bwd_map_exact((double)pick(vg[w], j), (double)xj, KIND == kBwdGeneral ? (double)pick(vb[w], j) : 1.0,
+                              KIND == kBwdGeneral ? (double)pick(vd[w], j) : 1.0, fr, lower, mu, lam, KIND, o5);
+                put(oa, j, (T)o5[0]);
+                if (KIND == kBwdGeneral) {
+                    put(ob, j, (T)o5[1]);
+                    put(od, j, (T)o5[2]);
+                    put(ol, j, (T)o5[3]);
+                    put(ou, j, (T)o5[4]);
                 }
             }
             store_or<T>(A.ga, sp, q, aligned, oa);

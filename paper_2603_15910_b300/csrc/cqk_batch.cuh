@@ -21,6 +21,7 @@ constexpr size_t kInstPartBytes = 2ull * kPartialQ * kMaxGroup * sizeof(double);
 //   [0, 256)                 BatchHeader
 //   inst headers             B x WsHeader (zeroed with the batch header before each launch)
 //   plan                     order[B] (int32), gsize[B] (int32), prefix[B+1] (int64)
+//   slot table               B x kMaxGroup int32: the plan position of every slot
 //   partials                 B x kInstPartBytes
 struct BatchHeader {
     unsigned long long cursor;  // next slot to hand out
@@ -30,7 +31,7 @@ struct BatchHeader {
 static_assert(sizeof(BatchHeader) == 256, "batch header must be 256 bytes");
 
 struct BatchLayout {
-    size_t hdr, inst_hdr, order, gsize, prefix, part, total;
+    size_t hdr, inst_hdr, order, gsize, prefix, slots, part, total;
 };
 __host__ __device__ inline size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 __host__ __device__ inline BatchLayout batch_layout(int64_t B) {
@@ -40,7 +41,8 @@ __host__ __device__ inline BatchLayout batch_layout(int64_t B) {
     L.order = align256(L.inst_hdr + (size_t)B * sizeof(WsHeader));
     L.gsize = align256(L.order + (size_t)B * 4);
     L.prefix = align256(L.gsize + (size_t)B * 4);
-    L.part = align256(L.prefix + (size_t)(B + 1) * 8);
+    L.slots = align256(L.prefix + (size_t)(B + 1) * 8);
+    L.part = align256(L.slots + (size_t)B * kMaxGroup * 4);
     L.total = align256(L.part + (size_t)B * kInstPartBytes);
     return L;
 }
@@ -51,6 +53,7 @@ struct BatchRefs {
     int* order;
     int* gsize;
     long long* prefix;
+    int* slots;
     double* part;
     __host__ __device__ static BatchRefs at(void* ws, int64_t B) {
         const BatchLayout L = batch_layout(B);
@@ -61,6 +64,7 @@ struct BatchRefs {
         R.order = reinterpret_cast<int*>(p + L.order);
         R.gsize = reinterpret_cast<int*>(p + L.gsize);
         R.prefix = reinterpret_cast<long long*>(p + L.prefix);
+        R.slots = reinterpret_cast<int*>(p + L.slots);
         R.part = reinterpret_cast<double*>(p + L.part);
         return R;
     }
@@ -79,16 +83,10 @@ __device__ __forceinline__ Slot next_slot(const BatchRefs& R, int64_t B) {
         const unsigned long long total = *(volatile unsigned long long*)&R.bh->total;
         Slot sl{-1, 0, 0};
         if (slot < total) {
-            // the last k with prefix[k] <= slot (instances in plan order)
-            int64_t lo = 0, hi = B;  // prefix[lo] <= slot < prefix[hi]
-            while (hi - lo > 1) {
-                const int64_t mid = (lo + hi) / 2;
-                if ((unsigned long long)R.prefix[mid] <= slot) lo = mid;
-                else hi = mid;
-            }
-            sl.inst = R.order[lo];
-            sl.member = (int)(slot - (unsigned long long)R.prefix[lo]);
-            sl.g = R.gsize[lo];
+            const int p = R.slots[slot];  // plan position of the slot's instance
+            sl.inst = R.order[p];
+            sl.member = (int)(slot - (unsigned long long)R.prefix[p]);
+            sl.g = R.gsize[p];
         }
         s_slot = sl;
     }

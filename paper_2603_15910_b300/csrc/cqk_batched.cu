@@ -72,7 +72,11 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(const int64_t* __res
         __syncthreads();
         long long before = 0;
         for (int w = 0; w < (tid >> 5); w++) before += warp_tot[w];
-        if (p < B) R.prefix[p] = s_base + before + incl - g;
+        if (p < B) {
+            const long long first = s_base + before + incl - g;
+            R.prefix[p] = first;
+            for (long long m = 0; m < g; m++) R.slots[first + m] = (int)p;
+        }
         __syncthreads();
         if (tid == kPlanThreads - 1) {
             long long all = 0;
