@@ -739,9 +739,10 @@ __device__ __forceinline__ void newton_sweep(const T* __restrict__ y, const Span
     }
 }
 
-// per-block totals of a pass (fixed order) -> partials slot `par`
+// per-block totals of a pass (fixed order) -> partials slot `par`, and into blk (thread 0);
+// a one-block group (solo) keeps them in registers only
 __device__ __forceinline__ void write_pass_partials(const Grp& gp, int par, double acc, unsigned cm, unsigned ct,
-                                                    double* sh_d, unsigned* sh_u) {
+                                                    double* sh_d, unsigned* sh_u, bool solo, double (&blk)[3]) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     acc = warp_sum(acc);
     cm = __reduce_add_sync(0xffffffffu, cm);
@@ -761,7 +762,10 @@ __device__ __forceinline__ void write_pass_partials(const Grp& gp, int par, doub
             c1 += sh_u[NWARP + w];
         }
         const double pv[3] = {t, (double)c0, (double)(c0 + c1)};
-        write_partials<3>(gp.part, gp.member, gp.g, par, pv);
+        if (!solo) write_partials<3>(gp.part, gp.member, gp.g, par, pv);
+        blk[0] = pv[0];
+        blk[1] = pv[1];
+        blk[2] = pv[2];
     }
 }
 
@@ -990,15 +994,21 @@ __device__ __forceinline__ void simplex_solve(const SimplexArgs& A, const Grp& g
             passes++;
             if (A.validate && first && __any_sync(0xffffffffu, pa.nan) && lane == 0)
                 atomicOr(&gp.hdr->flags, kFlagBadInput);
-            write_pass_partials(gp, par, pa.acc64, pa.cm, pa.ct, sh_d, sh_u);
-            if (!group_barrier(gp, bar_target, A.limit_ns, A.fault_inject != 0)) {
-                if (threadIdx.x == 0) A.info->status = CQK_TIMEOUT;
-                return;
+            // a one-block group needs neither the partials in memory nor a barrier: thread 0
+            // already holds the totals (bit-identical to the one-partial grid sum)
+            const bool solo = G == 1 && !A.fault_inject;
+            double blk[3];
+            write_pass_partials(gp, par, pa.acc64, pa.cm, pa.ct, sh_d, sh_u, solo, blk);
+            if (!solo) {
+                if (!group_barrier(gp, bar_target, A.limit_ns, A.fault_inject != 0)) {
+                    if (threadIdx.x == 0) A.info->status = CQK_TIMEOUT;
+                    return;
+                }
+                bar_target += (unsigned)G;
             }
-            bar_target += (unsigned)G;
             if (threadIdx.x < 32) {
-                double red[3];
-                warp0_grid_sums(gp.part, G, par, red);
+                double red[3] = {blk[0], blk[1], blk[2]};
+                if (!solo) warp0_grid_sums(gp.part, G, par, red);
                 if (threadIdx.x == 0) {
                     int done = 0, bad = 0, redo = 0;
                     double next = lam;
