@@ -110,7 +110,10 @@ typedef struct cqk_options {
     int32_t condat_chunk;   /* CQK_INIT_CONDAT: the partition has min(warps, ceil(n /            */
                             /* condat_chunk)) chunks; 0 (default): 512                          */
     const void* xbar;       /* CQK_INIT_WARM: the primal estimate (device; NULL otherwise)       */
-    int32_t reserved[4];
+    int32_t warp_elems;     /* batched projections: instances shorter than warp_elems (rounded  */
+                            /* down to a power of two) are solved by one warp each; 0 (default): */
+                            /* 4096; negative: never                                            */
+    int32_t reserved[3];
 } cqk_options;
 
 /* Written on the device by every solve. */

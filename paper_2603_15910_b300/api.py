@@ -58,7 +58,8 @@ class _Options(ctypes.Structure):
         ("group_elems", ctypes.c_int32),
         ("condat_chunk", ctypes.c_int32),
         ("xbar", ctypes.c_void_p),
-        ("reserved", ctypes.c_int32 * 4),
+        ("warp_elems", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 3),
     ]
 
 
@@ -185,7 +186,8 @@ def stream_handle(stream=None):
 
 
 def make_options(init=None, max_iter=100, lambda0=0.0, validate=True, final_step=None, spin_limit_us=2_000_000,
-                 max_blocks=0, fault_inject=False, group_elems=0, condat_chunk=0, xbar=None) -> _Options:
+                 max_blocks=0, fault_inject=False, group_elems=0, condat_chunk=0, xbar=None,
+                 warp_elems=0) -> _Options:
     o = _Options()
     library().cqk_default_options(ctypes.byref(o))
     o.max_iter = int(max_iter)
@@ -200,6 +202,7 @@ def make_options(init=None, max_iter=100, lambda0=0.0, validate=True, final_step
     o.group_elems = int(group_elems)
     o.condat_chunk = int(condat_chunk)
     o.xbar = xbar.data_ptr() if xbar is not None else None
+    o.warp_elems = int(warp_elems)
     return o
 
 

@@ -26,7 +26,9 @@ constexpr size_t kInstPartBytes = 2ull * kPartialQ * kMaxGroup * sizeof(double);
 struct BatchHeader {
     unsigned long long cursor;  // next slot to hand out
     unsigned long long total;   // number of slots (written by the planner)
-    unsigned pad[60];
+    unsigned long long large;   // slots of block groups; the slots after them are warp packs
+    long long nlarge;           // instances solved by block groups (plan positions [0, nlarge))
+    unsigned pad[56];
 };
 static_assert(sizeof(BatchHeader) == 256, "batch header must be 256 bytes");
 
@@ -70,9 +72,12 @@ struct BatchRefs {
     }
 };
 
-// One slot of the queue: the instance, this block's member index and the group size.
+// One slot of the queue: the instance, this block's member index and the group size; or a
+// pack of up to kWarpPack small instances, one per warp (plan positions pack_first + warp).
+constexpr int kWarpPack = NWARP;
 struct Slot {
     int inst, member, g;
+    long long pack_first;  // -1 unless the slot is a warp pack
 };
 
 // Called by all threads of a block: the next slot, or inst = -1 when the queue is empty.
@@ -81,12 +86,15 @@ __device__ __forceinline__ Slot next_slot(const BatchRefs& R, int64_t B) {
     if (threadIdx.x == 0) {
         const unsigned long long slot = atomicAdd(&R.bh->cursor, 1ull);
         const unsigned long long total = *(volatile unsigned long long*)&R.bh->total;
-        Slot sl{-1, 0, 0};
-        if (slot < total) {
+        const unsigned long long large = *(volatile unsigned long long*)&R.bh->large;
+        Slot sl{-1, 0, 0, -1};
+        if (slot < large) {
             const int p = R.slots[slot];  // plan position of the slot's instance
             sl.inst = R.order[p];
             sl.member = (int)(slot - (unsigned long long)R.prefix[p]);
             sl.g = R.gsize[p];
+        } else if (slot < total) {
+            sl.pack_first = *(volatile long long*)&R.bh->nlarge + (long long)(slot - large) * kWarpPack;
         }
         s_slot = sl;
     }

@@ -22,11 +22,14 @@ __device__ __forceinline__ long long warp_incl_scan(long long v, long long& tota
 // One block.  Buckets instances by floor(log2(length)) (longest first; the order inside a
 // bucket only affects scheduling, never a result), gives each a group of
 // clamp(ceil(length / per_block), 1, gmax) blocks, and writes the slot prefix sums.
+// Instances shorter than 2^small_log2 (small_log2 > 0) are not given block groups: they form
+// a suffix of the plan order and are handed out in packs of kWarpPack, one per warp.
 __global__ void __launch_bounds__(kPlanThreads) plan_kernel(const int64_t* __restrict__ offsets, int64_t B,
-                                                            int64_t per_block, int gmax, BatchRefs R) {
+                                                            int64_t per_block, int gmax, int small_log2,
+                                                            BatchRefs R) {
     __shared__ unsigned hist[64], start[64], fill[64];
     __shared__ long long warp_tot[kPlanThreads / 32];
-    __shared__ long long s_base;
+    __shared__ long long s_base, s_nlarge;
     const int tid = threadIdx.x;
     if (tid < 64) {
         hist[tid] = 0;
@@ -41,10 +44,13 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(const int64_t* __res
     __syncthreads();
     if (tid == 0) {
         unsigned acc = 0;
+        long long nl = 0;
         for (int b = 63; b >= 0; b--) {
             start[b] = acc;
             acc += hist[b];
+            if (small_log2 <= 0 || b >= small_log2) nl += hist[b];
         }
+        s_nlarge = nl;
     }
     __syncthreads();
     for (int64_t i = tid; i < B; i += kPlanThreads) {
@@ -55,10 +61,11 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(const int64_t* __res
     __syncthreads();
     if (tid == 0) s_base = 0;
     __syncthreads();
-    for (int64_t c = 0; c < B; c += kPlanThreads) {
+    const long long NL = s_nlarge;
+    for (int64_t c = 0; c < NL; c += kPlanThreads) {
         const int64_t p = c + tid;
         long long g = 0;
-        if (p < B) {
+        if (p < NL) {
             const int i = R.order[p];
             const long long len = offsets[i + 1] - offsets[i];
             g = (len + per_block - 1) / per_block;
@@ -72,7 +79,7 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(const int64_t* __res
         __syncthreads();
         long long before = 0;
         for (int w = 0; w < (tid >> 5); w++) before += warp_tot[w];
-        if (p < B) {
+        if (p < NL) {
             const long long first = s_base + before + incl - g;
             R.prefix[p] = first;
             for (long long m = 0; m < g; m++) R.slots[first + m] = (int)p;
@@ -86,8 +93,10 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(const int64_t* __res
         __syncthreads();
     }
     if (tid == 0) {
-        R.prefix[B] = s_base;
-        R.bh->total = (unsigned long long)s_base;
+        R.prefix[NL] = s_base;
+        R.bh->large = (unsigned long long)s_base;
+        R.bh->nlarge = NL;
+        R.bh->total = (unsigned long long)s_base + (unsigned long long)((B - NL + kWarpPack - 1) / kWarpPack);
         R.bh->cursor = 0ull;
     }
 }
@@ -96,7 +105,8 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(const int64_t* __res
 
 size_t batch_ws_bytes(int64_t B) { return batch_layout(B).total; }
 
-int plan_batch(const int64_t* offsets_dev, int64_t B, int64_t per_block, int gmax, void* ws, cudaStream_t s) {
+int plan_batch(const int64_t* offsets_dev, int64_t B, int64_t per_block, int gmax, void* ws, cudaStream_t s,
+               int small_log2) {
     const BatchLayout L = batch_layout(B);
     cudaError_t e = cudaMemsetAsync(ws, 0, L.order, s);  // batch header + per-instance headers
     if (e != cudaSuccess) {
@@ -105,7 +115,7 @@ int plan_batch(const int64_t* offsets_dev, int64_t B, int64_t per_block, int gma
     }
     if (gmax > kMaxGroup) gmax = kMaxGroup;
     if (gmax < 1) gmax = 1;
-    plan_kernel<<<1, kPlanThreads, 0, s>>>(offsets_dev, B, per_block, gmax, BatchRefs::at(ws, B));
+    plan_kernel<<<1, kPlanThreads, 0, s>>>(offsets_dev, B, per_block, gmax, small_log2, BatchRefs::at(ws, B));
     e = cudaGetLastError();
     if (e != cudaSuccess) {
         set_last_cuda_error(e);

@@ -156,6 +156,14 @@ struct WarpSweep {
         step = (int64_t)g * NWARP * 32 * U;
         count = first < qhi ? (qhi - first + step - 1) / step : 0;
     }
+    // one warp alone (a warp-level solve): warp index w of W warps
+    __device__ __forceinline__ static WarpSweep solo(int64_t qlo, int64_t qhi, int U) {
+        WarpSweep s(qlo, qhi, U, 0, 0);
+        s.first = (qlo / 32) * 32;
+        s.step = (int64_t)32 * U;
+        s.count = s.first < qhi ? (qhi - s.first + s.step - 1) / s.step : 0;
+        return s;
+    }
     __device__ __forceinline__ int64_t base(int64_t i, bool rev) const { return first + (rev ? count - 1 - i : i) * step; }
 };
 

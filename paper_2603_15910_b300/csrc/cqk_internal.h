@@ -43,6 +43,7 @@ struct Opts {
     int64_t group_elems;   // batched calls: one block of an instance's group per this many elements
     int64_t condat_chunk;  // CQK_INIT_CONDAT: minimum elements per chunk
     const void* xbar;      // CQK_INIT_WARM: primal estimate
+    int warp_log2;         // batched projections: instances shorter than 2^warp_log2 take one warp (0: none)
 };
 
 Opts resolve_options(const cqk_options* opt, int dtype, int default_init);
@@ -62,7 +63,8 @@ constexpr int64_t kGeneralGroupElems = 1 << 16;
 constexpr int64_t kCondatChunkElems = 512;
 constexpr int64_t kBackwardGroupElems = 1 << 18;
 size_t batch_ws_bytes(int64_t B);
-int plan_batch(const int64_t* offsets_dev, int64_t B, int64_t per_block, int gmax, void* ws, cudaStream_t s);
+int plan_batch(const int64_t* offsets_dev, int64_t B, int64_t per_block, int gmax, void* ws, cudaStream_t s,
+               int small_log2 = 0);
 int launch_simplex_batched(int64_t B, const int64_t* offsets, int dtype, const void* y, const double* r, int l1,
                            void* x, uint32_t* mask, cqk_info* info, const Opts& o, void* ws, cudaStream_t s);
 int launch_general_batched(int64_t B, const int64_t* offsets, int dtype, const void* a, const void* b,

@@ -667,14 +667,13 @@ struct PassAcc {
 };
 
 template <typename T, bool L1, bool NEG, bool FIRST>
-__device__ __forceinline__ void newton_sweep(const T* __restrict__ y, const Span& sp, const Grp& gp, bool aligned,
-                                             bool rev, unsigned long long tb, float rd, float ru, double lam, df Lm,
-                                             PassAcc& pa) {
+__device__ __forceinline__ void newton_sweep(const T* __restrict__ y, const Span& sp, const WarpSweep& sw,
+                                             bool aligned, bool rev, unsigned long long tb, float rd, float ru,
+                                             double lam, df Lm, PassAcc& pa) {
     constexpr int V = VecOf<T>::V;
     constexpr int U = kStreamU;
     using VT = typename VecOf<T>::type;
     const int lane = threadIdx.x & 31;
-    const WarpSweep sw(span_qlo<V>(sp), span_qhi<V>(sp), U, gp.member, gp.g);
     for (int64_t it = 0; it < sw.count; it++) {
         const int64_t base = sw.base(it, rev);
         const bool full = aligned && base * V >= sp.lo && (base + 32 * U) * V <= sp.hi;  // warp-uniform
@@ -739,6 +738,88 @@ __device__ __forceinline__ void newton_sweep(const T* __restrict__ y, const Span
     }
 }
 
+// one Newton pass at lambda: picks the comparison form (FP64: sign of the threshold; FP32:
+// directed roundings) and whether ties / NaN are counted (first)
+template <typename T, bool L1>
+__device__ __forceinline__ void newton_pass(const T* __restrict__ y, const Span& sp, const WarpSweep& sw, bool aligned,
+                                            bool rev, bool first, double lam, PassAcc& pa) {
+    pa.acc64 = 0.0;
+    pa.acc32 = df_make(0.0f);
+    pa.cm = pa.ct = 0u;
+    pa.nan = false;
+    if constexpr (sizeof(T) == 8) {
+        const GtThreshold g = make_gt(-lam);
+        const df Lm = df_make(0.0f);
+        if (g.neg) {
+            if (first) newton_sweep<T, L1, true, true>(y, sp, sw, aligned, rev, g.bits, 0.f, 0.f, lam, Lm, pa);
+            else newton_sweep<T, L1, true, false>(y, sp, sw, aligned, rev, g.bits, 0.f, 0.f, lam, Lm, pa);
+        } else {
+            if (first) newton_sweep<T, L1, false, true>(y, sp, sw, aligned, rev, g.bits, 0.f, 0.f, lam, Lm, pa);
+            else newton_sweep<T, L1, false, false>(y, sp, sw, aligned, rev, g.bits, 0.f, 0.f, lam, Lm, pa);
+        }
+    } else {
+        const float rd = f32_rd(-lam), ru = f32_ru(-lam);
+        const df Lm = df_from_f64(lam);
+        if (first) newton_sweep<T, L1, false, true>(y, sp, sw, aligned, rev, 0ull, rd, ru, lam, Lm, pa);
+        else newton_sweep<T, L1, false, false>(y, sp, sw, aligned, rev, 0ull, rd, ru, lam, Lm, pa);
+        pa.acc64 = df_to_f64(pa.acc32);
+    }
+}
+
+// The scalar part of one Alg. 4 iteration from phi(lambda_k) and its lateral slopes: bracket,
+// Newton step, the stopping tests of Sec. 4.  Returns true when the loop stops; then fin is
+// the final multiplier, else next is lambda_{k+1}.
+struct Alg4State {
+    double lower, upper, slope;
+    int stop;
+};
+__device__ __forceinline__ bool alg4_update(Alg4State& a, int k, double lam, double phi, double dminus, double dplus,
+                                            double r, double eps34, bool final_step, double& next, double& fin) {
+    const double gk = phi - r;
+    double step = 0.0;
+    bool done = false;
+    next = lam;
+    fin = lam;
+    if (k == 0) {
+        if (gk == 0.0) {
+            a.stop = CQK_STOP_EXACT;
+            done = true;
+        } else if (gk < 0.0) {
+            a.lower = lam;
+            a.slope = dplus;
+            step = -gk / dplus;
+        } else {
+            a.upper = lam;
+            a.slope = dminus;
+            step = -gk / dminus;
+        }
+    } else if (gk <= 0.0) {
+        a.stop = CQK_STOP_BELOW;
+        done = true;
+    } else {
+        a.upper = lam;
+        a.slope = dminus;
+        step = -gk / dminus;
+    }
+    if (!done && a.upper - a.lower < eps34 * fmax(fabs(a.upper), fabs(a.lower))) {
+        a.stop = CQK_STOP_BRACKET;
+        done = true;
+    }
+    if (!done && fabs(step) < eps34) {
+        a.stop = CQK_STOP_STEP;
+        done = true;
+        if (final_step) fin = lam + step;  // the Newton step already computed
+    }
+    if (!done) {
+        next = lam + step;
+        if (next == lam) {
+            a.stop = CQK_STOP_SAME;
+            done = true;
+        }
+    }
+    return done;
+}
+
 // per-block totals of a pass (fixed order) -> partials slot `par`, and into blk (thread 0);
 // a one-block group (solo) keeps them in registers only
 __device__ __forceinline__ void write_pass_partials(const Grp& gp, int par, double acc, unsigned cm, unsigned ct,
@@ -780,6 +861,76 @@ __device__ __forceinline__ void warp0_grid_sums(const double* part, int G, int p
     for (int q = 0; q < 3; q++) out[q] = warp_sum(v[q]);
 }
 
+// the final pass: x_i = max{0, y_i + lambda} (l1: sgn(y_i) max{0, |y_i| + lambda}; copy: x = y),
+// the free mask, and the sum of the stored |x| and the count of nonzero x
+template <typename T, bool L1>
+__device__ __forceinline__ void final_sweep(const T* __restrict__ y, T* __restrict__ x, uint32_t* mask,
+                                            const Span& sp, const WarpSweep& sw, bool aligned, bool rev, bool copy,
+                                            double lamf, double& sx, df& sx32, long long& nz) {
+    constexpr int V = VecOf<T>::V;
+    const int lane = threadIdx.x & 31;
+    {
+        const GtThreshold g = make_gt(-lamf);
+        const float rd = f32_rd(-lamf);
+        const df Lm = df_from_f64(lamf);
+        for (int64_t it = 0; it < sw.count; it++) {
+            const int64_t base = sw.base(it, rev);
+            T vv[kStreamU][V];
+            bool okk[kStreamU][V];
+#pragma unroll
+            for (int u = 0; u < kStreamU; u++) load_vec<T>(y, sp, base + u * 32 + lane, aligned, vv[u], okk[u]);
+#pragma unroll
+            for (int u = 0; u < kStreamU; u++) {
+                const int64_t qw = base + u * 32;
+                const int64_t q = qw + lane;
+                const T(&v)[V] = vv[u];
+                const bool(&ok)[V] = okk[u];
+                T o[V];
+                bool sel[V];
+                unsigned selv = 0;
+#pragma unroll
+                for (int j = 0; j < V; j++) {
+                    if constexpr (sizeof(T) == 8) {
+                        const unsigned long long b = bits_of((double)v[j]);
+                        const unsigned long long ab = b & 0x7FFFFFFFFFFFFFFFull;
+                        sel[j] = ok[j] && (copy ? ab != 0ull : gt_bits(L1 ? ab : b, g));
+                    } else {
+                        const float f = (float)v[j];
+                        sel[j] = ok[j] && (copy ? f != 0.0f : (L1 ? fabsf(f) : f) > rd);
+                    }
+                    o[j] = copy ? v[j] : T(0);
+                    nz += sel[j];
+                    selv |= (sel[j] && !copy ? 1u : 0u) << j;
+                }
+                // x_i = y_i + lambda (l1: sgn(y_i)(|y_i| + lambda)), one trip per selected element
+                for (unsigned m = selv; m; m &= m - 1) {
+                    const int j = __ffs(m) - 1;
+                    const T vj = pick(v, j);
+                    if constexpr (sizeof(T) == 8) {
+                        // |x_i| = |y_i| + lambda > 0; the l1 ball copies the sign of y_i (bit operations)
+                        const unsigned long long yb = bits_of((double)vj);
+                        const double xm =
+                            (L1 ? __longlong_as_double((long long)(yb & 0x7FFFFFFFFFFFFFFFull)) : (double)vj) + lamf;
+                        const double xv =
+                            L1 ? __longlong_as_double((long long)(bits_of(xm) | (yb & 0x8000000000000000ull))) : xm;
+                        put(o, j, (T)xv);
+                        sx += xm;
+                    } else {
+                        const float f = (float)vj;
+                        const df t = df_add_f(Lm, L1 ? fabsf(f) : f);
+                        float xv = __fadd_rn(t.hi, t.lo);
+                        if (L1 && f < 0.0f) xv = -xv;
+                        put(o, j, (T)xv);
+                        sx32 = df_add_f(sx32, fabsf(xv));
+                    }
+                }
+                store_vec<T>(x, sp, q, aligned, o);
+                if (mask) store_mask<V>(mask, sp, qw, sel);
+            }
+        }
+    }
+}
+
 // one pass over the group's span accumulating the sum and maximum of y (l1: |y|) and the NaN
 // check (every thread of the group)
 template <typename T, bool L1>
@@ -804,6 +955,31 @@ __device__ __forceinline__ void sum_sweep(const T* __restrict__ y, const Span& s
             // values outside the df operating range: exact FP64, one trip per element
             for (unsigned m = widem; m; m &= m - 1) sum_wide<T, L1>(sacc, pick2(vv, __ffs(m) - 1));
             // fold the lazy pair (at most 64 terms) into FP64: one FP64 add per 4 sweeps
+            if ((it & 3) == 3) sacc.fold();
+        }
+    }
+}
+
+// sum_sweep by one warp alone
+template <typename T, bool L1>
+__device__ __forceinline__ void sum_sweep_warp(const T* __restrict__ y, const Span& sp, bool aligned, SumAcc& sacc) {
+    constexpr int V = VecOf<T>::V;
+    const int lane = threadIdx.x & 31;
+    const WarpSweep sw = WarpSweep::solo(span_qlo<V>(sp), span_qhi<V>(sp), kStreamU);
+    for (int64_t it = 0; it < sw.count; it++) {
+        const int64_t base = sw.base(it, false);
+        T vv[kStreamU][V];
+        bool okk[kStreamU][V];
+#pragma unroll
+        for (int u = 0; u < kStreamU; u++) load_vec<T>(y, sp, base + u * 32 + lane, aligned, vv[u], okk[u]);
+        unsigned widem = 0;
+#pragma unroll
+        for (int uj = 0; uj < kStreamU * V; uj++) {
+            const int u = uj / V, j = uj % V;
+            if (okk[u][j] && sum_elem<T, L1>(sacc, vv[u][j])) widem |= 1u << uj;
+        }
+        if constexpr (sizeof(T) == 8) {
+            for (unsigned m = widem; m; m &= m - 1) sum_wide<T, L1>(sacc, pick2(vv, __ffs(m) - 1));
             if ((it & 3) == 3) sacc.fold();
         }
     }
@@ -948,14 +1124,14 @@ __device__ __forceinline__ void simplex_solve(const SimplexArgs& A, const Grp& g
     // ------------------------------------------------------------------ Newton loop (Alg. 4)
     // thread 0 keeps the bracket and the stopping logic; every thread keeps lambda
     double lam = lam0, final_lam = lam0;
-    double lower = -INFINITY, upper = INFINITY, slope = 0.0;  // thread 0
-    int status = CQK_OK, stop = CQK_STOP_NONE, k = 0;         // thread 0 (status also all)
+    Alg4State a4{-INFINITY, INFINITY, 0.0, CQK_STOP_NONE};  // thread 0
+    int status = CQK_OK, k = 0;                              // status: all threads
     bool copy = false;                                       // l1 ball, y inside
     if (bad_input) {
         status = CQK_BAD_INPUT;
     } else if (L1 && abs_sum <= r) {
         copy = true;
-        stop = CQK_STOP_INSIDE;
+        a4.stop = CQK_STOP_INSIDE;
         lam = final_lam = 0.0;
     } else {
         int par = par0;
@@ -974,23 +1150,7 @@ __device__ __forceinline__ void simplex_solve(const SimplexArgs& A, const Grp& g
             pa.nan = false;
             const bool rev = (k & 1) == 0;
             const bool first = (k == 0) && ties;
-            if constexpr (sizeof(T) == 8) {
-                const GtThreshold g = make_gt(-lam);
-                const df Lm = df_make(0.0f);
-                if (g.neg) {
-                    if (first) newton_sweep<T, L1, true, true>(y, sp, gp, aligned, rev, g.bits, 0.f, 0.f, lam, Lm, pa);
-                    else newton_sweep<T, L1, true, false>(y, sp, gp, aligned, rev, g.bits, 0.f, 0.f, lam, Lm, pa);
-                } else {
-                    if (first) newton_sweep<T, L1, false, true>(y, sp, gp, aligned, rev, g.bits, 0.f, 0.f, lam, Lm, pa);
-                    else newton_sweep<T, L1, false, false>(y, sp, gp, aligned, rev, g.bits, 0.f, 0.f, lam, Lm, pa);
-                }
-            } else {
-                const float rd = f32_rd(-lam), ru = f32_ru(-lam);
-                const df Lm = df_from_f64(lam);
-                if (first) newton_sweep<T, L1, false, true>(y, sp, gp, aligned, rev, 0ull, rd, ru, lam, Lm, pa);
-                else newton_sweep<T, L1, false, false>(y, sp, gp, aligned, rev, 0ull, rd, ru, lam, Lm, pa);
-                pa.acc64 = df_to_f64(pa.acc32);
-            }
+            newton_pass<T, L1>(y, sp, WarpSweep(qlo, qhi, kStreamU, gp.member, gp.g), aligned, rev, first, lam, pa);
             passes++;
             if (A.validate && first && __any_sync(0xffffffffu, pa.nan) && lane == 0)
                 atomicOr(&gp.hdr->flags, kFlagBadInput);
@@ -1018,47 +1178,9 @@ __device__ __forceinline__ void simplex_solve(const SimplexArgs& A, const Grp& g
                     } else if (k == 0 && !first && red[0] - r < 0.0) {
                         redo = 1;  // phi(lambda_0) < r: the step needs phi'_+, count the ties
                     } else {
-                        const double phi = red[0], dminus = red[1], dplus = red[2];
-                        const double gk = phi - r;
-                        double step = 0.0;
-                        if (k == 0) {
-                            if (gk == 0.0) {
-                                stop = CQK_STOP_EXACT;
-                                done = 1;
-                            } else if (gk < 0.0) {
-                                lower = lam;
-                                slope = dplus;
-                                step = -gk / dplus;
-                            } else {
-                                upper = lam;
-                                slope = dminus;
-                                step = -gk / dminus;
-                            }
-                        } else if (gk <= 0.0) {
-                            stop = CQK_STOP_BELOW;
-                            done = 1;
-                        } else {
-                            upper = lam;
-                            slope = dminus;
-                            step = -gk / dminus;
-                        }
-                        double fin = lam;
-                        if (!done && upper - lower < A.eps34 * fmax(fabs(upper), fabs(lower))) {
-                            stop = CQK_STOP_BRACKET;
-                            done = 1;
-                        }
-                        if (!done && fabs(step) < A.eps34) {
-                            stop = CQK_STOP_STEP;
-                            done = 1;
-                            if (A.final_step) fin = lam + step;  // the Newton step already computed
-                        }
-                        if (!done) {
-                            next = lam + step;
-                            if (next == lam) {
-                                stop = CQK_STOP_SAME;
-                                done = 1;
-                            }
-                        }
+                        double fin;
+                        done = alg4_update(a4, k, lam, red[0], red[1], red[2], r, A.eps34, A.final_step != 0, next,
+                                           fin) ? 1 : 0;
                         s_final = fin;
                     }
                     s_lam = next;
@@ -1097,69 +1219,9 @@ __device__ __forceinline__ void simplex_solve(const SimplexArgs& A, const Grp& g
     df sx32 = df_make(0.0f);
     long long nz = 0;
     T* __restrict__ x = static_cast<T*>(A.x);
-    if (!bad_input) {
-        const double lamf = final_lam;
-        const GtThreshold g = make_gt(-lamf);
-        const float rd = f32_rd(-lamf);
-        const df Lm = df_from_f64(lamf);
-        const WarpSweep sw(qlo, qhi, kStreamU, gp.member, gp.g);
-        const bool rev = (k & 1) == 0;  // opposite direction to the last Newton pass
-        for (int64_t it = 0; it < sw.count; it++) {
-            const int64_t base = sw.base(it, rev);
-            T vv[kStreamU][V];
-            bool okk[kStreamU][V];
-#pragma unroll
-            for (int u = 0; u < kStreamU; u++) load_vec<T>(y, sp, base + u * 32 + lane, aligned, vv[u], okk[u]);
-#pragma unroll
-            for (int u = 0; u < kStreamU; u++) {
-                const int64_t qw = base + u * 32;
-                const int64_t q = qw + lane;
-                const T(&v)[V] = vv[u];
-                const bool(&ok)[V] = okk[u];
-                T o[V];
-                bool sel[V];
-                unsigned selv = 0;
-#pragma unroll
-                for (int j = 0; j < V; j++) {
-                    if constexpr (sizeof(T) == 8) {
-                        const unsigned long long b = bits_of((double)v[j]);
-                        const unsigned long long ab = b & 0x7FFFFFFFFFFFFFFFull;
-                        sel[j] = ok[j] && (copy ? ab != 0ull : gt_bits(L1 ? ab : b, g));
-                    } else {
-                        const float f = (float)v[j];
-                        sel[j] = ok[j] && (copy ? f != 0.0f : (L1 ? fabsf(f) : f) > rd);
-                    }
-                    o[j] = copy ? v[j] : T(0);
-                    nz += sel[j];
-                    selv |= (sel[j] && !copy ? 1u : 0u) << j;
-                }
-                // x_i = y_i + lambda (l1: sgn(y_i)(|y_i| + lambda)), one trip per selected element
-                for (unsigned m = selv; m; m &= m - 1) {
-                    const int j = __ffs(m) - 1;
-                    const T vj = pick(v, j);
-                    if constexpr (sizeof(T) == 8) {
-                        // |x_i| = |y_i| + lambda > 0; the l1 ball copies the sign of y_i (bit operations)
-                        const unsigned long long yb = bits_of((double)vj);
-                        const double xm =
-                            (L1 ? __longlong_as_double((long long)(yb & 0x7FFFFFFFFFFFFFFFull)) : (double)vj) + lamf;
-                        const double xv =
-                            L1 ? __longlong_as_double((long long)(bits_of(xm) | (yb & 0x8000000000000000ull))) : xm;
-                        put(o, j, (T)xv);
-                        sx += xm;
-                    } else {
-                        const float f = (float)vj;
-                        const df t = df_add_f(Lm, L1 ? fabsf(f) : f);
-                        float xv = __fadd_rn(t.hi, t.lo);
-                        if (L1 && f < 0.0f) xv = -xv;
-                        put(o, j, (T)xv);
-                        sx32 = df_add_f(sx32, fabsf(xv));
-                    }
-                }
-                store_vec<T>(x, sp, q, aligned, o);
-                if (A.mask) store_mask<V>(A.mask, sp, qw, sel);
-            }
-        }
-    }
+    if (!bad_input)
+        final_sweep<T, L1>(y, x, A.mask, sp, WarpSweep(qlo, qhi, kStreamU, gp.member, gp.g), aligned, (k & 1) == 0,
+                           copy, final_lam, sx, sx32, nz);
     if constexpr (sizeof(T) == 4) sx = df_to_f64(sx32);
     double pv[2] = {sx, (double)nz}, tot[2];
     if (last_block_sums<2>(gp.part, gp.member, G, &gp.hdr->ticket, pv, tot, sh) && threadIdx.x == 0) {
@@ -1168,16 +1230,205 @@ __device__ __forceinline__ void simplex_solve(const SimplexArgs& A, const Grp& g
         inf.lambda = final_lam;
         inf.residual = sumx - r;
         inf.abs_bx = sumx;
-        inf.slope = slope;
+        inf.slope = a4.slope;
         inf.lambda0 = lam0;
         inf.nfree = (int64_t)tot[1];
         inf.iters = k;
         const int e = *(volatile int*)&gp.hdr->error;
         inf.status = e ? e : status;
         inf.passes = passes + (bad_input ? 0 : 1);
-        inf.stop = stop;
+        inf.stop = a4.stop;
         inf.nchunks = nchunks;
         inf.tile = tile;
+        *A.info = inf;
+    }
+}
+
+// ---- one small projection by one warp ------------------------------------------------------
+// The same method as simplex_solve for an instance that one warp streams quickly: the Alg. 2
+// start is one chunk (the whole instance, tiles of 32 vectors in index order), the Newton
+// loop reduces with warp shuffles only, and every lane runs the same scalar update (no
+// barrier, no shared state but the warp's accepted-value list).  Called by the 32 lanes of
+// one warp; list has kWarpList entries.
+constexpr int kWarpList = 1024;
+static_assert(kWarpList * NWARP * sizeof(double) <= kCondatSmem, "warp lists fit the stage memory");
+
+template <typename T, bool L1>
+__device__ void simplex_warp_solve(const SimplexArgs& A, const Span& sp, double* list) {
+    constexpr int V = VecOf<T>::V;
+    const T* __restrict__ y = static_cast<const T*>(A.y);
+    const int lane = threadIdx.x & 31;
+    const int64_t n = sp.hi - sp.lo;
+    const int64_t qlo = span_qlo<V>(sp), qhi = span_qhi<V>(sp);
+    const bool aligned = A.aligned != 0;
+    const double r = A.r;
+    const bool warm = A.init == CQK_INIT_WARM;
+    const bool condat = A.init == CQK_INIT_CONDAT || warm;
+    const T* __restrict__ xb = warm ? static_cast<const T*>(A.xbar) : nullptr;
+    int passes = 0;
+
+    // ---- pass 0: start
+    SumAcc sacc;
+    sacc.init();
+    double lam0 = 0.0, abs_sum = 0.0, Sunion = 0.0;
+    bool condat_start = false;
+    if (!condat) {
+        sum_sweep_warp<T, L1>(y, sp, aligned, sacc);
+        passes++;
+    } else {
+        CondatState st;
+        st.S = 0.0;
+        st.Sd = df{0.0f, 0.0f};
+        st.nJ = 0;
+        st.rs = -1;
+        st.lam = df{0.0f, 0.0f};
+        st.band = 0.0f;
+        st.sderr = 0.0f;
+        st.sdok = true;
+        st.dfok = df_in_range(r, false) && r != 0.0;
+        st.eS = st.ey = 0.0;
+        st.en = 0;
+        st.clo = -INFINITY;
+        st.chi = INFINITY;
+        st.glo = make_gt(-INFINITY);
+        st.ghi = make_gt(INFINITY);
+        st.list = list;
+        st.cnt = 0;
+        st.jt_end = 0;
+        const df rdf = split_f64(r);
+        for (int64_t q0 = (qlo / 32) * 32; q0 < qhi; q0 += 32) {
+            const int64_t q = q0 + lane;
+            T v[V];
+            bool ok[V];
+            load_vec<T>(y, sp, q, aligned, v, ok);
+#pragma unroll
+            for (int j = 0; j < V; j++) {
+                if constexpr (sizeof(T) == 8) sacc.bad |= ok[j] && u64_is_nan(bits_of((double)v[j]));
+                else sacc.bad |= ok[j] && (v[j] != v[j]);
+            }
+            support_mask<T, L1>(xb, sp, q, aligned, ok);
+            condat_slab<T, L1>(v, ok, q * V, r, rdf, st);
+        }
+        passes++;
+        if (st.nJ > 0) {
+            if (st.jt_end <= kWarpList) {  // the final loop of Alg. 2 over J~
+                __syncwarp();
+                for (int e = 0; e < st.jt_end; e++) {
+                    const double val = list[e];
+                    if (condat_gt<L1>(val, st, r)) condat_add<L1>(st, r, rdf, val);
+                }
+            } else {
+                for (int64_t q0 = (qlo / 32) * 32; q0 * V <= st.rs; q0 += 32) {
+                    const int64_t q = q0 + lane;
+                    T v[V];
+                    bool ok[V];
+                    load_vec<T>(y, sp, q, aligned, v, ok);
+                    support_mask<T, L1>(xb, sp, q, aligned, ok);
+                    condat_rescan_slab<T, L1>(v, ok, q * V, r, rdf, st);
+                }
+            }
+            lam0 = (r - st.S) / (double)st.nJ;  // eq. (lambdaJ)
+            condat_start = true;
+            Sunion = st.S;
+        } else {
+            // warm start with an empty J_+ (Sec. 3.3)
+            const double y1 = (double)y[sp.lo];
+            lam0 = fmax(r / (double)n, L1 ? -fabs(y1) : -y1);
+        }
+    }
+    const bool bad_input = A.validate && __any_sync(0xffffffffu, sacc.bad);
+    if (!condat) {
+        const double sum = warp_sum(sacc.sum()), mx = warp_max(sum_max<T>(sacc));
+        abs_sum = sum;
+        if (A.init == CQK_INIT_GIVEN) lam0 = fmax(A.lambda0, -mx);  // Alg. 4, line 1
+        else lam0 = fmax((r - sum) / (double)n, -mx);                // eq. (CQKlambda0); Alg. 4 line 1
+    } else if (L1) {
+        // the inside test of the l1 ball (see simplex_solve)
+        const bool outside = condat_start && (r - Sunion) < -1e-13 * (fabs(r) + fabs(Sunion));
+        if (outside) {
+            abs_sum = INFINITY;
+        } else {
+            SumAcc s2;
+            s2.init();
+            sum_sweep_warp<T, L1>(y, sp, aligned, s2);
+            passes++;
+            abs_sum = warp_sum(s2.sum());
+        }
+    }
+
+    // ---- Newton loop (Alg. 4): every lane holds the same state
+    double lam = lam0, final_lam = lam0;
+    Alg4State a4{-INFINITY, INFINITY, 0.0, CQK_STOP_NONE};
+    int status = CQK_OK, k = 0;
+    bool copy = false;
+    if (bad_input) {
+        status = CQK_BAD_INPUT;
+    } else if (L1 && abs_sum <= r) {
+        copy = true;
+        a4.stop = CQK_STOP_INSIDE;
+        lam = final_lam = 0.0;
+    } else {
+        bool ties = !condat_start;
+        for (k = 0;; k++) {
+            if (k >= A.max_iter) {
+                status = CQK_MAXITER;
+                break;
+            }
+            const bool first = (k == 0) && ties;
+            PassAcc pa;
+            newton_pass<T, L1>(y, sp, WarpSweep::solo(qlo, qhi, kStreamU), aligned, (k & 1) == 0, first, lam, pa);
+            passes++;
+            const double phi = warp_sum(pa.acc64);
+            const double dminus = (double)__reduce_add_sync(0xffffffffu, pa.cm);
+            const double dplus = dminus + (double)__reduce_add_sync(0xffffffffu, pa.ct);
+            if (A.validate && first && __any_sync(0xffffffffu, pa.nan)) {
+                status = CQK_BAD_INPUT;
+                k++;
+                copy = false;
+                final_lam = lam;
+                break;
+            }
+            if (k == 0 && !first && phi - r < 0.0) {  // the first step needs phi'_+: count the ties
+                ties = true;
+                k--;
+                continue;
+            }
+            double next, fin;
+            if (alg4_update(a4, k, lam, phi, dminus, dplus, r, A.eps34, A.final_step != 0, next, fin)) {
+                final_lam = fin;
+                k++;
+                break;
+            }
+            lam = next;
+            final_lam = lam;
+        }
+    }
+
+    // ---- final pass: x, mask, sums
+    double sx = 0.0;
+    df sx32 = df_make(0.0f);
+    long long nz = 0;
+    if (status != CQK_BAD_INPUT)
+        final_sweep<T, L1>(y, static_cast<T*>(A.x), A.mask, sp, WarpSweep::solo(qlo, qhi, kStreamU), aligned,
+                           (k & 1) == 0, copy, final_lam, sx, sx32, nz);
+    if constexpr (sizeof(T) == 4) sx = df_to_f64(sx32);
+    sx = warp_sum(sx);
+    const long long nzt = (long long)__reduce_add_sync(0xffffffffu, (unsigned)nz);
+    if (lane == 0) {
+        cqk_info inf;
+        const double sumx = copy ? abs_sum : sx;
+        inf.lambda = final_lam;
+        inf.residual = sumx - r;
+        inf.abs_bx = sumx;
+        inf.slope = a4.slope;
+        inf.lambda0 = lam0;
+        inf.nfree = nzt;
+        inf.iters = k;
+        inf.status = status;
+        inf.passes = passes + (status == CQK_BAD_INPUT ? 0 : 1);
+        inf.stop = a4.stop;
+        inf.nchunks = condat ? 1 : 0;
+        inf.tile = condat ? condat_tile<T>() : 0;
         *A.info = inf;
     }
 }
@@ -1227,6 +1478,28 @@ __global__ void __launch_bounds__(NT, 2) simplex_batched_kernel(SimplexBatchArgs
     init_condat_bars(bars);
     while (true) {
         const Slot sl = next_slot(P.R, P.B);
+        if (sl.pack_first >= 0) {  // a pack of small instances, one per warp
+            const long long p = sl.pack_first + (threadIdx.x >> 5);
+            if (p < P.B) {
+                const int inst = P.R.order[p];
+                const Span sp{P.offsets[inst], P.offsets[inst + 1]};
+                SimplexArgs A = P.base;
+                A.r = P.r[inst];
+                A.info = P.info + inst;
+                const int64_t len = sp.hi - sp.lo;
+                const bool r_ok = A.r > 0.0 && A.r < INFINITY;
+                if (len <= 0 || !r_ok) {
+                    if ((threadIdx.x & 31) == 0) {
+                        if (len < 0 || !r_ok) write_plain_info(A.info, CQK_BAD_ARG, CQK_STOP_NONE, A.r);
+                        else if (L1) write_plain_info(A.info, CQK_OK, CQK_STOP_INSIDE, A.r);
+                        else write_plain_info(A.info, CQK_INFEASIBLE, CQK_STOP_NONE, A.r);
+                    }
+                } else {
+                    simplex_warp_solve<T, L1>(A, sp, reinterpret_cast<double*>(dyn_smem) + (threadIdx.x >> 5) * kWarpList);
+                }
+            }
+            continue;
+        }
         if (sl.inst < 0) break;
         const Grp gp = slot_group(P.R, P.offsets, sl);
         SimplexArgs A = P.base;
@@ -1288,7 +1561,8 @@ int launch_simplex_batched(int64_t B, const int64_t* offsets, int dtype, const v
     if (grid <= 0) return CQK_CUDA_ERROR;
     if ((int64_t)grid > B * kMaxGroup) grid = (int)(B * kMaxGroup);
     const int64_t per_block = o.group_elems > 0 ? o.group_elems : kSimplexGroupElems;
-    int rc = plan_batch(offsets, B, per_block, grid, ws, s);
+    // instances shorter than 2^warp_log2 are solved one per warp
+    int rc = plan_batch(offsets, B, per_block, grid, ws, s, o.warp_log2);
     if (rc != CQK_OK) return rc;
     void* args[] = {&P};
     e = cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(NT), args, kCondatSmem, s);
