@@ -112,7 +112,7 @@ typedef struct cqk_options {
     const void* xbar;       /* CQK_INIT_WARM: the primal estimate (device; NULL otherwise)       */
     int32_t warp_elems;     /* batched projections: instances shorter than warp_elems (rounded  */
                             /* down to a power of two) are solved by one warp each; 0 (default): */
-                            /* 4096; negative: never                                            */
+                            /* 16384; negative: never                                           */
     int32_t reserved[3];
 } cqk_options;
 

@@ -33,11 +33,11 @@ Opts resolve_options(const cqk_options* opt, int dtype, int default_init) {
     o.group_elems = d.group_elems > 0 ? d.group_elems : 0;
     o.condat_chunk = d.condat_chunk > 0 ? d.condat_chunk : kCondatChunkElems;
     o.xbar = d.xbar;
-    // warp_elems: 0 -> 4096 (default), < 0 -> no warp-level instances, else rounded down to 2^k
+    // warp_elems: 0 -> 16384 (default), < 0 -> no warp-level instances, else rounded down to 2^k
     if (d.warp_elems < 0) {
         o.warp_log2 = 0;
     } else {
-        const long long we = d.warp_elems > 0 ? d.warp_elems : 4096;
+        const long long we = d.warp_elems > 0 ? d.warp_elems : 16384;
         int lg = 0;
         while ((2ll << lg) <= we && lg < 30) lg++;
         o.warp_log2 = lg;

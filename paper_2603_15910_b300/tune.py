@@ -5,6 +5,7 @@ Tunables (all options of ``cqk_options``; the kernels are the same, only the wor
 changes):
   group_elems   elements per block of an instance's group (how many blocks solve one instance)
   condat_chunk  minimum elements per chunk of the parallel Alg. 2 start (projections)
+  warp_elems    instances shorter than this are solved by one warp each (projections)
   max_blocks    an upper bound on the persistent grid
 
 The signature of a batch is (entry point, dtype, number of instances, log2 of the total
@@ -27,9 +28,10 @@ _cache: dict = {}
 _lock = threading.Lock()
 
 SIMPLEX_CANDIDATES = [
-    dict(group_elems=ge, condat_chunk=cc)
+    dict(group_elems=ge, condat_chunk=cc, warp_elems=we)
     for ge in (1 << 16, 1 << 18, 1 << 20, (1 << 31) - 1)
     for cc in (512, 1 << 14)
+    for we in (4096, 16384, 1 << 17)
 ]
 GENERAL_CANDIDATES = [dict(group_elems=ge) for ge in (1 << 14, 1 << 15, 1 << 16, 1 << 17, 1 << 18)]
 
