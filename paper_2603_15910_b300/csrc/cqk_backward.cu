@@ -22,7 +22,8 @@
 namespace cqk {
 namespace {
 
-constexpr int kBwdU = 2;  // 16-byte vectors per array in flight per lane
+constexpr int kBwdU = 2;     // 16-byte vectors per array in flight per lane (projections: 2 arrays)
+constexpr int kBwdUGen = 1;  // general: 6 arrays, and the register budget of the double-float map
 
 enum BwdKind { kBwdGeneral = 0, kBwdSimplex = 1, kBwdL1 = 2 };
 
@@ -44,6 +45,28 @@ struct BwdArgs {
     BatchRefs R;
 };
 
+// order comparisons of stored values on the integer pipe (an FP64 compare per element would
+// take the FP64 unit): keys with -0 taken as +0; NaN never compares
+template <typename T>
+__device__ __forceinline__ long long cmpkey(T v) {
+    if constexpr (sizeof(T) == 8) {
+        const unsigned long long b = opaque_bits((double)v);
+        return (b << 1) == 0ull ? 0ll : order_key((double)v);
+    } else {
+        return (long long)__float_as_int((float)v);  // unused for floats
+    }
+}
+template <typename T>
+__device__ __forceinline__ bool lt_val(T a, T b) {
+    if constexpr (sizeof(T) == 8) return !f64_is_nan((double)a) && !f64_is_nan((double)b) && cmpkey(a) < cmpkey(b);
+    else return a < b;
+}
+template <typename T>
+__device__ __forceinline__ bool eq_val(T a, T b) {
+    if constexpr (sizeof(T) == 8) return !f64_is_nan((double)a) && cmpkey(a) == cmpkey(b);
+    else return a == b;
+}
+
 // free bits of the V elements of vector q (from the forward mask, else from l < x < u)
 template <typename T, int KIND>
 __device__ __forceinline__ unsigned free_bits(const BwdArgs& A, const Span& sp, int64_t q, const T (&x)[VecOf<T>::V],
@@ -59,7 +82,7 @@ __device__ __forceinline__ unsigned free_bits(const BwdArgs& A, const Span& sp, 
 #pragma unroll
     for (int j = 0; j < V; j++) {
         bool fr;
-        if (KIND == kBwdGeneral) fr = l[j] < x[j] && x[j] < u[j];
+        if (KIND == kBwdGeneral) fr = lt_val<T>(l[j], x[j]) && lt_val<T>(x[j], u[j]);
         else if (KIND == kBwdSimplex) fr = x[j] > T(0);
         else fr = x[j] != T(0);
         f |= (fr ? 1u : 0u) << j;
@@ -97,6 +120,13 @@ __device__ __forceinline__ df to_df(T v) {
 template <typename T>
 __device__ __forceinline__ T from_df(df v) {
     if constexpr (sizeof(T) == 8) return df_to_f64_bits(v);
+    else return __fadd_rn(v.hi, v.lo);
+}
+// the same through one FP64 add (spreads the conversions of the general map over the FP64
+// and integer pipes)
+template <typename T>
+__device__ __forceinline__ T from_df_add(df v) {
+    if constexpr (sizeof(T) == 8) return df_to_f64_int(v);
     else return __fadd_rn(v.hi, v.lo);
 }
 // 1/d as a float pair (d > 0)
@@ -142,7 +172,7 @@ __device__ __noinline__ void bwd_map_exact(double g, double x, double b, double 
 template <typename T, int KIND>
 __device__ __forceinline__ void bwd_instance(const BwdArgs& A, const Grp& gp, int64_t inst) {
     constexpr int V = VecOf<T>::V;
-    constexpr int U = kBwdU;
+    constexpr int U = KIND == kBwdGeneral ? kBwdUGen : kBwdU;
     __shared__ double sh[kPartialQ][NWARP];
     __shared__ double bc[kPartialQ];
     const Span sp = gp.sp;
@@ -281,15 +311,15 @@ __device__ __forceinline__ void bwd_instance(const BwdArgs& A, const Grp& gp, in
                     const df mx = df_mul(M, X);
                     if (fr) {
                         const df ga = df_mul(res, inv_df(to_df<T>(vd[w][j])));
-                        oa[j] = from_df<T>(ga);
+                        oa[j] = from_df_add<T>(ga);
                         od[j] = from_df<T>(df_neg(df_mul(X, ga)));
-                        ob[j] = from_df<T>(df_add(df_mul(Lm, ga), df_neg(mx)));
+                        ob[j] = from_df_add<T>(df_add(df_mul(Lm, ga), df_neg(mx)));
                     } else {
-                        ob[j] = from_df<T>(df_neg(mx));
+                        ob[j] = from_df_add<T>(df_neg(mx));
                         bool lower = false;
                         if (need_lu) {
-                            lower = vx[w][j] == vl[w][j];
-                            if (lower && vl[w][j] == vu[w][j] && A.a) {
+                            lower = eq_val<T>(vx[w][j], vl[w][j]);
+                            if (lower && eq_val<T>(vl[w][j], vu[w][j]) && A.a) {
                                 // a fixed variable (l = u) is at its lower bound when (a + lambda b)/d <= l
                                 const double aj = (double)static_cast<const T*>(A.a)[q * V + j];
                                 lower = (aj + lam * (double)vb[w][j]) / (double)vd[w][j] <= (double)vl[w][j];
@@ -311,8 +341,8 @@ __device__ __forceinline__ void bwd_instance(const BwdArgs& A, const Grp& gp, in
                 bool lower = false;
                 if (KIND == kBwdGeneral && !fr && need_lu) {
                     const T lj = pick(vl[w], j), uj = pick(vu[w], j);
-                    lower = xj == lj;
-                    if (lower && lj == uj && A.a) {
+                    lower = eq_val<T>(xj, lj);
+                    if (lower && eq_val<T>(lj, uj) && A.a) {
                         const double aj = (double)static_cast<const T*>(A.a)[q * V + j];
                         lower = (aj + lam * (double)pick(vb[w], j)) / (double)pick(vd[w], j) <= (double)lj;
                     }
@@ -429,7 +459,8 @@ int launch_backward(int kind, int64_t B, const int64_t* offsets, int64_t n, int 
         grid = persistent_grid(kern, NT, 0, INT64_MAX / 2, o.max_blocks);
         if (grid <= 0) return CQK_CUDA_ERROR;
         if ((int64_t)grid > B * kMaxGroup) grid = (int)(B * kMaxGroup);
-        const int64_t per_block = o.group_elems > 0 ? o.group_elems : kBackwardGroupElems;
+        const int64_t per_block =
+            o.group_elems > 0 ? o.group_elems : (kind == kBwdGeneral ? kBackwardGroupElems : kSimplexGroupElems);
         const int rc = plan_batch(offsets, B, per_block, grid, ws, s);
         if (rc != CQK_OK) return rc;
     } else {

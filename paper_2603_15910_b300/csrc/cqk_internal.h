@@ -61,7 +61,7 @@ int launch_phi(int64_t n, int dtype, const void* a, const void* b, const void* d
 constexpr int64_t kSimplexGroupElems = 1 << 20;
 constexpr int64_t kGeneralGroupElems = 1 << 16;
 constexpr int64_t kCondatChunkElems = 512;
-constexpr int64_t kBackwardGroupElems = 1 << 18;
+constexpr int64_t kBackwardGroupElems = 1 << 15;  // general adjoint (projections: kSimplexGroupElems)
 size_t batch_ws_bytes(int64_t B);
 int plan_batch(const int64_t* offsets_dev, int64_t B, int64_t per_block, int gmax, void* ws, cudaStream_t s,
                int small_log2 = 0);
