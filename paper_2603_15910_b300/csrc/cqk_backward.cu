@@ -22,7 +22,7 @@
 namespace cqk {
 namespace {
 
-constexpr int kBwdU = 2;     // 16-byte vectors per array in flight per lane (projections: 2 arrays)
+constexpr int kBwdU = 4;     // 16-byte vectors per array in flight per lane (projections: 2 arrays)
 constexpr int kBwdUGen = 1;  // general: 6 arrays, and the register budget of the double-float map
 
 enum BwdKind { kBwdGeneral = 0, kBwdSimplex = 1, kBwdL1 = 2 };
@@ -168,8 +168,8 @@ __device__ __noinline__ void bwd_map_exact(double g, double x, double b, double 
     }
 }
 
-// one instance by one group
-template <typename T, int KIND>
+// one instance by one group (WARP: by one warp alone; gp.sp is the only field used)
+template <typename T, int KIND, bool WARP = false>
 __device__ __forceinline__ void bwd_instance(const BwdArgs& A, const Grp& gp, int64_t inst) {
     constexpr int V = VecOf<T>::V;
     constexpr int U = KIND == kBwdGeneral ? kBwdUGen : kBwdU;
@@ -182,7 +182,8 @@ __device__ __forceinline__ void bwd_instance(const BwdArgs& A, const Grp& gp, in
     const double lam = KIND == kBwdGeneral ? inf->lambda : 0.0;
     const bool inside = KIND == kBwdL1 && inf->stop == CQK_STOP_INSIDE;
     const bool need_lu = KIND == kBwdGeneral && (!A.mask || A.gl || A.gu);
-    const WarpSweep sw(span_qlo<V>(sp), span_qhi<V>(sp), U, gp.member, gp.g);
+    const WarpSweep sw = WARP ? WarpSweep::solo(span_qlo<V>(sp), span_qhi<V>(sp), U)
+                              : WarpSweep(span_qlo<V>(sp), span_qhi<V>(sp), U, gp.member, gp.g);
 
     // ---- pass 1: sum_F b g/d and Q = sum_F b^2/d (simplex / l1: sum_F (s) g and |F|)
     LazyDf Sl{0.0f, 0.0f}, Ql{0.0f, 0.0f};
@@ -250,15 +251,20 @@ __device__ __forceinline__ void bwd_instance(const BwdArgs& A, const Grp& gp, in
         }
     }
     double pv[2] = {lazy_value(Sl) + S64, KIND == kBwdGeneral ? lazy_value(Ql) + Q64 : (double)nF + Q64};
-    block_sum<2>(pv, sh);
-    write_partials<2>(gp.part, gp.member, gp.g, 0, pv);
-    const unsigned target = (unsigned)gp.g + (A.fault_inject ? 1u : 0u);
-    if (!group_barrier(gp, target, A.limit_ns, A.fault_inject != 0)) {
-        if (threadIdx.x == 0 && A.status) A.status[inst] = CQK_TIMEOUT;
-        return;
-    }
     double red[2];
-    grid_reduce<2>(gp.part, gp.g, 0, -1, red, sh, bc);
+    if constexpr (WARP) {
+        red[0] = warp_sum(pv[0]);
+        red[1] = warp_sum(pv[1]);
+    } else {
+        block_sum<2>(pv, sh);
+        write_partials<2>(gp.part, gp.member, gp.g, 0, pv);
+        const unsigned target = (unsigned)gp.g + (A.fault_inject ? 1u : 0u);
+        if (!group_barrier(gp, target, A.limit_ns, A.fault_inject != 0)) {
+            if (threadIdx.x == 0 && A.status) A.status[inst] = CQK_TIMEOUT;
+            return;
+        }
+        grid_reduce<2>(gp.part, gp.g, 0, -1, red, sh, bc);
+    }
     const bool nondiff = !inside && !(red[1] > 0.0);
     const double mu = (inside || nondiff) ? 0.0 : red[0] / red[1];
     const df M = df_from_f64(mu), Lm = df_from_f64(lam);
@@ -367,7 +373,12 @@ __device__ __forceinline__ void bwd_instance(const BwdArgs& A, const Grp& gp, in
             }
         }
     }
-    if (gp.member == 0 && threadIdx.x == 0) {
+    if constexpr (WARP) {
+        if (lane == 0) {
+            if (A.gr) A.gr[inst] = mu;
+            if (A.status) A.status[inst] = nondiff ? CQK_NONDIFF : CQK_OK;
+        }
+    } else if (gp.member == 0 && threadIdx.x == 0) {
         if (A.gr) A.gr[inst] = mu;
         if (A.status) {
             const int e = *(volatile int*)&gp.hdr->error;
@@ -390,6 +401,27 @@ __global__ void __launch_bounds__(NT, 2) backward_kernel(BwdArgs A) {
     } else {
         while (true) {
             const Slot sl = next_slot(A.R, A.B);
+            if (KIND != kBwdGeneral && sl.pack_first >= 0) {  // small instances, one per warp
+                const long long p = sl.pack_first + (threadIdx.x >> 5);
+                if (p < A.B) {
+                    const int inst = A.R.order[p];
+                    Grp gw;
+                    gw.member = 0;
+                    gw.g = 1;
+                    gw.sp = Span{A.offsets[inst], A.offsets[inst + 1]};
+                    gw.hdr = nullptr;
+                    gw.part = nullptr;
+                    if (gw.sp.hi < gw.sp.lo) {
+                        if ((threadIdx.x & 31) == 0) {
+                            if (A.gr) A.gr[inst] = 0.0;
+                            if (A.status) A.status[inst] = CQK_BAD_ARG;
+                        }
+                    } else {
+                        bwd_instance<T, KIND, true>(A, gw, inst);
+                    }
+                }
+                continue;
+            }
             if (sl.inst < 0) break;
             const Grp gp = slot_group(A.R, A.offsets, sl);
             if (gp.sp.hi < gp.sp.lo) {
@@ -461,7 +493,7 @@ int launch_backward(int kind, int64_t B, const int64_t* offsets, int64_t n, int 
         if ((int64_t)grid > B * kMaxGroup) grid = (int)(B * kMaxGroup);
         const int64_t per_block =
             o.group_elems > 0 ? o.group_elems : (kind == kBwdGeneral ? kBackwardGroupElems : kSimplexGroupElems);
-        const int rc = plan_batch(offsets, B, per_block, grid, ws, s);
+        const int rc = plan_batch(offsets, B, per_block, grid, ws, s, kind == kBwdGeneral ? 0 : o.warp_log2);
         if (rc != CQK_OK) return rc;
     } else {
         A.n = n;
