@@ -191,6 +191,24 @@ __device__ __forceinline__ void put(X (&a)[N], int j, X v) {
 
 __device__ __forceinline__ unsigned long long bits_of(double v) { return opaque_bits(v); }
 
+// Combine the per-warp values sh[q][0..NWARP) in warp 0 with a fixed butterfly, so every lane
+// of warp 0 ends with the same bits (q == qmax takes the maximum, the others the sum).  Called
+// by the threads of warp 0 only.
+template <int NQ>
+__device__ __forceinline__ void warp0_combine(const double (*sh)[NWARP], int qmax, double (&out)[NQ]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int q = 0; q < NQ; q++) out[q] = lane < NWARP ? sh[q][lane] : ((q == qmax) ? -INFINITY : 0.0);
+#pragma unroll
+    for (int o = NWARP / 2; o > 0; o >>= 1) {
+#pragma unroll
+        for (int q = 0; q < NQ; q++) {
+            const double t = __shfl_xor_sync(0xffffffffu, out[q], o);
+            out[q] = (q == qmax) ? fmax(out[q], t) : out[q] + t;
+        }
+    }
+}
+
 // Sum NQ doubles over the block (fixed order); result valid in thread 0.
 template <int NQ>
 __device__ __forceinline__ void block_sum(double (&v)[NQ], double (*sh)[NWARP]) {
@@ -202,32 +220,31 @@ __device__ __forceinline__ void block_sum(double (&v)[NQ], double (*sh)[NWARP]) 
         for (int q = 0; q < NQ; q++) sh[q][wid] = v[q];
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
+        double t[NQ];
+        warp0_combine<NQ>(sh, -1, t);
 #pragma unroll
-        for (int q = 0; q < NQ; q++) {
-            double s = 0.0;
-            for (int w = 0; w < NWARP; w++) s += sh[q][w];
-            v[q] = s;
-        }
+        for (int q = 0; q < NQ; q++) v[q] = t[q];
     }
     __syncthreads();
 }
 
-// Reduce the partials of the group's g blocks for pass parity `par` (sums, and a max for
-// q == qmax); every block computes the same values in the same order.  Result in out[] (all
-// threads).
+// Totals of the group's g partials of pass parity `par` (sums, and a max for q == qmax), in
+// a fixed order; valid in every lane of warp 0.  Called by all threads; every block computes
+// the same bits.  The block's loads of the g partials are all in flight at once (g <= NT in
+// one round).
 template <int NQ>
-__device__ __forceinline__ void grid_reduce(const double* part, int g, int par, int qmax, double (&out)[NQ],
-                                            double (*sh)[NWARP], double* bc) {
+__device__ __forceinline__ void grid_totals_warp0(const double* part, int g, int par, int qmax, double (&out)[NQ],
+                                                  double (*sh)[NWARP]) {
     double v[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; q++) v[q] = (q == qmax) ? -INFINITY : 0.0;
     for (int bIdx = threadIdx.x; bIdx < g; bIdx += NT) {
+        double t[NQ];
 #pragma unroll
-        for (int q = 0; q < NQ; q++) {
-            double t = ld_cg(part + ((size_t)par * kPartialQ + q) * g + bIdx);
-            v[q] = (q == qmax) ? fmax(v[q], t) : v[q] + t;
-        }
+        for (int q = 0; q < NQ; q++) t[q] = ld_cg(part + ((size_t)par * kPartialQ + q) * g + bIdx);
+#pragma unroll
+        for (int q = 0; q < NQ; q++) v[q] = (q == qmax) ? fmax(v[q], t[q]) : v[q] + t[q];
     }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
@@ -237,13 +254,20 @@ __device__ __forceinline__ void grid_reduce(const double* part, int g, int par, 
         for (int q = 0; q < NQ; q++) sh[q][wid] = v[q];
     }
     __syncthreads();
+    if (threadIdx.x < 32) warp0_combine<NQ>(sh, qmax, out);
+}
+
+// Reduce the partials of the group's g blocks for pass parity `par` (sums, and a max for
+// q == qmax); every block computes the same values in the same order.  Result in out[] (all
+// threads).
+template <int NQ>
+__device__ __forceinline__ void grid_reduce(const double* part, int g, int par, int qmax, double (&out)[NQ],
+                                            double (*sh)[NWARP], double* bc) {
+    double t[NQ];
+    grid_totals_warp0<NQ>(part, g, par, qmax, t, sh);
     if (threadIdx.x == 0) {
 #pragma unroll
-        for (int q = 0; q < NQ; q++) {
-            double s = (q == qmax) ? -INFINITY : 0.0;
-            for (int w = 0; w < NWARP; w++) s = (q == qmax) ? fmax(s, sh[q][w]) : s + sh[q][w];
-            bc[q] = s;
-        }
+        for (int q = 0; q < NQ; q++) bc[q] = t[q];
     }
     __syncthreads();
 #pragma unroll

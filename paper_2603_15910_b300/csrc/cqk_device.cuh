@@ -328,21 +328,20 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned target, i
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        __threadfence();
+        // the release orders this block's writes (ordered before it by the block barrier)
+        // before the arrival; the acquire orders the other blocks' writes before the block
+        // barrier that ends the wait
         red_release_add_u32(count, 1u);
         int ok = 1;
         unsigned long long t0 = globaltimer_ns();
-        unsigned ns = 32;
         while (ld_acquire_u32(count) < target) {
             if (globaltimer_ns() - t0 > limit_ns) {
                 atomicExch(error, timeout_code);
                 ok = 0;
                 break;
             }
-            __nanosleep(ns);
-            if (ns < 256) ns <<= 1;
+            __nanosleep(32);
         }
-        __threadfence();
         s_ok = ok;
     }
     __syncthreads();

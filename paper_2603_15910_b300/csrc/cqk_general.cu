@@ -885,10 +885,9 @@ __device__ __forceinline__ void general_solve(const GeneralArgs& A, const Grp& g
             bp = warp_max(bp);
             if ((threadIdx.x & 31) == 0) sh[0][threadIdx.x >> 5] = bp;
             __syncthreads();
-            if (threadIdx.x == 0) {
-                double m = -INFINITY;
-                for (int w = 0; w < NWARP; w++) m = fmax(m, sh[0][w]);
-                const double pvb[1] = {m};
+            if (threadIdx.x < 32) {
+                double pvb[1];
+                warp0_combine<1>(sh, 0, pvb);
                 write_partials<1>(gp.part, gp.member, G, par, pvb);
             }
             __syncthreads();

@@ -156,21 +156,26 @@ constexpr int kJList = 1024;  // accepted values kept for the final loop
 
 struct CondatShared {
     unsigned msk[NWARP][16];  // filter ballots of each warp, (k, j) -> bit lane
+    unsigned pmsk[kCondatStages][32 * 4];  // pipelined filter: ballots of group g, (g, j) -> bit lane
     double list[kJList];
-    unsigned long long tb;    // the published test threshold
-    int tneg;
-    float trd;
+    unsigned long long tb;    // the published test threshold (FP64 data: bit pattern)
+    float trd;                // (FP32 data)
 };
 
 // ---- the scalar recurrence of Alg. 2 --------------------------------------------------------
-// The scan is one long dependency chain (lambda_{k+1} from lambda_k), and on this GPU every
-// dependent FP64 operation costs ~100 cycles (a chain update with one division measured
-// ~1150 cycles).  The decisions of the scan — y_j + lambda > 0 and the restart test
+// The scan is one long dependency chain (lambda_{k+1} from lambda_k) run by one warp, and on
+// this GPU dependent FP64 operations are slow (measured in one warp: a step in FP64 with the
+// reciprocal of the next count formed alongside ~1160 cycles, the double-float step below
+// ~800).  The decisions of the scan — y_j + lambda > 0 and the restart test
 // lambda_{J u {j}} < r - y_j — are therefore taken in double-float (FP32 pipe, error below
 // `band`) whenever the margin exceeds the bound, and otherwise from the exact FP64 values of
 // the sequential scan, recomputed from their exact operands: the FP64 sum S of J is kept in
 // the scan's order alongside its double-float copy.  The decisions, hence J, J~, |J| and S,
 // are those of the FP64 scan.
+//
+// The parts of the next lambda that depend on J alone (r - S, 1/(|J|+1), the error-bound
+// magnitudes) are formed right after each step, while the warp re-tests and picks the next
+// candidate, so that the chain of the next step starts from the candidate's own operands.
 struct CondatState {
     double S;  // exact: the FP64 sum of J in scan order
     df Sd;     // S in double-float
@@ -187,10 +192,57 @@ struct CondatState {
     // floats rounded outward around c(lambda): v > chi certainly passes, v <= clo certainly
     // fails (as doubles); in between the exact FP64 threshold decides
     float clo, chi;
-    GtThreshold glo, ghi;
+    GtThreshold glo, ghi;  // the same bounds as double bit patterns
+    // prepared for the next step (condat_prep): r - Sd, 1/(|J|+1) as a float pair and rounded
+    // up, |r| + |Sd| (float parts), and whether |J|+1 is not exact in a float
+    df rmS, inv;
+    float r0u, ab;
+    bool big;
     double* list;
     int cnt, jt_end;
 };
+
+__device__ __forceinline__ void condat_init(CondatState& st, double r, double* list) {
+    st.S = 0.0;
+    st.Sd = df{0.0f, 0.0f};
+    st.nJ = 0;
+    st.rs = -1;
+    st.lam = df{0.0f, 0.0f};
+    st.band = 0.0f;
+    st.sderr = 0.0f;
+    st.sdok = true;
+    st.dfok = df_in_range(r, false) && r != 0.0;
+    st.eS = st.ey = 0.0;
+    st.en = 0;
+    st.clo = -INFINITY;
+    st.chi = INFINITY;
+    st.glo = make_gt(-INFINITY);
+    st.ghi = make_gt(INFINITY);
+    st.rmS = st.inv = df{0.0f, 0.0f};
+    st.r0u = st.ab = 0.0f;
+    st.big = false;
+    st.list = list;
+    st.cnt = 0;
+    st.jt_end = 0;
+}
+
+// the operands of one candidate y (l1: |y|)
+struct CondatOp {
+    double y;
+    df yd;       // split of y
+    df rmy;      // r - y in double-float
+    float rb;    // error-bound magnitude of r - y
+    bool inr;    // y in the double-float range
+};
+__device__ __forceinline__ CondatOp condat_op(double y, df rd) {
+    CondatOp o;
+    o.y = y;
+    o.yd = split_f64(y);
+    o.rmy = df_add(rd, df_neg(o.yd));
+    o.rb = 2.8e-14f * (fabsf(rd.hi) + fabsf(o.yd.hi));
+    o.inr = df_in_range(y, false);
+    return o;
+}
 
 __device__ __forceinline__ df df_of_count(long long n) {  // exact for n < 2^36, normalised
     if (n < (1ll << 24)) return df{(float)n, 0.0f};
@@ -198,33 +250,45 @@ __device__ __forceinline__ df df_of_count(long long n) {  // exact for n < 2^36,
     return df{(float)h, (float)(n - h)};
 }
 
-// lambda_J u {y} = (r - S - y)/(|J| + 1) with S, y the exact operands; lambda = r - y when
-// restart is set (then S is unused)
+// the J-only parts of lambda_{J u {y}} for the current J (after every change of S, Sd, |J|)
+__device__ __forceinline__ void condat_prep(CondatState& st, df rd) {
+    st.rmS = df_add(rd, df_neg(st.Sd));
+    const long long n1 = st.nJ + 1;
+    st.big = n1 >= (1ll << 24);  // then the bound is infinite and FP64 decides
+    // 1/n as a float pair (n < 2^24 exactly representable; ~2^-46 relative): cheaper than a
+    // double-float division
+    const float nf = (float)(int)(st.big ? (1ll << 24) : n1);
+    const float r0 = __frcp_rn(nf);
+    const float e0 = fmaf(-nf, r0, 1.0f);
+    st.inv = fast_two_sum(r0, __fmul_rn(r0, e0));
+    st.r0u = __fmul_ru(r0, 1.0000001f);
+    st.ab = fabsf(rd.hi) + fabsf(st.Sd.hi);
+}
+
 template <bool L1>
 __device__ __forceinline__ void condat_bounds(CondatState& st);
 
+// lambda_{J u {y}} = (r - S - y)/(|J| + 1) into nx (st: the state before the step)
 template <bool L1>
-__device__ __forceinline__ void condat_lam(CondatState& st, double r, df rd, double S, df Sd, double y, df yd,
-                                           long long n_new, bool restart) {
-    st.eS = S;
-    st.ey = y;
-    st.en = restart ? 0 : n_new;
-    if (restart) {
-        st.lam = df_add(rd, df_neg(yd));
-        st.band = 2.8e-14f * (fabsf(rd.hi) + fabsf(yd.hi)) + 1e-37f;
-    } else {
-        const df num = df_add(df_add(rd, df_neg(Sd)), df_neg(yd));
-        // 1/n as a float pair (n < 2^24 exactly representable; ~2^-46 relative), then one
-        // double-float product: cheaper than a double-float division
-        const float nf = (float)n_new;
-        const float r0 = __frcp_rn(nf);
-        const float e0 = fmaf(-nf, r0, 1.0f);
-        const df inv = fast_two_sum(r0, __fmul_rn(r0, e0));
-        st.lam = df_mul(num, inv);
-        const float scale = 9.1e-13f * (fabsf(rd.hi) + fabsf(Sd.hi) + fabsf(yd.hi)) + 2.0f * st.sderr;
-        st.band = __fmul_ru(scale, __fmul_ru(r0, 1.0000001f)) + 9.1e-13f * fabsf(st.lam.hi) + 1e-37f;
-        if (n_new >= (1ll << 24)) st.band = INFINITY;  // n not exact in a float: FP64 decides
-    }
+__device__ __forceinline__ void condat_lam_next(CondatState& nx, const CondatState& st, const CondatOp& op) {
+    nx.eS = st.S;
+    nx.ey = op.y;
+    nx.en = st.nJ + 1;
+    const df num = df_add(st.rmS, df_neg(op.yd));
+    nx.lam = df_mul(num, st.inv);
+    const float scale = 9.1e-13f * (st.ab + fabsf(op.yd.hi)) + 2.0f * st.sderr;
+    nx.band = __fmul_ru(scale, st.r0u) + 9.1e-13f * fabsf(nx.lam.hi) + 1e-37f;
+    if (st.big) nx.band = INFINITY;  // n not exact in a float: FP64 decides
+    condat_bounds<L1>(nx);
+}
+// lambda = r - y (a restart with J = {y})
+template <bool L1>
+__device__ __forceinline__ void condat_lam_restart(CondatState& st, const CondatOp& op) {
+    st.eS = 0.0;
+    st.ey = op.y;
+    st.en = 0;
+    st.lam = op.rmy;
+    st.band = op.rb + 1e-37f;
     condat_bounds<L1>(st);
 }
 
@@ -278,15 +342,14 @@ __device__ __forceinline__ bool condat_gt(double v, const CondatState& st, doubl
 }
 
 // the restart test of Alg. 2: accept y (J <- J u {y}) iff lambda_{J u {y}} < r - y
-__device__ __forceinline__ bool condat_accepts(const CondatState& nx, double r, df rd, double y, df yd) {
-    if (nx.dfok && nx.sdok && df_in_range(y, false)) {
-        const df rmy = df_add(rd, df_neg(yd));
-        const df d = df_add(nx.lam, df_neg(rmy));
-        const float bd = nx.band + 2.8e-14f * (fabsf(rd.hi) + fabsf(yd.hi));
+__device__ __forceinline__ bool condat_accepts(const CondatState& nx, double r, const CondatOp& op) {
+    if (nx.dfok && nx.sdok && op.inr) {
+        const df d = df_add(nx.lam, df_neg(op.rmy));
+        const float bd = nx.band + op.rb;
         if (d.hi < -bd) return true;
         if (d.hi > bd) return false;
     }
-    return condat_exact_accepts(nx.eS, nx.ey, nx.en, r, y);  // rare: exact FP64
+    return condat_exact_accepts(nx.eS, nx.ey, nx.en, r, op.y);  // rare: exact FP64
 }
 
 __device__ __forceinline__ void condat_record(CondatState& st, double v) {
@@ -294,54 +357,62 @@ __device__ __forceinline__ void condat_record(CondatState& st, double v) {
     st.cnt++;
 }
 
+// J <- {y} (the first element of the chunk, or a restart)
+template <bool L1>
+__device__ __forceinline__ void condat_start_j(CondatState& st, df rd, const CondatOp& op) {
+    st.S = op.y;
+    st.Sd = op.yd;
+    st.sderr = 1.5e-14f * fabsf(op.yd.hi);
+    st.sdok = op.inr;
+    st.nJ = 1;
+    condat_lam_restart<L1>(st, op);
+    st.jt_end = st.cnt;
+}
+// J <- J u {y} with lambda_{J u {y}} already in nx
+__device__ __forceinline__ void condat_join(CondatState& st, const CondatState& nx, const CondatOp& op) {
+    st.lam = nx.lam;
+    st.band = nx.band;
+    st.eS = nx.eS;
+    st.ey = nx.ey;
+    st.en = nx.en;
+    st.clo = nx.clo;
+    st.chi = nx.chi;
+    st.glo = nx.glo;
+    st.ghi = nx.ghi;
+    st.S += op.y;
+    st.Sd = df_add(st.Sd, op.yd);
+    st.sderr += 2.8e-14f * (fabsf(st.Sd.hi) + fabsf(op.yd.hi));
+    st.sdok = st.sdok && op.inr;
+    st.nJ += 1;
+}
+
 // one element taken by the first loop of Alg. 2 (J started): add it or restart with it
 template <bool L1>
-__device__ __forceinline__ void condat_take(CondatState& st, double r, df rd, double y, int64_t e) {
-    const df yd = split_f64(y);
+__device__ __forceinline__ void condat_take(CondatState& st, double r, df rd, const CondatOp& op, int64_t e) {
     CondatState nx = st;
-    condat_lam<L1>(nx, r, rd, st.S, st.Sd, y, yd, st.nJ + 1, false);
-    if (condat_accepts(nx, r, rd, y, yd)) {
-        st.lam = nx.lam;
-        st.band = nx.band;
-        st.eS = nx.eS;
-        st.ey = nx.ey;
-        st.en = nx.en;
-        st.clo = nx.clo;
-        st.chi = nx.chi;
-        st.glo = nx.glo;
-        st.ghi = nx.ghi;
-        st.S += y;
-        st.Sd = df_add(st.Sd, yd);
-        st.sderr += 2.8e-14f * (fabsf(st.Sd.hi) + fabsf(yd.hi));
-        st.sdok = st.sdok && df_in_range(y, false);
-        st.nJ += 1;
+    condat_lam_next<L1>(nx, st, op);
+    if (condat_accepts(nx, r, op)) {
+        condat_join(st, nx, op);
     } else {  // restart: J~ <- J~ u J, J <- {j}
         st.rs = e;
-        st.S = y;
-        st.Sd = yd;
-        st.sderr = 1.5e-14f * fabsf(yd.hi);
-        st.sdok = df_in_range(y, false);
-        st.nJ = 1;
-        condat_lam<L1>(st, r, rd, 0.0, yd, y, yd, 1, true);
-        st.jt_end = st.cnt;
+        condat_start_j<L1>(st, rd, op);
     }
-    condat_record(st, y);
+    condat_record(st, op.y);
+    condat_prep(st, rd);
 }
 
 // the final loop of Alg. 2: J <- J u {y} (no restart test)
 template <bool L1>
 __device__ __forceinline__ void condat_add(CondatState& st, double r, df rd, double y) {
-    const df yd = split_f64(y);
-    condat_lam<L1>(st, r, rd, st.S, st.Sd, y, yd, st.nJ + 1, false);
-    st.S += y;
-    st.Sd = df_add(st.Sd, yd);
-    st.sderr += 2.8e-14f * (fabsf(st.Sd.hi) + fabsf(yd.hi));
-    st.sdok = st.sdok && df_in_range(y, false);
-    st.nJ += 1;
+    const CondatOp op = condat_op(y, rd);
+    CondatState nx = st;
+    condat_lam_next<L1>(nx, st, op);
+    condat_join(st, nx, op);
+    condat_prep(st, rd);
 }
 
 // the block filter's threshold: a float at or below c(lambda) - band (a superset of the
-// elements the scan can accept), as a float (FP32 data) and as double bits (FP64 data)
+// elements the scan can accept), as a float (FP32 data); FP64 data take st.glo
 __device__ __forceinline__ float condat_filter_rd(const CondatState& st) { return st.clo; }
 
 // Warp 0: the first loop of Alg. 2 over one group of 32 vectors in index order (lane, j);
@@ -372,17 +443,11 @@ __device__ __forceinline__ void condat_slab(const T (&vals)[VecOf<T>::V], const 
 #pragma unroll
         for (int j = V - 1; j >= 0; j--)
             if ((mo[j] >> L0) & 1u) j0 = j;
-        const double y0 = __shfl_sync(0xffffffffu, pick(av, j0), L0);
-        const df y0d = split_f64(y0);
-        st.S = y0;
-        st.Sd = y0d;
-        st.sderr = 1.5e-14f * fabsf(y0d.hi);
-        st.sdok = df_in_range(y0, false);
-        st.nJ = 1;
+        const CondatOp o0 = condat_op(__shfl_sync(0xffffffffu, pick(av, j0), L0), rd);
         st.rs = __shfl_sync(0xffffffffu, eidx0, L0) + j0;
-        condat_lam<L1>(st, r, rd, 0.0, y0d, y0, y0d, 1, true);
-        st.jt_end = st.cnt;
-        condat_record(st, y0);
+        condat_start_j<L1>(st, rd, o0);
+        condat_record(st, o0.y);
+        condat_prep(st, rd);
 #pragma unroll
         for (int j = 0; j < V; j++) {
             const bool after = (lane > L0) || (lane == L0 && j > j0);
@@ -408,7 +473,7 @@ __device__ __forceinline__ void condat_slab(const T (&vals)[VecOf<T>::V], const 
             if ((m[j] >> Lf) & 1u) jf = j;
         const double yv = __shfl_sync(0xffffffffu, pick(av, jf), Lf);
         const int64_t e = __shfl_sync(0xffffffffu, eidx0, Lf) + jf;
-        condat_take<L1>(st, r, rd, yv, e);
+        condat_take<L1>(st, r, rd, condat_op(yv, rd), e);
 #pragma unroll
         for (int j = 0; j < V; j++) {
             const bool after = (lane > Lf) || (lane == Lf && j > jf);
@@ -492,20 +557,98 @@ __device__ __forceinline__ void tile_vec(const T* __restrict__ y, const Span& sp
     }
 }
 
+// The block filter of one tile against the published threshold (tb: the exact 64-bit
+// test of FP64 data; trd: FP32 data): the ballots of the passing elements go to s.msk, and
+// the NaN check of the data rides along into sacc.bad.  Returns whether this thread's elements
+// passed.
+template <typename T, bool L1>
+__device__ __forceinline__ bool condat_filter_exact(const T* __restrict__ y, const T* __restrict__ xb,
+                                                    const Span& sp, bool aligned, const T* stage, bool staged,
+                                                    int64_t c, int64_t sb0, int64_t sb1, CondatShared& s,
+                                                    SumAcc& sacc) {
+    constexpr int V = VecOf<T>::V;
+    constexpr int TT = condat_tile<T>();
+    constexpr int KC = TT / V / NT;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const GtThreshold g{s.tb, (s.tb >> 63) != 0ull};
+    const float rd = s.trd;
+    bool anyp = false;
+#pragma unroll
+    for (int k = 0; k < KC; k++) {
+        const int ql = k * NT + (int)threadIdx.x;
+        T v[V];
+        bool ok[V];
+        tile_vec<T>(y, sp, stage, staged, c, ql, sb0, sb1, v, ok);
+#pragma unroll
+        for (int j = 0; j < V; j++) {
+            if constexpr (sizeof(T) == 8) sacc.bad |= ok[j] && u64_is_nan(bits_of((double)v[j]));
+            else sacc.bad |= ok[j] && (v[j] != v[j]);
+        }
+        support_mask<T, L1>(xb, sp, c * (TT / V) + ql, aligned, ok);
+#pragma unroll
+        for (int j = 0; j < V; j++) {
+            const bool p = ok[j] && condat_test<T, L1>(v[j], g, rd);
+            const unsigned bal = __ballot_sync(0xffffffffu, p);
+            if (lane == 0) s.msk[wid][k * V + j] = bal;
+            anyp |= p;
+        }
+    }
+    return anyp;
+}
+
+// A cheaper test of one vector of a tile in the stage: whether it holds an element that may
+// pass the exact filter.  FP64 data: the high words alone (y > c implies hi(y) >= hi(c) as
+// signed words for c >= 0, hi(y) <= hi(c) as unsigned words for c < 0), and a NaN always
+// passes (so that the exact filter, which checks for NaN, sees it); FP32 data: the unordered
+// comparison (a NaN passes).  A superset of the exact filter, so a tile it rejects has no
+// element the scan can accept.
+template <typename T, bool L1>
+__device__ __forceinline__ bool condat_prefilter(const T* stage, const T* __restrict__ xb, const Span& sp,
+                                                 int64_t c, int ql, bool aligned, unsigned long long tb, float trd) {
+    constexpr int V = VecOf<T>::V;
+    constexpr int TT = condat_tile<T>();
+    const uint4 w = reinterpret_cast<const uint4*>(stage)[ql];
+    bool ok[V];
+#pragma unroll
+    for (int j = 0; j < V; j++) ok[j] = true;
+    support_mask<T, L1>(xb, sp, c * (TT / V) + ql, aligned, ok);
+    bool p = false;
+    if constexpr (sizeof(T) == 8) {
+        const unsigned th = (unsigned)(tb >> 32);
+        const bool tneg = (tb >> 63) != 0ull;
+        const unsigned h[2] = {w.y, w.w};
+#pragma unroll
+        for (int j = 0; j < 2; j++) {
+            bool q;
+            if (L1) q = (int)(h[j] & 0x7FFFFFFFu) >= (int)th;  // |y|: a NaN has the largest word
+            else if (!tneg) q = ((int)h[j] >= (int)th) | (h[j] >= 0xFFF00000u);
+            else q = (h[j] <= th) | (h[j] >= 0xFFF00000u);
+            p |= ok[j] && q;
+        }
+    } else {
+        const unsigned u[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            float f = __uint_as_float(u[j]);
+            if (L1) f = fabsf(f);
+            p |= ok[j] && !(f <= trd);
+        }
+    }
+    return p;
+}
+
 // Alg. 2 on the chunk of block `member` of `nchunk` (blocks with member >= nchunk have none).
-// Called by all threads; (S_out, nJ_out) = (sum_J y, |J|) valid in thread 0.  With SUM the
-// same pass also accumulates the sum and maximum of y (l1: |y|) into sacc (the chunks of all
-// blocks cover the span once; blocks without a chunk add nothing).
+// Called by all threads; (S_out, nJ_out) = (sum_J y, |J|) valid in thread 0; the NaN check
+// of the data rides on this pass, into sacc.bad.
 //
-// Per tile: every thread tests its KC vectors against the published threshold and the warps
-// store their ballots; a block vote skips the rest of the tile when nothing passed (the usual
-// case once lambda is close); otherwise warp 0 walks the passing elements in index order
+// Per tile: every thread tests its KC vectors (interior tiles: first the cheap prefilter of the
+// whole block, the usual verdict being that nothing can pass); when something may pass, the
+// exact filter stores the warps' ballots and warp 0 walks the passing elements in index order
 // (k, warp, lane, j), re-reading their values from the stage, with the exact scan.
-template <typename T, bool L1, bool SUM>
+template <typename T, bool L1>
 __device__ void condat_block(const T* __restrict__ y, const T* __restrict__ xb, const Span& sp, bool aligned,
                              double r, int member, int nchunk, T* smem, uint64_t* bars, unsigned& parity, int* err,
                              unsigned long long limit_ns, SumAcc& sacc, double& S_out, long long& nJ_out) {
-    // (without SUM the NaN check of the data rides on this pass, into sacc.bad)
     constexpr int V = VecOf<T>::V;
     constexpr int TT = condat_tile<T>();
     constexpr int KC = TT / V / NT;
@@ -513,29 +656,10 @@ __device__ void condat_block(const T* __restrict__ y, const T* __restrict__ xb, 
     __shared__ CondatShared s;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     CondatState st;
-    st.S = 0.0;
-    st.Sd = df{0.0f, 0.0f};
-    st.nJ = 0;
-    st.rs = -1;
-    st.lam = df{0.0f, 0.0f};
-    st.band = 0.0f;
-    st.sderr = 0.0f;
-    st.sdok = true;
-    st.dfok = df_in_range(r, false) && r != 0.0;
-    st.eS = st.ey = 0.0;
-    st.en = 0;
-    st.clo = -INFINITY;
-    st.chi = INFINITY;
-    st.glo = make_gt(-INFINITY);
-    st.ghi = make_gt(INFINITY);
-    st.list = s.list;
-    st.cnt = 0;
-    st.jt_end = 0;
+    condat_init(st, r, s.list);
     const df rdf = split_f64(r);
     if (threadIdx.x == 0) {  // before J starts every element passes the filter
-        const GtThreshold g0 = make_gt(-INFINITY);
-        s.tb = g0.bits;
-        s.tneg = 1;
+        s.tb = make_gt(-INFINITY).bits;  // the sign bit of the pattern is the sign of the threshold
         s.trd = -INFINITY;
     }
     TileRing<T, 1, TT> ring;
@@ -548,84 +672,143 @@ __device__ void condat_block(const T* __restrict__ y, const T* __restrict__ xb, 
     if (staged && threadIdx.x == 0)
         for (int k = 0; k < kCondatStages - 1; k++)
             if (k < ring.count) ring.issue(ring.tile(k, false), k, src);
-    for (int64_t i = 0; i < ring.count; i++) {
-        const int stg = (int)(i % kCondatStages);
-        if (staged) {
-            if (threadIdx.x == 0 && i + kCondatStages - 1 < ring.count)
-                ring.issue(ring.tile(i + kCondatStages - 1, false), (int)((i + kCondatStages - 1) % kCondatStages), src);
-            mbar_wait(&ring.bar[stg], (ring.parity >> stg) & 1u, err, limit_ns, CQK_TIMEOUT);
-            ring.parity ^= 1u << stg;
-        }
-        const int64_t c = ring.tile(i, false);
-        const int64_t sb0 = staged ? ring.b0(c) : 0, sb1 = staged ? ring.b1(c) : 0;
-        const T* stage = ring.stage(stg, 0);
-        const GtThreshold g{s.tb, s.tneg != 0};
-        const float rd = s.trd;
-        bool anyp = false;
+    if (staged) {
+        // Pipelined: warps 1..NWARP-1 filter the tiles as they land (up to kCondatStages - 1
+        // tiles ahead of the scan) and signal the stage's second mbarrier; warp 0 runs the scan
+        // over the groups with survivors, then refills the stage it is done with.  The
+        // filters read the threshold the scan last published, which can only be lower than
+        // the scan's own (c(lambda) only grows during the first loop), so they pass a superset.
+        constexpr int NVEC = TT / V;  // vectors of a tile
+        constexpr int NG = NVEC / 32;  // groups of 32 vectors, in index order
+        constexpr int NP = NWARP - 1;  // filtering warps; group g belongs to warp 1 + g % NP
+        constexpr int KP = (NG + NP - 1) / NP;
+        static_assert(NG == 32 && KP * V <= 32, "one lane per group");
+        uint64_t* fullb = bars + kCondatStages;
+        if (wid > 0) {
+            const int pw = wid - 1;
+            for (int64_t i = 0; i < ring.count; i++) {
+                const int stg = (int)(i % kCondatStages);
+                mbar_wait(&ring.bar[stg], (ring.parity >> stg) & 1u, err, limit_ns, CQK_TIMEOUT);
+                ring.parity ^= 1u << stg;
+                const int64_t c = ring.tile(i, false);
+                const int64_t sb0 = ring.b0(c), sb1 = ring.b1(c);
+                const T* stage = ring.stage(stg, 0);
+                const unsigned long long tb = *reinterpret_cast<volatile unsigned long long*>(&s.tb);
+                const float trd = *reinterpret_cast<volatile float*>(&s.trd);
+                bool may = !(sb0 == c * TT && sb1 == (c + 1) * TT);  // a partial tile: exact filter
+                if (!may) {
 #pragma unroll
-        for (int k = 0; k < KC; k++) {
-            const int ql = k * NT + (int)threadIdx.x;
-            T v[V];
-            bool ok[V];
-            tile_vec<T>(y, sp, stage, staged, c, ql, sb0, sb1, v, ok);
-            if constexpr (SUM) {
-                unsigned widem = 0;
-#pragma unroll
-                for (int j = 0; j < V; j++)
-                    if (ok[j] && sum_elem<T, L1>(sacc, v[j])) widem |= 1u << j;
-                for (unsigned m = widem; m; m &= m - 1) sum_wide<T, L1>(sacc, pick(v, __ffs(m) - 1));
-            } else {
-#pragma unroll
-                for (int j = 0; j < V; j++) {
-                    if constexpr (sizeof(T) == 8) sacc.bad |= ok[j] && u64_is_nan(bits_of((double)v[j]));
-                    else sacc.bad |= ok[j] && (v[j] != v[j]);
+                    for (int k = 0; k < KP; k++) {
+                        const int gi = k * NP + pw;
+                        if (gi < NG) may |= condat_prefilter<T, L1>(stage, xb, sp, c, gi * 32 + lane, aligned, tb, trd);
+                    }
                 }
+                unsigned* mk = s.pmsk[stg];
+                if (__any_sync(0xffffffffu, may)) {
+                    const GtThreshold g{tb, (tb >> 63) != 0ull};
+#pragma unroll
+                    for (int k = 0; k < KP; k++) {
+                        const int gi = k * NP + pw;
+                        if (gi >= NG) break;
+                        const int ql = gi * 32 + lane;
+                        T v[V];
+                        bool ok[V];
+                        tile_vec<T>(y, sp, stage, true, c, ql, sb0, sb1, v, ok);
+#pragma unroll
+                        for (int j = 0; j < V; j++) {
+                            if constexpr (sizeof(T) == 8) sacc.bad |= ok[j] && u64_is_nan(bits_of((double)v[j]));
+                            else sacc.bad |= ok[j] && (v[j] != v[j]);
+                        }
+                        support_mask<T, L1>(xb, sp, c * NVEC + ql, aligned, ok);
+#pragma unroll
+                        for (int j = 0; j < V; j++) {
+                            const unsigned bal = __ballot_sync(0xffffffffu, ok[j] && condat_test<T, L1>(v[j], g, trd));
+                            if (lane == 0) mk[gi * V + j] = bal;
+                        }
+                    }
+                } else if (lane == 0) {
+#pragma unroll
+                    for (int k = 0; k < KP; k++) {
+                        const int gi = k * NP + pw;
+                        if (gi < NG)
+#pragma unroll
+                            for (int j = 0; j < V; j++) mk[gi * V + j] = 0u;
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&fullb[stg]);  // release: the ballots of this warp
             }
-            support_mask<T, L1>(xb, sp, c * (TT / V) + ql, aligned, ok);
+        } else {
+            for (int64_t i = 0; i < ring.count; i++) {
+                const int stg = (int)(i % kCondatStages);
+                // the stage of tile i - 1 is free: its filters signalled and its scan is done
+                if (lane == 0 && i + kCondatStages - 1 < ring.count)
+                    ring.issue(ring.tile(i + kCondatStages - 1, false), (int)((i + kCondatStages - 1) % kCondatStages),
+                               src);
+                __syncwarp();
+                mbar_wait(&fullb[stg], (ring.parity >> stg) & 1u, err, limit_ns, CQK_TIMEOUT);
+                mbar_wait(&ring.bar[stg], (ring.parity >> stg) & 1u, err, limit_ns, CQK_TIMEOUT);
+                ring.parity ^= 1u << stg;
+                const unsigned* mk = s.pmsk[stg];
+                unsigned gany = 0;
 #pragma unroll
-            for (int j = 0; j < V; j++) {
-                const bool p = ok[j] && condat_test<T, L1>(v[j], g, rd);
-                const unsigned bal = __ballot_sync(0xffffffffu, p);
-                if (lane == 0) s.msk[wid][k * V + j] = bal;
-                anyp |= p;
-            }
-        }
-        if constexpr (SUM && sizeof(T) == 8) sacc.fold();
-        // a tile with no survivor needs no scan (the vote is also the barrier after which the
-        // stage may be refilled and the ballots rewritten)
-        if (!__syncthreads_or(anyp)) continue;
-        if (wid == 0) {
-            // lane g looks at group g = (k, w) of 32 vectors; the groups are visited in order
-            static_assert(KC * NWARP <= 32, "one lane per group");
-            unsigned gany = 0;
-            if (lane < KC * NWARP)
-#pragma unroll
-                for (int j = 0; j < V; j++) gany |= s.msk[lane % NWARP][(lane / NWARP) * V + j];
-            for (unsigned groups = __ballot_sync(0xffffffffu, gany != 0u); groups; groups &= groups - 1) {
-                const int gi = __ffs(groups) - 1;
-                const int k = gi / NWARP, w = gi % NWARP;
-                unsigned mj[V];
-#pragma unroll
-                for (int j = 0; j < V; j++) mj[j] = s.msk[w][k * V + j];
-                {
-                    const int ql = k * NT + w * 32 + lane;
+                for (int j = 0; j < V; j++) gany |= mk[lane * V + j];
+                const unsigned groups = __ballot_sync(0xffffffffu, gany != 0u);
+                if (!groups) continue;
+                const int64_t c = ring.tile(i, false);
+                const int64_t sb0 = ring.b0(c), sb1 = ring.b1(c);
+                const T* stage = ring.stage(stg, 0);
+                for (unsigned gs = groups; gs; gs &= gs - 1) {
+                    const int gi = __ffs(gs) - 1;
+                    const int ql = gi * 32 + lane;
                     T v[V];
                     bool ok[V];
-                    tile_vec<T>(y, sp, stage, staged, c, ql, sb0, sb1, v, ok);
+                    tile_vec<T>(y, sp, stage, true, c, ql, sb0, sb1, v, ok);
 #pragma unroll
-                    for (int j = 0; j < V; j++) ok[j] = ((mj[j] >> lane) & 1u) != 0u;
-                    condat_slab<T, L1>(v, ok, (c * (TT / V) + ql) * V, r, rdf, st);
+                    for (int j = 0; j < V; j++) ok[j] = ((mk[gi * V + j] >> lane) & 1u) != 0u;
+                    condat_slab<T, L1>(v, ok, (c * NVEC + ql) * V, r, rdf, st);
                 }
-            }
-            if (lane == 0 && st.nJ > 0) {
-                const float fr = condat_filter_rd(st);
-                const GtThreshold gf = st.glo;
-                s.tb = gf.bits;
-                s.tneg = gf.neg ? 1 : 0;
-                s.trd = fr;
+                if (lane == 0 && st.nJ > 0) {
+                    *reinterpret_cast<volatile float*>(&s.trd) = condat_filter_rd(st);
+                    *reinterpret_cast<volatile unsigned long long*>(&s.tb) = st.glo.bits;
+                }
             }
         }
         __syncthreads();
+    } else {
+        // data not 16-byte aligned: no staging; per tile the exact filter of the whole block,
+        // then warp 0 scans the survivors while the block waits
+        for (int64_t i = 0; i < ring.count; i++) {
+            const int64_t c = ring.tile(i, false);
+            const bool anyp = condat_filter_exact<T, L1>(y, xb, sp, aligned, nullptr, false, c, 0, 0, s, sacc);
+            // a tile with no survivor needs no scan (the vote is also the barrier after which the
+            // ballots may be rewritten)
+            if (!__syncthreads_or(anyp)) continue;
+            if (wid == 0) {
+                // lane g looks at group g = (k, w) of 32 vectors; the groups are visited in order
+                static_assert(KC * NWARP <= 32, "one lane per group");
+                unsigned gany = 0;
+                if (lane < KC * NWARP)
+#pragma unroll
+                    for (int j = 0; j < V; j++) gany |= s.msk[lane % NWARP][(lane / NWARP) * V + j];
+                for (unsigned groups = __ballot_sync(0xffffffffu, gany != 0u); groups; groups &= groups - 1) {
+                    const int gi = __ffs(groups) - 1;
+                    const int k = gi / NWARP, w = gi % NWARP;
+                    const int ql = k * NT + w * 32 + lane;
+                    T v[V];
+                    bool ok[V];
+                    tile_vec<T>(y, sp, nullptr, false, c, ql, 0, 0, v, ok);
+#pragma unroll
+                    for (int j = 0; j < V; j++) ok[j] = ((s.msk[w][k * V + j] >> lane) & 1u) != 0u;
+                    condat_slab<T, L1>(v, ok, (c * (TT / V) + ql) * V, r, rdf, st);
+                }
+                if (lane == 0 && st.nJ > 0) {
+                    s.tb = st.glo.bits;
+                    s.trd = condat_filter_rd(st);
+                }
+            }
+            __syncthreads();
+        }
     }
     parity = ring.parity;
     // final loop of Alg. 2 over J~ (warp 0)
@@ -821,44 +1004,28 @@ __device__ __forceinline__ bool alg4_update(Alg4State& a, int k, double lam, dou
 }
 
 // per-block totals of a pass (fixed order) -> partials slot `par`, and into blk (thread 0);
-// a one-block group (solo) keeps them in registers only
+// a one-block group (solo) keeps them in registers only.  The counts are summed as doubles
+// (integers below 2^53, so exactly).
 __device__ __forceinline__ void write_pass_partials(const Grp& gp, int par, double acc, unsigned cm, unsigned ct,
-                                                    double* sh_d, unsigned* sh_u, bool solo, double (&blk)[3]) {
+                                                    double (*sh)[NWARP], bool solo, double (&blk)[3]) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     acc = warp_sum(acc);
     cm = __reduce_add_sync(0xffffffffu, cm);
     ct = __reduce_add_sync(0xffffffffu, ct);
     if (lane == 0) {
-        sh_d[wid] = acc;
-        sh_u[wid] = cm;
-        sh_u[NWARP + wid] = ct;
+        sh[0][wid] = acc;
+        sh[1][wid] = (double)cm;
+        sh[2][wid] = (double)cm + (double)ct;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        unsigned long long c0 = 0, c1 = 0;
-        for (int w = 0; w < NWARP; w++) {
-            t += sh_d[w];
-            c0 += sh_u[w];
-            c1 += sh_u[NWARP + w];
-        }
-        const double pv[3] = {t, (double)c0, (double)(c0 + c1)};
+    if (threadIdx.x < 32) {
+        double pv[3];
+        warp0_combine<3>(sh, -1, pv);
         if (!solo) write_partials<3>(gp.part, gp.member, gp.g, par, pv);
         blk[0] = pv[0];
         blk[1] = pv[1];
         blk[2] = pv[2];
     }
-}
-
-// grid totals of slot `par` by warp 0 (fixed order); valid in lane 0 of warp 0
-__device__ __forceinline__ void warp0_grid_sums(const double* part, int G, int par, double (&out)[3]) {
-    const int lane = threadIdx.x & 31;
-    double v[3] = {0.0, 0.0, 0.0};
-    for (int bI = lane; bI < G; bI += 32)
-#pragma unroll
-        for (int q = 0; q < 3; q++) v[q] += ld_cg(part + ((size_t)par * kPartialQ + q) * G + bI);
-#pragma unroll
-    for (int q = 0; q < 3; q++) out[q] = warp_sum(v[q]);
 }
 
 // the final pass: x_i = max{0, y_i + lambda} (l1: sgn(y_i) max{0, |y_i| + lambda}; copy: x = y),
@@ -994,8 +1161,6 @@ __device__ __forceinline__ void simplex_solve(const SimplexArgs& A, const Grp& g
     constexpr int V = VecOf<T>::V;
     __shared__ double sh[kPartialQ][NWARP];
     __shared__ double bc[kPartialQ];
-    __shared__ double sh_d[NWARP];
-    __shared__ unsigned sh_u[2 * NWARP];
     // loop state written by thread 0 after each update, read by all threads
     __shared__ double s_lam, s_final;
     __shared__ int s_done, s_bad, s_redo;
@@ -1035,7 +1200,7 @@ __device__ __forceinline__ void simplex_solve(const SimplexArgs& A, const Grp& g
         if (condat) {
             double Sw = 0.0;
             long long nJw = 0;
-            condat_block<T, L1, false>(y, warm ? static_cast<const T*>(A.xbar) : nullptr, sp, aligned, r, gp.member,
+            condat_block<T, L1>(y, warm ? static_cast<const T*>(A.xbar) : nullptr, sp, aligned, r, gp.member,
                                        nchunk, smem, bars, ring_parity, &gp.hdr->error, A.limit_ns, sacc, Sw, nJw);
             q[1] = threadIdx.x == 0 ? Sw : 0.0;
             q[2] = threadIdx.x == 0 ? (double)nJw : 0.0;
@@ -1055,15 +1220,9 @@ __device__ __forceinline__ void simplex_solve(const SimplexArgs& A, const Grp& g
             if (badw && A.validate) atomicOr(&gp.hdr->flags, kFlagBadInput);
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
-            double t0 = 0, t1 = 0, t2 = 0, t3 = -INFINITY;
-            for (int w = 0; w < NWARP; w++) {
-                t0 += sh[0][w];
-                t1 += sh[1][w];
-                t2 += sh[2][w];
-                t3 = fmax(t3, sh[3][w]);
-            }
-            const double pv[4] = {t0, t1, t2, t3};
+        if (threadIdx.x < 32) {
+            double pv[4];
+            warp0_combine<4>(sh, 3, pv);
             write_partials<4>(gp.part, gp.member, G, 0, pv);
         }
         __syncthreads();
@@ -1158,7 +1317,7 @@ __device__ __forceinline__ void simplex_solve(const SimplexArgs& A, const Grp& g
             // already holds the totals (bit-identical to the one-partial grid sum)
             const bool solo = G == 1 && !A.fault_inject;
             double blk[3];
-            write_pass_partials(gp, par, pa.acc64, pa.cm, pa.ct, sh_d, sh_u, solo, blk);
+            write_pass_partials(gp, par, pa.acc64, pa.cm, pa.ct, sh, solo, blk);
             if (!solo) {
                 if (!group_barrier(gp, bar_target, A.limit_ns, A.fault_inject != 0)) {
                     if (threadIdx.x == 0) A.info->status = CQK_TIMEOUT;
@@ -1166,9 +1325,9 @@ __device__ __forceinline__ void simplex_solve(const SimplexArgs& A, const Grp& g
                 }
                 bar_target += (unsigned)G;
             }
-            if (threadIdx.x < 32) {
-                double red[3] = {blk[0], blk[1], blk[2]};
-                if (!solo) warp0_grid_sums(gp.part, G, par, red);
+            double red[3] = {blk[0], blk[1], blk[2]};
+            if (!solo) grid_totals_warp0<3>(gp.part, G, par, -1, red, sh);
+            {
                 if (threadIdx.x == 0) {
                     int done = 0, bad = 0, redo = 0;
                     double next = lam;
@@ -1277,24 +1436,7 @@ __device__ void simplex_warp_solve(const SimplexArgs& A, const Span& sp, double*
         passes++;
     } else {
         CondatState st;
-        st.S = 0.0;
-        st.Sd = df{0.0f, 0.0f};
-        st.nJ = 0;
-        st.rs = -1;
-        st.lam = df{0.0f, 0.0f};
-        st.band = 0.0f;
-        st.sderr = 0.0f;
-        st.sdok = true;
-        st.dfok = df_in_range(r, false) && r != 0.0;
-        st.eS = st.ey = 0.0;
-        st.en = 0;
-        st.clo = -INFINITY;
-        st.chi = INFINITY;
-        st.glo = make_gt(-INFINITY);
-        st.ghi = make_gt(INFINITY);
-        st.list = list;
-        st.cnt = 0;
-        st.jt_end = 0;
+        condat_init(st, r, list);
         const df rdf = split_f64(r);
         for (int64_t q0 = (qlo / 32) * 32; q0 < qhi; q0 += 32) {
             const int64_t q = q0 + lane;
@@ -1437,7 +1579,10 @@ __device__ void simplex_warp_solve(const SimplexArgs& A, const Span& sp, double*
 // their mbarriers, initialised once per block
 __device__ __forceinline__ void init_condat_bars(uint64_t* bars) {
     if (threadIdx.x == 0) {
-        for (int k = 0; k < kCondatStages; k++) mbar_init(&bars[k], 1);
+        for (int k = 0; k < kCondatStages; k++) {
+            mbar_init(&bars[k], 1);                           // the stage's bulk copy
+            mbar_init(&bars[kCondatStages + k], NWARP - 1);  // the filtering warps (pipelined Alg. 2)
+        }
         fence_barrier_init();
     }
     __syncthreads();
@@ -1446,7 +1591,7 @@ __device__ __forceinline__ void init_condat_bars(uint64_t* bars) {
 template <typename T, bool L1>
 __global__ void __launch_bounds__(NT, 2) simplex_kernel(SimplexArgs A) {
     extern __shared__ __align__(128) unsigned char dyn_smem[];
-    __shared__ uint64_t bars[kCondatStages];
+    __shared__ uint64_t bars[2 * kCondatStages];
     unsigned parity = 0;
     init_condat_bars(bars);
     Grp gp;
@@ -1473,7 +1618,7 @@ struct SimplexBatchArgs {
 template <typename T, bool L1>
 __global__ void __launch_bounds__(NT, 2) simplex_batched_kernel(SimplexBatchArgs P) {
     extern __shared__ __align__(128) unsigned char dyn_smem[];
-    __shared__ uint64_t bars[kCondatStages];
+    __shared__ uint64_t bars[2 * kCondatStages];
     unsigned parity = 0;
     init_condat_bars(bars);
     while (true) {
