@@ -287,8 +287,8 @@ def run_ours(args, world, rank, local):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": "simplex + l1-ball projection, n=1e8, FP64, y~N(0,1), r=1, Condat start "
-                               "(Alg. 2 per warp chunk) then Alg. 4",
+        "config": {"workload": f"simplex + l1-ball projection, n={n}, FP64, y~N(0,1), r=1, Condat start "
+                               "(Alg. 2 per block chunk) then Alg. 4",
                    "n": n, "init": "condat", "projections_per_step": 2, "iters_simplex": i1.iters,
                    "iters_l1": i2.iters, "passes_simplex": i1.passes, "passes_l1": i2.passes,
                    "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (800 MB per vector)"},
