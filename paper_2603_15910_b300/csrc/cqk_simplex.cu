@@ -153,6 +153,7 @@ template <typename T>
 __host__ __device__ constexpr int condat_tile() { return 16384 / (int)sizeof(T); }  // elements per tile
 constexpr size_t kCondatSmem = (size_t)kCondatStages * 16384;                      // dynamic shared memory
 constexpr int kJList = 1024;  // accepted values kept for the final loop
+constexpr int kStartBit = 16;  // bit of the start barrier's phase in the ring parity word
 
 struct CondatShared {
     unsigned msk[NWARP][16];  // filter ballots of each warp, (k, j) -> bit lane
@@ -684,10 +685,14 @@ __device__ void condat_block(const T* __restrict__ y, const T* __restrict__ xb, 
         constexpr int KP = (NG + NP - 1) / NP;
         static_assert(NG == 32 && KP * V <= 32, "one lane per group");
         uint64_t* fullb = bars + kCondatStages;
+        uint64_t* startb = bars + 2 * kCondatStages;  // the scan is done with the first tile
         if (wid > 0) {
             const int pw = wid - 1;
             for (int64_t i = 0; i < ring.count; i++) {
                 const int stg = (int)(i % kCondatStages);
+                // before J starts every element passes: the filters wait for the threshold of the
+                // scan's first tile instead of passing whole tiles to it
+                if (i == 1) mbar_wait(startb, (ring.parity >> kStartBit) & 1u, err, limit_ns, CQK_TIMEOUT);
                 mbar_wait(&ring.bar[stg], (ring.parity >> stg) & 1u, err, limit_ns, CQK_TIMEOUT);
                 ring.parity ^= 1u << stg;
                 const int64_t c = ring.tile(i, false);
@@ -700,7 +705,8 @@ __device__ void condat_block(const T* __restrict__ y, const T* __restrict__ xb, 
 #pragma unroll
                     for (int k = 0; k < KP; k++) {
                         const int gi = k * NP + pw;
-                        if (gi < NG) may |= condat_prefilter<T, L1>(stage, xb, sp, c, gi * 32 + lane, aligned, tb, trd);
+                        if (gi < NG)
+                            may |= condat_prefilter<T, L1>(stage, xb, sp, c, gi * 32 + lane, aligned, tb, trd);
                     }
                 }
                 unsigned* mk = s.pmsk[stg];
@@ -754,7 +760,10 @@ __device__ void condat_block(const T* __restrict__ y, const T* __restrict__ xb, 
 #pragma unroll
                 for (int j = 0; j < V; j++) gany |= mk[lane * V + j];
                 const unsigned groups = __ballot_sync(0xffffffffu, gany != 0u);
-                if (!groups) continue;
+                if (!groups) {
+                    if (i == 0 && lane == 0) mbar_arrive(startb);
+                    continue;
+                }
                 const int64_t c = ring.tile(i, false);
                 const int64_t sb0 = ring.b0(c), sb1 = ring.b1(c);
                 const T* stage = ring.stage(stg, 0);
@@ -772,8 +781,13 @@ __device__ void condat_block(const T* __restrict__ y, const T* __restrict__ xb, 
                     *reinterpret_cast<volatile float*>(&s.trd) = condat_filter_rd(st);
                     *reinterpret_cast<volatile unsigned long long*>(&s.tb) = st.glo.bits;
                 }
+                if (i == 0) {
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(startb);  // release: the published threshold
+                }
             }
         }
+        if (ring.count > 0) ring.parity ^= 1u << kStartBit;  // (every thread: one phase per call)
         __syncthreads();
     } else {
         // data not 16-byte aligned: no staging; per tile the exact filter of the whole block,
@@ -1583,6 +1597,7 @@ __device__ __forceinline__ void init_condat_bars(uint64_t* bars) {
             mbar_init(&bars[k], 1);                           // the stage's bulk copy
             mbar_init(&bars[kCondatStages + k], NWARP - 1);  // the filtering warps (pipelined Alg. 2)
         }
+        mbar_init(&bars[2 * kCondatStages], 1);  // the scan's first tile (pipelined Alg. 2)
         fence_barrier_init();
     }
     __syncthreads();
@@ -1591,7 +1606,7 @@ __device__ __forceinline__ void init_condat_bars(uint64_t* bars) {
 template <typename T, bool L1>
 __global__ void __launch_bounds__(NT, 2) simplex_kernel(SimplexArgs A) {
     extern __shared__ __align__(128) unsigned char dyn_smem[];
-    __shared__ uint64_t bars[2 * kCondatStages];
+    __shared__ uint64_t bars[2 * kCondatStages + 1];
     unsigned parity = 0;
     init_condat_bars(bars);
     Grp gp;
@@ -1618,7 +1633,7 @@ struct SimplexBatchArgs {
 template <typename T, bool L1>
 __global__ void __launch_bounds__(NT, 2) simplex_batched_kernel(SimplexBatchArgs P) {
     extern __shared__ __align__(128) unsigned char dyn_smem[];
-    __shared__ uint64_t bars[2 * kCondatStages];
+    __shared__ uint64_t bars[2 * kCondatStages + 1];
     unsigned parity = 0;
     init_condat_bars(bars);
     while (true) {
