@@ -22,7 +22,8 @@
 namespace cqk {
 namespace {
 
-constexpr int kBwdU = 4;     // 16-byte vectors per array in flight per lane (projections: 2 arrays)
+constexpr int kBwdU = 4;      // 16-byte vectors per array in flight per lane (projections: g and x)
+constexpr int kBwdUNoX = 6;   // the simplex with the forward mask: g alone
 constexpr int kBwdUGen = 1;  // general: 6 arrays, and the register budget of the double-float map
 
 enum BwdKind { kBwdGeneral = 0, kBwdSimplex = 1, kBwdL1 = 2 };
@@ -168,11 +169,12 @@ __device__ __noinline__ void bwd_map_exact(double g, double x, double b, double 
     }
 }
 
-// one instance by one group (WARP: by one warp alone; gp.sp is the only field used)
-template <typename T, int KIND, bool WARP = false>
+// one instance by one group (WARP: by one warp alone; gp.sp is the only field used).  NOX: the
+// simplex with the forward mask, where F comes from the mask and x is not read.
+template <typename T, int KIND, bool NOX, bool WARP = false>
 __device__ __forceinline__ void bwd_instance(const BwdArgs& A, const Grp& gp, int64_t inst) {
     constexpr int V = VecOf<T>::V;
-    constexpr int U = KIND == kBwdGeneral ? kBwdUGen : kBwdU;
+    constexpr int U = KIND == kBwdGeneral ? kBwdUGen : (NOX ? kBwdUNoX : kBwdU);
     __shared__ double sh[kPartialQ][NWARP];
     __shared__ double bc[kPartialQ];
     const Span sp = gp.sp;
@@ -182,6 +184,7 @@ __device__ __forceinline__ void bwd_instance(const BwdArgs& A, const Grp& gp, in
     const double lam = KIND == kBwdGeneral ? inf->lambda : 0.0;
     const bool inside = KIND == kBwdL1 && inf->stop == CQK_STOP_INSIDE;
     const bool need_lu = KIND == kBwdGeneral && (!A.mask || A.gl || A.gu);
+    const void* xp = NOX ? nullptr : A.x;
     const WarpSweep sw = WARP ? WarpSweep::solo(span_qlo<V>(sp), span_qhi<V>(sp), U)
                               : WarpSweep(span_qlo<V>(sp), span_qhi<V>(sp), U, gp.member, gp.g);
 
@@ -203,7 +206,7 @@ __device__ __forceinline__ void bwd_instance(const BwdArgs& A, const Grp& gp, in
             for (int w = 0; w < U; w++) {
                 const int64_t q = base + w * 32 + lane;
                 load_vec<T>(static_cast<const T*>(A.g), sp, q, aligned, vg[w], ok[w]);
-                load_or<T>(A.x, sp, q, aligned, vx[w], ok[w], T(0));
+                load_or<T>(xp, sp, q, aligned, vx[w], ok[w], T(0));
                 if (KIND == kBwdGeneral) {
                     load_or<T>(A.b, sp, q, aligned, vb[w], ok[w], T(1));
                     load_or<T>(A.d, sp, q, aligned, vd[w], ok[w], T(1));
@@ -279,7 +282,7 @@ __device__ __forceinline__ void bwd_instance(const BwdArgs& A, const Grp& gp, in
         for (int w = 0; w < U; w++) {
             const int64_t q = base + w * 32 + lane;
             load_vec<T>(static_cast<const T*>(A.g), sp, q, aligned, vg[w], ok[w]);
-            load_or<T>(A.x, sp, q, aligned, vx[w], ok[w], T(0));
+            load_or<T>(xp, sp, q, aligned, vx[w], ok[w], T(0));
             if (KIND == kBwdGeneral) {
                 load_or<T>(A.b, sp, q, aligned, vb[w], ok[w], T(1));
                 load_or<T>(A.d, sp, q, aligned, vd[w], ok[w], T(1));
@@ -387,7 +390,7 @@ __device__ __forceinline__ void bwd_instance(const BwdArgs& A, const Grp& gp, in
     }
 }
 
-template <typename T, int KIND, bool BATCHED>
+template <typename T, int KIND, bool BATCHED, bool NOX>
 __global__ void __launch_bounds__(NT, 2) backward_kernel(BwdArgs A) {
     if constexpr (!BATCHED) {
         Grp gp;
@@ -396,7 +399,7 @@ __global__ void __launch_bounds__(NT, 2) backward_kernel(BwdArgs A) {
         gp.sp = Span{0, A.n};
         gp.hdr = A.hdr;
         gp.part = A.part;
-        bwd_instance<T, KIND>(A, gp, 0);
+        bwd_instance<T, KIND, NOX>(A, gp, 0);
         return;
     } else {
         while (true) {
@@ -417,7 +420,7 @@ __global__ void __launch_bounds__(NT, 2) backward_kernel(BwdArgs A) {
                             if (A.status) A.status[inst] = CQK_BAD_ARG;
                         }
                     } else {
-                        bwd_instance<T, KIND, true>(A, gw, inst);
+                        bwd_instance<T, KIND, NOX, true>(A, gw, inst);
                     }
                 }
                 continue;
@@ -431,14 +434,14 @@ __global__ void __launch_bounds__(NT, 2) backward_kernel(BwdArgs A) {
                 }
                 continue;
             }
-            bwd_instance<T, KIND>(A, gp, sl.inst);
+            bwd_instance<T, KIND, NOX>(A, gp, sl.inst);
         }
     }
 }
 
-template <typename T, int KIND>
+template <typename T, int KIND, bool NOX = false>
 const void* pick_kernel(bool batched) {
-    return batched ? (const void*)backward_kernel<T, KIND, true> : (const void*)backward_kernel<T, KIND, false>;
+    return batched ? (const void*)backward_kernel<T, KIND, true, NOX> : (const void*)backward_kernel<T, KIND, false, NOX>;
 }
 
 }  // namespace
@@ -472,13 +475,16 @@ int launch_backward(int kind, int64_t B, const int64_t* offsets, int64_t n, int 
     A.aligned = (all % 16 == 0) ? 1 : 0;
     const bool batched = offsets != nullptr;
     const void* kern;
+    const bool nox = kind == kBwdSimplex && mask;  // F from the mask: x is not read
     if (dtype == CQK_F64) {
         kern = kind == kBwdGeneral ? pick_kernel<double, kBwdGeneral>(batched)
-               : kind == kBwdSimplex ? pick_kernel<double, kBwdSimplex>(batched)
+               : kind == kBwdSimplex ? (nox ? pick_kernel<double, kBwdSimplex, true>(batched)
+                                            : pick_kernel<double, kBwdSimplex>(batched))
                                      : pick_kernel<double, kBwdL1>(batched);
     } else {
         kern = kind == kBwdGeneral ? pick_kernel<float, kBwdGeneral>(batched)
-               : kind == kBwdSimplex ? pick_kernel<float, kBwdSimplex>(batched)
+               : kind == kBwdSimplex ? (nox ? pick_kernel<float, kBwdSimplex, true>(batched)
+                                            : pick_kernel<float, kBwdSimplex>(batched))
                                      : pick_kernel<float, kBwdL1>(batched);
     }
     const int64_t vec = dtype == CQK_F64 ? 2 : 4;
