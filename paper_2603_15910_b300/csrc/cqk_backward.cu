@@ -68,17 +68,22 @@ __device__ __forceinline__ bool eq_val(T a, T b) {
     else return a == b;
 }
 
-// free bits of the V elements of vector q (from the forward mask, else from l < x < u)
+// the forward mask word holding vector q (0 when the vector has no element of the span), loaded
+// with the vector's data so that both share one memory round trip
+template <typename T>
+__device__ __forceinline__ uint32_t mask_word(const BwdArgs& A, const Span& sp, int64_t q) {
+    constexpr int V = VecOf<T>::V;
+    const int64_t e0 = q * V;
+    if (!A.mask || e0 >= sp.hi || e0 + V <= sp.lo) return 0u;
+    return __ldg(A.mask + (e0 >> 5));
+}
+
+// free bits of the V elements of vector q (from the forward mask word, else from l < x < u)
 template <typename T, int KIND>
-__device__ __forceinline__ unsigned free_bits(const BwdArgs& A, const Span& sp, int64_t q, const T (&x)[VecOf<T>::V],
+__device__ __forceinline__ unsigned free_bits(const BwdArgs& A, int64_t q, uint32_t mw, const T (&x)[VecOf<T>::V],
                                               const T (&l)[VecOf<T>::V], const T (&u)[VecOf<T>::V]) {
     constexpr int V = VecOf<T>::V;
-    if (A.mask) {
-        const int64_t e0 = q * V;
-        if (e0 >= sp.hi || e0 + V <= sp.lo) return 0u;  // no element of the span: no mask word
-        const uint32_t w = __ldg(A.mask + (e0 >> 5));
-        return (w >> (e0 & 31)) & ((1u << V) - 1u);
-    }
+    if (A.mask) return (mw >> ((q * V) & 31)) & ((1u << V) - 1u);
     unsigned f = 0;
 #pragma unroll
     for (int j = 0; j < V; j++) {
@@ -202,10 +207,12 @@ __device__ __forceinline__ void bwd_instance(const BwdArgs& A, const Grp& gp, in
             const int64_t base = sw.base(it, false);
             T vg[U][V], vx[U][V], vb[U][V], vd[U][V], vl[U][V], vu[U][V];
             bool ok[U][V];
+            uint32_t mw[U];
 #pragma unroll
             for (int w = 0; w < U; w++) {
                 const int64_t q = base + w * 32 + lane;
                 load_vec<T>(static_cast<const T*>(A.g), sp, q, aligned, vg[w], ok[w]);
+                mw[w] = mask_word<T>(A, sp, q);
                 load_or<T>(xp, sp, q, aligned, vx[w], ok[w], T(0));
                 if (KIND == kBwdGeneral) {
                     load_or<T>(A.b, sp, q, aligned, vb[w], ok[w], T(1));
@@ -219,7 +226,7 @@ __device__ __forceinline__ void bwd_instance(const BwdArgs& A, const Grp& gp, in
 #pragma unroll
             for (int w = 0; w < U; w++) {
                 const int64_t q = base + w * 32 + lane;
-                const unsigned fb = free_bits<T, KIND>(A, sp, q, vx[w], vl[w], vu[w]);
+                const unsigned fb = free_bits<T, KIND>(A, q, mw[w], vx[w], vl[w], vu[w]);
                 unsigned widem = 0;
 #pragma unroll
                 for (int j = 0; j < V; j++) {
@@ -278,10 +285,12 @@ __device__ __forceinline__ void bwd_instance(const BwdArgs& A, const Grp& gp, in
         const int64_t base = sw.base(it, true);
         T vg[U][V], vx[U][V], vb[U][V], vd[U][V], vl[U][V], vu[U][V];
         bool ok[U][V];
+        uint32_t mw[U];
 #pragma unroll
         for (int w = 0; w < U; w++) {
             const int64_t q = base + w * 32 + lane;
             load_vec<T>(static_cast<const T*>(A.g), sp, q, aligned, vg[w], ok[w]);
+            mw[w] = inside ? 0u : mask_word<T>(A, sp, q);
             load_or<T>(xp, sp, q, aligned, vx[w], ok[w], T(0));
             if (KIND == kBwdGeneral) {
                 load_or<T>(A.b, sp, q, aligned, vb[w], ok[w], T(1));
@@ -295,7 +304,7 @@ __device__ __forceinline__ void bwd_instance(const BwdArgs& A, const Grp& gp, in
 #pragma unroll
         for (int w = 0; w < U; w++) {
             const int64_t q = base + w * 32 + lane;
-            const unsigned fb = inside ? ((1u << V) - 1u) : free_bits<T, KIND>(A, sp, q, vx[w], vl[w], vu[w]);
+            const unsigned fb = inside ? ((1u << V) - 1u) : free_bits<T, KIND>(A, q, mw[w], vx[w], vl[w], vu[w]);
             T oa[V], ob[V], od[V], ol[V], ou[V];
             unsigned widem = 0;
 #pragma unroll
