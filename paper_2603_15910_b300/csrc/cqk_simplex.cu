@@ -164,173 +164,104 @@ struct CondatShared {
 };
 
 // ---- the scalar recurrence of Alg. 2 --------------------------------------------------------
-// The scan is one long dependency chain (lambda_{k+1} from lambda_k) run by one warp, and on
-// this GPU dependent FP64 operations are slow (measured in one warp: a step in FP64 with the
-// reciprocal of the next count formed alongside ~1160 cycles, the double-float step below
-// ~800).  The decisions of the scan — y_j + lambda > 0 and the restart test
-// lambda_{J u {j}} < r - y_j — are therefore taken in double-float (FP32 pipe, error below
-// `band`) whenever the margin exceeds the bound, and otherwise from the exact FP64 values of
-// the sequential scan, recomputed from their exact operands: the FP64 sum S of J is kept in
-// the scan's order alongside its double-float copy.  The decisions, hence J, J~, |J| and S,
-// are those of the FP64 scan.
-//
-// The parts of the next lambda that depend on J alone (r - S, 1/(|J|+1), the error-bound
-// magnitudes) are formed right after each step, while the warp re-tests and picks the next
-// candidate, so that the chain of the next step starts from the candidate's own operands.
+// The scan is one long dependency chain (lambda_{k+1} from lambda_k) run by one warp, so its
+// cost is the latency and the instruction count of one step.  The scan's own FP64 operations
+// are kept except the division: S (the sum of J in scan order), r - S and t = (r - S) - y are
+// formed exactly as the sequential scan forms them, and lambda = fl(t / (|J|+1)) is replaced
+// by the product t * w with w within 2^-46 of 1/(|J|+1) (a float reciprocal and one Newton
+// correction, formed while the previous step runs), which lies within kLamUlps units in the
+// last place of the scan's quotient (2^-46 + 2^-52 relative, at most ~2^8 units across a
+// binade boundary).  Every decision of the scan — y > -lambda (l1: |y| > max{0, -lambda}) and
+// the restart test lambda < r - y — is taken from the product when it holds for every value
+// within kLamUlps units of it (integer compares of order keys), and from the exact quotient
+// otherwise (out of line, rare).  The decisions, hence J, J~, |J| and S, are those of the
+// FP64 scan.  (A double-float version of the step measured ~800 cycles in one warp, an FP64
+// one with a correctly rounded reciprocal ~1160.)
+constexpr long long kLamUlps = 512;
+
 struct CondatState {
-    double S;  // exact: the FP64 sum of J in scan order
-    df Sd;     // S in double-float
+    double S;     // the FP64 sum of J in scan order
+    double rmS;   // fl(r - S)
     long long nJ;
-    int64_t rs;
-    df lam;       // lambda in double-float
-    float band;   // bound on |lam - lambda|
-    float sderr;  // bound on |Sd - S|
-    bool sdok;    // every y of J in the double-float range (Sd meaningful)
-    bool dfok;    // r and every y of J in the double-float range (else decisions are taken in FP64)
-    // lambda = fl(fl(fl(r - eS) - ey) / en) when en > 0, fl(r - ey) when en == 0
-    double eS, ey;
-    long long en;
-    // floats rounded outward around c(lambda): v > chi certainly passes, v <= clo certainly
-    // fails (as doubles); in between the exact FP64 threshold decides
-    float clo, chi;
-    GtThreshold glo, ghi;  // the same bounds as double bit patterns
-    // prepared for the next step (condat_prep): r - Sd, 1/(|J|+1) as a float pair and rounded
-    // up, |r| + |Sd| (float parts), and whether |J|+1 is not exact in a float
-    df rmS, inv;
-    float r0u, ab;
-    bool big;
+    int64_t rs;   // index of the last restart
+    double w1;    // ~1/(|J|+1) (relative error below 2^-46; |J|+1 < 2^24)
+    // the scan's lambda is fl(t / en) (en > 0) or t itself (en == 0); lk = order key of the
+    // approximation, within kLamUlps of the key of lambda (exact when en == 0)
+    double t;
+    long long en, lk;
+    GtThreshold glo, ghi;  // v <= glo: certainly fails; v > ghi: certainly passes
     double* list;
     int cnt, jt_end;
 };
 
-__device__ __forceinline__ void condat_init(CondatState& st, double r, double* list) {
+__device__ __forceinline__ void condat_init(CondatState& st, double* list) {
     st.S = 0.0;
-    st.Sd = df{0.0f, 0.0f};
+    st.rmS = 0.0;
     st.nJ = 0;
     st.rs = -1;
-    st.lam = df{0.0f, 0.0f};
-    st.band = 0.0f;
-    st.sderr = 0.0f;
-    st.sdok = true;
-    st.dfok = df_in_range(r, false) && r != 0.0;
-    st.eS = st.ey = 0.0;
+    st.w1 = 1.0;
+    st.t = 0.0;
     st.en = 0;
-    st.clo = -INFINITY;
-    st.chi = INFINITY;
-    st.glo = make_gt(-INFINITY);
-    st.ghi = make_gt(INFINITY);
-    st.rmS = st.inv = df{0.0f, 0.0f};
-    st.r0u = st.ab = 0.0f;
-    st.big = false;
+    st.lk = 0;
+    st.glo = make_gt(-INFINITY);  // before J starts every element passes
+    st.ghi = make_gt(-INFINITY);
     st.list = list;
     st.cnt = 0;
     st.jt_end = 0;
 }
 
-// the operands of one candidate y (l1: |y|)
-struct CondatOp {
-    double y;
-    df yd;       // split of y
-    df rmy;      // r - y in double-float
-    float rb;    // error-bound magnitude of r - y
-    bool inr;    // y in the double-float range
-};
-__device__ __forceinline__ CondatOp condat_op(double y, df rd) {
-    CondatOp o;
-    o.y = y;
-    o.yd = split_f64(y);
-    o.rmy = df_add(rd, df_neg(o.yd));
-    o.rb = 2.8e-14f * (fabsf(rd.hi) + fabsf(o.yd.hi));
-    o.inr = df_in_range(y, false);
-    return o;
-}
-
-__device__ __forceinline__ df df_of_count(long long n) {  // exact for n < 2^36, normalised
-    if (n < (1ll << 24)) return df{(float)n, 0.0f};
-    const long long h = n & ~0xFFFll;
-    return df{(float)h, (float)(n - h)};
-}
-
-// the J-only parts of lambda_{J u {y}} for the current J (after every change of S, Sd, |J|)
-__device__ __forceinline__ void condat_prep(CondatState& st, df rd) {
-    st.rmS = df_add(rd, df_neg(st.Sd));
-    const long long n1 = st.nJ + 1;
-    st.big = n1 >= (1ll << 24);  // then the bound is infinite and FP64 decides
-    // 1/n as a float pair (n < 2^24 exactly representable; ~2^-46 relative): cheaper than a
-    // double-float division
-    const float nf = (float)(int)(st.big ? (1ll << 24) : n1);
+// ~1/n for 1 <= n < 2^24: the float reciprocal and one Newton correction (error below
+// 2^-46 relative), as a double (the float parts converted on the integer pipe)
+__device__ __forceinline__ double condat_recip(long long n) {
+    const float nf = (float)(int)n;
     const float r0 = __frcp_rn(nf);
     const float e0 = fmaf(-nf, r0, 1.0f);
-    st.inv = fast_two_sum(r0, __fmul_rn(r0, e0));
-    st.r0u = __fmul_ru(r0, 1.0000001f);
-    st.ab = fabsf(rd.hi) + fabsf(st.Sd.hi);
+    return f32_to_f64_bits(r0) + f32_to_f64_bits(__fmul_rn(r0, e0));
 }
 
+// the thresholds of the tests from the key of lambda, +-m keys (l1: c = max{0, -lambda})
 template <bool L1>
-__device__ __forceinline__ void condat_bounds(CondatState& st);
-
-// lambda_{J u {y}} = (r - S - y)/(|J| + 1) into nx (st: the state before the step)
-template <bool L1>
-__device__ __forceinline__ void condat_lam_next(CondatState& nx, const CondatState& st, const CondatOp& op) {
-    nx.eS = st.S;
-    nx.ey = op.y;
-    nx.en = st.nJ + 1;
-    const df num = df_add(st.rmS, df_neg(op.yd));
-    nx.lam = df_mul(num, st.inv);
-    const float scale = 9.1e-13f * (st.ab + fabsf(op.yd.hi)) + 2.0f * st.sderr;
-    nx.band = __fmul_ru(scale, st.r0u) + 9.1e-13f * fabsf(nx.lam.hi) + 1e-37f;
-    if (st.big) nx.band = INFINITY;  // n not exact in a float: FP64 decides
-    condat_bounds<L1>(nx);
-}
-// lambda = r - y (a restart with J = {y})
-template <bool L1>
-__device__ __forceinline__ void condat_lam_restart(CondatState& st, const CondatOp& op) {
-    st.eS = 0.0;
-    st.ey = op.y;
-    st.en = 0;
-    st.lam = op.rmy;
-    st.band = op.rb + 1e-37f;
-    condat_bounds<L1>(st);
+__device__ __forceinline__ void condat_thresholds(CondatState& st, long long m) {
+    // c = -lambda: key(-x) = -key(x) - 1; the larger keys of lambda give the smaller c
+    long long klo = -(st.lk + m) - 1, khi = -(st.lk - m) - 1;
+    if (L1) {
+        klo = klo < 0 ? 0 : klo;
+        khi = khi < 0 ? 0 : khi;
+    }
+    st.glo = make_gt(from_order_key(klo));
+    st.ghi = make_gt(from_order_key(khi));
 }
 
-// c(lambda) = -lambda (l1: max{0, -lambda}) in double-float
-template <bool L1>
-__device__ __forceinline__ df condat_cdf(df lam) {
-    df c = df_neg(lam);
-    if (L1 && c.hi < 0.0f) c = df{0.0f, 0.0f};
-    return c;
+// the approximation's neighbourhood stays inside the finite range (else FP64 decides)
+__device__ __forceinline__ bool condat_lam_ok(double lam_approx) {
+    return ((hi_word(lam_approx) >> 20) & 0x7FFu) < 0x7FEu;
 }
 
+// lambda of the current (t, en) and its thresholds
 template <bool L1>
-__device__ __forceinline__ void condat_bounds(CondatState& st) {
-    const df c = condat_cdf<L1>(st.lam);
-    float lo = __fsub_rd(__fadd_rd(c.hi, c.lo), st.band);
-    float hi = __fadd_ru(__fadd_ru(c.hi, c.lo), st.band);
-    if (!(st.dfok && st.sdok && lo == lo && hi == hi && fabsf(lo) < 1e30f && fabsf(hi) < 1e30f)) {
-        st.clo = -INFINITY;  // no certain decision: every test goes to FP64
-        st.chi = INFINITY;
+__device__ __forceinline__ void condat_set_lambda(CondatState& st, double lam_approx) {
+    st.lk = order_key(lam_approx);
+    if (st.en == 0) {
+        condat_thresholds<L1>(st, 0);
+    } else if (!condat_lam_ok(lam_approx) || st.en >= (1ll << 24)) {  // no certain decision
         st.glo = make_gt(-INFINITY);
         st.ghi = make_gt(INFINITY);
-        return;
+    } else {
+        condat_thresholds<L1>(st, kLamUlps);
     }
-    st.clo = lo;
-    st.chi = hi;
-    st.glo = make_gt(f32_to_f64_bits(lo));
-    st.ghi = make_gt(f32_to_f64_bits(hi));
 }
 
 // The exact FP64 decisions, out of line: inlined, the compiler evaluates the FP64 division
-// speculatively on every test (measured: ~2400 cycles per test instead of a few).
+// speculatively on every test.
 template <bool L1>
-__device__ __noinline__ bool condat_exact_gt(unsigned long long vb, double eS, double ey, long long en, double r) {
-    const double le = en == 0 ? r - ey : ((r - eS) - ey) / (double)en;
+__device__ __noinline__ bool condat_exact_gt(unsigned long long vb, double t, long long en) {
+    const double le = en == 0 ? t : t / (double)en;
     unsigned long long cb = opaque_bits(le) ^ 0x8000000000000000ull;
     if (L1 && (cb >> 63)) cb = 0ull;
     return gt_bits(vb, make_gt(__longlong_as_double((long long)cb)));
 }
-__device__ __noinline__ bool condat_exact_accepts(double eS, double ey, long long en, double r, double y) {
-    const double le = en == 0 ? r - ey : ((r - eS) - ey) / (double)en;
-    return le < r - y;
+__device__ __noinline__ bool condat_exact_less(double t, long long en, double rmy) {
+    return t / (double)en < rmy;
 }
 
 // the test v > c(lambda) of the FP64 scan (v = y_j, l1: |y_j|)
@@ -339,18 +270,7 @@ __device__ __forceinline__ bool condat_gt(double v, const CondatState& st, doubl
     const unsigned long long vb = opaque_bits(v);
     if (gt_bits(vb, st.ghi)) return true;
     if (!gt_bits(vb, st.glo)) return false;
-    return condat_exact_gt<L1>(vb, st.eS, st.ey, st.en, r);  // rare
-}
-
-// the restart test of Alg. 2: accept y (J <- J u {y}) iff lambda_{J u {y}} < r - y
-__device__ __forceinline__ bool condat_accepts(const CondatState& nx, double r, const CondatOp& op) {
-    if (nx.dfok && nx.sdok && op.inr) {
-        const df d = df_add(nx.lam, df_neg(op.rmy));
-        const float bd = nx.band + op.rb;
-        if (d.hi < -bd) return true;
-        if (d.hi > bd) return false;
-    }
-    return condat_exact_accepts(nx.eS, nx.ey, nx.en, r, op.y);  // rare: exact FP64
+    return condat_exact_gt<L1>(vb, st.t, st.en);  // rare
 }
 
 __device__ __forceinline__ void condat_record(CondatState& st, double v) {
@@ -358,69 +278,73 @@ __device__ __forceinline__ void condat_record(CondatState& st, double v) {
     st.cnt++;
 }
 
-// J <- {y} (the first element of the chunk, or a restart)
+// J <- {y} (the first element of the chunk, or a restart): lambda = r - y exactly
 template <bool L1>
-__device__ __forceinline__ void condat_start_j(CondatState& st, df rd, const CondatOp& op) {
-    st.S = op.y;
-    st.Sd = op.yd;
-    st.sderr = 1.5e-14f * fabsf(op.yd.hi);
-    st.sdok = op.inr;
+__device__ __forceinline__ void condat_start_j(CondatState& st, double r, double y) {
+    st.S = y;
+    st.rmS = r - y;
     st.nJ = 1;
-    condat_lam_restart<L1>(st, op);
+    st.w1 = 0.5;
+    st.t = st.rmS;
+    st.en = 0;
+    condat_set_lambda<L1>(st, st.rmS);
     st.jt_end = st.cnt;
-}
-// J <- J u {y} with lambda_{J u {y}} already in nx
-__device__ __forceinline__ void condat_join(CondatState& st, const CondatState& nx, const CondatOp& op) {
-    st.lam = nx.lam;
-    st.band = nx.band;
-    st.eS = nx.eS;
-    st.ey = nx.ey;
-    st.en = nx.en;
-    st.clo = nx.clo;
-    st.chi = nx.chi;
-    st.glo = nx.glo;
-    st.ghi = nx.ghi;
-    st.S += op.y;
-    st.Sd = df_add(st.Sd, op.yd);
-    st.sderr += 2.8e-14f * (fabsf(st.Sd.hi) + fabsf(op.yd.hi));
-    st.sdok = st.sdok && op.inr;
-    st.nJ += 1;
 }
 
 // one element taken by the first loop of Alg. 2 (J started): add it or restart with it
 template <bool L1>
-__device__ __forceinline__ void condat_take(CondatState& st, double r, df rd, const CondatOp& op, int64_t e) {
-    CondatState nx = st;
-    condat_lam_next<L1>(nx, st, op);
-    if (condat_accepts(nx, r, op)) {
-        condat_join(st, nx, op);
+__device__ __forceinline__ void condat_take(CondatState& st, double r, double y, int64_t e) {
+    const double t = st.rmS - y;
+    const double lam = t * st.w1;
+    const double rmy = r - y;
+    const double w2 = condat_recip(st.nJ + 2);  // for the step after an addition
+    const long long lk = order_key(lam), ky = order_key(rmy);
+    // restart test lambda < r - y, from the approximation unless within its uncertainty
+    const bool sure = condat_lam_ok(lam) && st.nJ + 1 < (1ll << 24);
+    bool acc;
+    if (sure && lk + kLamUlps < ky) acc = true;
+    else if (sure && lk - kLamUlps >= ky) acc = false;
+    else acc = condat_exact_less(t, st.nJ + 1, rmy);  // rare
+    if (acc) {
+        st.S += y;
+        st.rmS = r - st.S;
+        st.nJ += 1;
+        st.w1 = w2;
+        st.t = t;
+        st.en = st.nJ;
+        condat_set_lambda<L1>(st, lam);
     } else {  // restart: J~ <- J~ u J, J <- {j}
         st.rs = e;
-        condat_start_j<L1>(st, rd, op);
+        condat_start_j<L1>(st, r, y);
     }
-    condat_record(st, op.y);
-    condat_prep(st, rd);
+    condat_record(st, y);
 }
 
 // the final loop of Alg. 2: J <- J u {y} (no restart test)
 template <bool L1>
-__device__ __forceinline__ void condat_add(CondatState& st, double r, df rd, double y) {
-    const CondatOp op = condat_op(y, rd);
-    CondatState nx = st;
-    condat_lam_next<L1>(nx, st, op);
-    condat_join(st, nx, op);
-    condat_prep(st, rd);
+__device__ __forceinline__ void condat_add(CondatState& st, double r, double y) {
+    const double t = st.rmS - y;
+    const double lam = t * st.w1;
+    st.S += y;
+    st.rmS = r - st.S;
+    st.nJ += 1;
+    st.w1 = condat_recip(st.nJ + 1);
+    st.t = t;
+    st.en = st.nJ;
+    condat_set_lambda<L1>(st, lam);
 }
 
-// the block filter's threshold: a float at or below c(lambda) - band (a superset of the
-// elements the scan can accept), as a float (FP32 data); FP64 data take st.glo
-__device__ __forceinline__ float condat_filter_rd(const CondatState& st) { return st.clo; }
+// the block filter's threshold for FP32 data: a float at or below every c the scan can still
+// use (the FP64 data take the bit pattern st.glo)
+__device__ __forceinline__ float condat_filter_rd(const CondatState& st) {
+    return __double2float_rd(__longlong_as_double((long long)st.glo.bits));
+}
 
 // Warp 0: the first loop of Alg. 2 over one group of 32 vectors in index order (lane, j);
 // okv marks the elements that passed the block's filter.
 template <typename T, bool L1>
 __device__ __forceinline__ void condat_slab(const T (&vals)[VecOf<T>::V], const bool (&okv)[VecOf<T>::V],
-                                            int64_t eidx0, double r, df rd, CondatState& st) {
+                                            int64_t eidx0, double r, CondatState& st) {
     constexpr int V = VecOf<T>::V;
     const int lane = threadIdx.x & 31;
     double av[V];
@@ -444,11 +368,10 @@ __device__ __forceinline__ void condat_slab(const T (&vals)[VecOf<T>::V], const 
 #pragma unroll
         for (int j = V - 1; j >= 0; j--)
             if ((mo[j] >> L0) & 1u) j0 = j;
-        const CondatOp o0 = condat_op(__shfl_sync(0xffffffffu, pick(av, j0), L0), rd);
+        const double y0 = __shfl_sync(0xffffffffu, pick(av, j0), L0);
         st.rs = __shfl_sync(0xffffffffu, eidx0, L0) + j0;
-        condat_start_j<L1>(st, rd, o0);
-        condat_record(st, o0.y);
-        condat_prep(st, rd);
+        condat_start_j<L1>(st, r, y0);
+        condat_record(st, y0);
 #pragma unroll
         for (int j = 0; j < V; j++) {
             const bool after = (lane > L0) || (lane == L0 && j > j0);
@@ -474,7 +397,7 @@ __device__ __forceinline__ void condat_slab(const T (&vals)[VecOf<T>::V], const 
             if ((m[j] >> Lf) & 1u) jf = j;
         const double yv = __shfl_sync(0xffffffffu, pick(av, jf), Lf);
         const int64_t e = __shfl_sync(0xffffffffu, eidx0, Lf) + jf;
-        condat_take<L1>(st, r, rd, condat_op(yv, rd), e);
+        condat_take<L1>(st, r, yv, e);
 #pragma unroll
         for (int j = 0; j < V; j++) {
             const bool after = (lane > Lf) || (lane == Lf && j > jf);
@@ -483,11 +406,32 @@ __device__ __forceinline__ void condat_slab(const T (&vals)[VecOf<T>::V], const 
     }
 }
 
+// warp 0: the final loop of Alg. 2 over the first n entries of the J~ list, 32 at a time: every
+// lane tests its entry against the current lambda, and the passing entries are added in list
+// order, the later ones re-tested after each addition (an addition only raises c(lambda), so
+// an entry that fails stays out)
+template <bool L1>
+__device__ __forceinline__ void condat_final_list(const double* list, int n, double r, CondatState& st) {
+    const int lane = threadIdx.x & 31;
+    for (int base = 0; base < n; base += 32) {
+        const int e = base + lane;
+        const double val = e < n ? list[e] : 0.0;
+        bool pass = e < n && condat_gt<L1>(val, st, r);
+        while (true) {
+            const unsigned m = __ballot_sync(0xffffffffu, pass);
+            if (!m) break;
+            const int Lf = __ffs(m) - 1;
+            condat_add<L1>(st, r, __shfl_sync(0xffffffffu, val, Lf));
+            pass = pass && lane > Lf && condat_gt<L1>(val, st, r);
+        }
+    }
+}
+
 // warp 0, J~ outgrew the list: the final loop of Alg. 2 as a re-scan of one slab (32 vectors)
 // of the chunk prefix before the last restart
 template <typename T, bool L1>
 __device__ __forceinline__ void condat_rescan_slab(const T (&vals)[VecOf<T>::V], const bool (&okv)[VecOf<T>::V],
-                                                   int64_t eidx0, double r, df rd, CondatState& st) {
+                                                   int64_t eidx0, double r, CondatState& st) {
     constexpr int V = VecOf<T>::V;
     const int lane = threadIdx.x & 31;
     double av[V];
@@ -514,7 +458,7 @@ __device__ __forceinline__ void condat_rescan_slab(const T (&vals)[VecOf<T>::V],
         for (int j = V - 1; j >= 0; j--)
             if ((m[j] >> Lf) & 1u) jf = j;
         const double yv = __shfl_sync(0xffffffffu, pick(av, jf), Lf);
-        condat_add<L1>(st, r, rd, yv);
+        condat_add<L1>(st, r, yv);
 #pragma unroll
         for (int j = 0; j < V; j++) {
             const bool after = (lane > Lf) || (lane == Lf && j > jf);
@@ -657,8 +601,7 @@ __device__ void condat_block(const T* __restrict__ y, const T* __restrict__ xb, 
     __shared__ CondatShared s;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     CondatState st;
-    condat_init(st, r, s.list);
-    const df rdf = split_f64(r);
+    condat_init(st, s.list);
     if (threadIdx.x == 0) {  // before J starts every element passes the filter
         s.tb = make_gt(-INFINITY).bits;  // the sign bit of the pattern is the sign of the threshold
         s.trd = -INFINITY;
@@ -767,15 +710,23 @@ __device__ void condat_block(const T* __restrict__ y, const T* __restrict__ xb, 
                 const int64_t c = ring.tile(i, false);
                 const int64_t sb0 = ring.b0(c), sb1 = ring.b1(c);
                 const T* stage = ring.stage(stg, 0);
+                const bool whole = sb0 == c * TT && sb1 == (c + 1) * TT;  // the stage holds every element
                 for (unsigned gs = groups; gs; gs &= gs - 1) {
                     const int gi = __ffs(gs) - 1;
                     const int ql = gi * 32 + lane;
                     T v[V];
                     bool ok[V];
-                    tile_vec<T>(y, sp, stage, true, c, ql, sb0, sb1, v, ok);
+                    if (whole) {
+                        using VT = typename VecOf<T>::type;
+                        const VT w = reinterpret_cast<const VT*>(stage)[ql];
+#pragma unroll
+                        for (int j = 0; j < V; j++) v[j] = reinterpret_cast<const T*>(&w)[j];
+                    } else {
+                        tile_vec<T>(y, sp, stage, true, c, ql, sb0, sb1, v, ok);
+                    }
 #pragma unroll
                     for (int j = 0; j < V; j++) ok[j] = ((mk[gi * V + j] >> lane) & 1u) != 0u;
-                    condat_slab<T, L1>(v, ok, (c * NVEC + ql) * V, r, rdf, st);
+                    condat_slab<T, L1>(v, ok, (c * NVEC + ql) * V, r, st);
                 }
                 if (lane == 0 && st.nJ > 0) {
                     *reinterpret_cast<volatile float*>(&s.trd) = condat_filter_rd(st);
@@ -814,7 +765,7 @@ __device__ void condat_block(const T* __restrict__ y, const T* __restrict__ xb, 
                     tile_vec<T>(y, sp, nullptr, false, c, ql, 0, 0, v, ok);
 #pragma unroll
                     for (int j = 0; j < V; j++) ok[j] = ((s.msk[w][k * V + j] >> lane) & 1u) != 0u;
-                    condat_slab<T, L1>(v, ok, (c * (TT / V) + ql) * V, r, rdf, st);
+                    condat_slab<T, L1>(v, ok, (c * (TT / V) + ql) * V, r, st);
                 }
                 if (lane == 0 && st.nJ > 0) {
                     s.tb = st.glo.bits;
@@ -829,10 +780,7 @@ __device__ void condat_block(const T* __restrict__ y, const T* __restrict__ xb, 
     if (wid == 0 && st.nJ > 0) {
         if (st.jt_end <= kJList) {
             __syncwarp();
-            for (int e = 0; e < st.jt_end; e++) {
-                const double val = st.list[e];
-                if (condat_gt<L1>(val, st, r)) condat_add<L1>(st, r, rdf, val);
-            }
+            condat_final_list<L1>(st.list, st.jt_end, r, st);
         } else if (st.rs >= 0) {
             const int64_t c0 = sp.lo / TT;
             for (int64_t c = c0 + member; c * TT <= st.rs; c += nchunk) {
@@ -842,7 +790,7 @@ __device__ void condat_block(const T* __restrict__ y, const T* __restrict__ xb, 
                     bool okv[V];
                     load_vec<T>(y, sp, q, aligned, vals, okv);
                     support_mask<T, L1>(xb, sp, q, aligned, okv);
-                    condat_rescan_slab<T, L1>(vals, okv, q * V, r, rdf, st);
+                    condat_rescan_slab<T, L1>(vals, okv, q * V, r, st);
                 }
             }
         }
@@ -1450,8 +1398,7 @@ __device__ void simplex_warp_solve(const SimplexArgs& A, const Span& sp, double*
         passes++;
     } else {
         CondatState st;
-        condat_init(st, r, list);
-        const df rdf = split_f64(r);
+        condat_init(st, list);
         for (int64_t q0 = (qlo / 32) * 32; q0 < qhi; q0 += 32) {
             const int64_t q = q0 + lane;
             T v[V];
@@ -1463,16 +1410,13 @@ __device__ void simplex_warp_solve(const SimplexArgs& A, const Span& sp, double*
                 else sacc.bad |= ok[j] && (v[j] != v[j]);
             }
             support_mask<T, L1>(xb, sp, q, aligned, ok);
-            condat_slab<T, L1>(v, ok, q * V, r, rdf, st);
+            condat_slab<T, L1>(v, ok, q * V, r, st);
         }
         passes++;
         if (st.nJ > 0) {
             if (st.jt_end <= kWarpList) {  // the final loop of Alg. 2 over J~
                 __syncwarp();
-                for (int e = 0; e < st.jt_end; e++) {
-                    const double val = list[e];
-                    if (condat_gt<L1>(val, st, r)) condat_add<L1>(st, r, rdf, val);
-                }
+                condat_final_list<L1>(list, st.jt_end, r, st);
             } else {
                 for (int64_t q0 = (qlo / 32) * 32; q0 * V <= st.rs; q0 += 32) {
                     const int64_t q = q0 + lane;
@@ -1480,7 +1424,7 @@ __device__ void simplex_warp_solve(const SimplexArgs& A, const Span& sp, double*
                     bool ok[V];
                     load_vec<T>(y, sp, q, aligned, v, ok);
                     support_mask<T, L1>(xb, sp, q, aligned, ok);
-                    condat_rescan_slab<T, L1>(v, ok, q * V, r, rdf, st);
+                    condat_rescan_slab<T, L1>(v, ok, q * V, r, st);
                 }
             }
             lam0 = (r - st.S) / (double)st.nJ;  // eq. (lambdaJ)
