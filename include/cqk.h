@@ -113,7 +113,13 @@ typedef struct cqk_options {
     int32_t warp_elems;     /* batched projections: instances shorter than warp_elems (rounded  */
                             /* down to a power of two) are solved by one warp each; 0 (default): */
                             /* 16384; negative: never                                           */
-    int32_t reserved[3];
+    int32_t scan_warps;     /* CQK_INIT_CONDAT projections on 16-byte aligned data: each block   */
+                            /* deals its tiles to scan_warps chunks (1, 2 or 4; other positive   */
+                            /* values round down to one of these), scanned by as                */
+                            /* many warps side by side (the partition then has nchunks =         */
+                            /* blocks * scan_warps, a looser union start); 0 (default): 4 for a  */
+                            /* one-block instance of 4 to 15 tiles of 16 KB, else 1             */
+    int32_t reserved[2];
 } cqk_options;
 
 /* Written on the device by every solve. */

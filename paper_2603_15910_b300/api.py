@@ -59,7 +59,8 @@ class _Options(ctypes.Structure):
         ("condat_chunk", ctypes.c_int32),
         ("xbar", ctypes.c_void_p),
         ("warp_elems", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 3),
+        ("scan_warps", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 2),
     ]
 
 
@@ -187,7 +188,7 @@ def stream_handle(stream=None):
 
 def make_options(init=None, max_iter=100, lambda0=0.0, validate=True, final_step=None, spin_limit_us=2_000_000,
                  max_blocks=0, fault_inject=False, group_elems=0, condat_chunk=0, xbar=None,
-                 warp_elems=0) -> _Options:
+                 warp_elems=0, scan_warps=0) -> _Options:
     o = _Options()
     library().cqk_default_options(ctypes.byref(o))
     o.max_iter = int(max_iter)
@@ -203,6 +204,7 @@ def make_options(init=None, max_iter=100, lambda0=0.0, validate=True, final_step
     o.condat_chunk = int(condat_chunk)
     o.xbar = xbar.data_ptr() if xbar is not None else None
     o.warp_elems = int(warp_elems)
+    o.scan_warps = int(scan_warps)
     return o
 
 

@@ -42,6 +42,8 @@ Opts resolve_options(const cqk_options* opt, int dtype, int default_init) {
         while ((2ll << lg) <= we && lg < 30) lg++;
         o.warp_log2 = lg;
     }
+    // scan_warps: 0 (automatic) or 1, 2, 4 (other positive values round down to one of these)
+    o.scan_warps = d.scan_warps >= 4 ? 4 : d.scan_warps >= 2 ? 2 : d.scan_warps >= 1 ? 1 : 0;
     return o;
 }
 

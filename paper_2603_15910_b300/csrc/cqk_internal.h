@@ -44,6 +44,7 @@ struct Opts {
     int64_t condat_chunk;  // CQK_INIT_CONDAT: minimum elements per chunk
     const void* xbar;      // CQK_INIT_WARM: primal estimate
     int warp_log2;         // batched projections: instances shorter than 2^warp_log2 take one warp (0: none)
+    int scan_warps;        // pipelined Alg. 2: chunks (scan warps) per block; 0 = automatic
 };
 
 Opts resolve_options(const cqk_options* opt, int dtype, int default_init);

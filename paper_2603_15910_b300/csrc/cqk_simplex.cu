@@ -49,6 +49,7 @@ struct SimplexArgs {
     unsigned long long limit_ns;
     int fault_inject;
     int64_t condat_chunk;  // minimum elements per chunk of the parallel Alg. 2 start
+    int scan_warps;        // chunks (scan warps) per block of the pipelined start; 0 = automatic
     const void* xbar;      // CQK_INIT_WARM: primal estimate
     WsHeader* hdr;
     double* part;  // [2][kPartialQ][gridDim.x]
@@ -153,14 +154,15 @@ template <typename T>
 __host__ __device__ constexpr int condat_tile() { return 16384 / (int)sizeof(T); }  // elements per tile
 constexpr size_t kCondatSmem = (size_t)kCondatStages * 16384;                      // dynamic shared memory
 constexpr int kJList = 1024;  // accepted values kept for the final loop
-constexpr int kStartBit = 16;  // bit of the start barrier's phase in the ring parity word
+constexpr int kStartBit = 16;  // bit of the first start barrier's phase in the ring parity word
+constexpr int kMaxScan = 4;    // scan warps (chunks) per block in the pipelined Alg. 2
 
 struct CondatShared {
     unsigned msk[NWARP][16];  // filter ballots of each warp, (k, j) -> bit lane
     unsigned pmsk[kCondatStages][32 * 4];  // pipelined filter: ballots of group g, (g, j) -> bit lane
     double list[kJList];
-    unsigned long long tb;    // the published test threshold (FP64 data: bit pattern)
-    float trd;                // (FP32 data)
+    unsigned long long tb[kMaxScan];  // the published test thresholds (FP64 data: bit patterns)
+    float trd[kMaxScan];              // (FP32 data)
 };
 
 // ---- the scalar recurrence of Alg. 2 --------------------------------------------------------
@@ -190,11 +192,11 @@ struct CondatState {
     double t;
     long long en, lk;
     GtThreshold glo, ghi;  // v <= glo: certainly fails; v > ghi: certainly passes
-    double* list;
-    int cnt, jt_end;
+    double* list;  // accepted values in acceptance order (the first cap of them)
+    int cap, cnt, jt_end;
 };
 
-__device__ __forceinline__ void condat_init(CondatState& st, double* list) {
+__device__ __forceinline__ void condat_init(CondatState& st, double* list, int cap) {
     st.S = 0.0;
     st.rmS = 0.0;
     st.nJ = 0;
@@ -206,6 +208,7 @@ __device__ __forceinline__ void condat_init(CondatState& st, double* list) {
     st.glo = make_gt(-INFINITY);  // before J starts every element passes
     st.ghi = make_gt(-INFINITY);
     st.list = list;
+    st.cap = cap;
     st.cnt = 0;
     st.jt_end = 0;
 }
@@ -274,7 +277,7 @@ __device__ __forceinline__ bool condat_gt(double v, const CondatState& st, doubl
 }
 
 __device__ __forceinline__ void condat_record(CondatState& st, double v) {
-    if ((threadIdx.x & 31) == 0 && st.cnt < kJList) st.list[st.cnt] = v;
+    if ((threadIdx.x & 31) == 0 && st.cnt < st.cap) st.list[st.cnt] = v;
     st.cnt++;
 }
 
@@ -515,8 +518,8 @@ __device__ __forceinline__ bool condat_filter_exact(const T* __restrict__ y, con
     constexpr int TT = condat_tile<T>();
     constexpr int KC = TT / V / NT;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const GtThreshold g{s.tb, (s.tb >> 63) != 0ull};
-    const float rd = s.trd;
+    const GtThreshold g{s.tb[0], (s.tb[0] >> 63) != 0ull};
+    const float rd = s.trd[0];
     bool anyp = false;
 #pragma unroll
     for (int k = 0; k < KC; k++) {
@@ -582,83 +585,80 @@ __device__ __forceinline__ bool condat_prefilter(const T* stage, const T* __rest
     return p;
 }
 
-// Alg. 2 on the chunk of block `member` of `nchunk` (blocks with member >= nchunk have none).
-// Called by all threads; (S_out, nJ_out) = (sum_J y, |J|) valid in thread 0; the NaN check
-// of the data rides on this pass, into sacc.bad.
-//
-// Per tile: every thread tests its KC vectors (interior tiles: first the cheap prefilter of the
-// whole block, the usual verdict being that nothing can pass); when something may pass, the
-// exact filter stores the warps' ballots and warp 0 walks the passing elements in index order
-// (k, warp, lane, j), re-reading their values from the stage, with the exact scan.
+// Alg. 2 on the chunks of block `member` of `nchunk` (blocks with member >= nchunk have none):
+// the block's tiles i = 0, 1, ... (tile member + i*nchunk of the span) are dealt to nscan
+// chunks, tile i to chunk i mod nscan, so that chunk k of block m is chunk m + nchunk*k of a
+// partition into nchunk*nscan chunks by tiles taken round robin.  Called by all threads;
+// (S_out, nJ_out) = (sum_J y, |J|) of each chunk, valid in lane 0 of scan warp k (zero
+// elsewhere); the NaN check of the data rides on this pass, into sacc.bad.
 template <typename T, bool L1>
 __device__ void condat_block(const T* __restrict__ y, const T* __restrict__ xb, const Span& sp, bool aligned,
-                             double r, int member, int nchunk, T* smem, uint64_t* bars, unsigned& parity, int* err,
-                             unsigned long long limit_ns, SumAcc& sacc, double& S_out, long long& nJ_out) {
+                             double r, int member, int nchunk, int nscan, T* smem, uint64_t* bars, unsigned& parity,
+                             int* err, unsigned long long limit_ns, SumAcc& sacc, double& S_out, long long& nJ_out) {
     constexpr int V = VecOf<T>::V;
     constexpr int TT = condat_tile<T>();
     constexpr int KC = TT / V / NT;
+    constexpr int S = kCondatStages;
     static_assert(KC * V * NT == TT && KC * V <= 16, "tile layout");
     __shared__ CondatShared s;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const bool staged = aligned;
+    if (!staged) nscan = 1;
+    const int cap = kJList / nscan;
     CondatState st;
-    condat_init(st, s.list);
-    if (threadIdx.x == 0) {  // before J starts every element passes the filter
-        s.tb = make_gt(-INFINITY).bits;  // the sign bit of the pattern is the sign of the threshold
-        s.trd = -INFINITY;
+    condat_init(st, s.list + (wid < nscan ? wid : 0) * cap, cap);
+    if (threadIdx.x < kMaxScan) {  // before J starts every element passes the filter
+        s.tb[threadIdx.x] = make_gt(-INFINITY).bits;  // the sign bit of the pattern is the sign of the threshold
+        s.trd[threadIdx.x] = -INFINITY;
     }
     TileRing<T, 1, TT> ring;
     ring.setup(sp.lo, sp.hi, smem, bars, member, nchunk);
     if (member >= nchunk) ring.count = 0;
     ring.parity = parity;
-    const bool staged = aligned;
     const T* src[1] = {y};
     __syncthreads();
-    if (staged && threadIdx.x == 0)
-        for (int k = 0; k < kCondatStages - 1; k++)
-            if (k < ring.count) ring.issue(ring.tile(k, false), k, src);
     if (staged) {
-        // Pipelined: warps 1..NWARP-1 filter the tiles as they land (up to kCondatStages - 1
-        // tiles ahead of the scan) and signal the stage's second mbarrier; warp 0 runs the scan
-        // over the groups with survivors, then refills the stage it is done with.  The
-        // filters read the threshold the scan last published, which can only be lower than
-        // the scan's own (c(lambda) only grows during the first loop), so they pass a superset.
+        // Pipelined: warps nscan..NWARP-1 filter the tiles as they land and signal the stage's
+        // second mbarrier; scan warp k runs the scan of chunk k over the groups with survivors
+        // of its tiles, then refills the stage it is done with.  The filters read the threshold
+        // that chunk's scan last published, which can only be lower than the scan's own
+        // (c(lambda) only grows during the first loop), so they pass a superset.
         constexpr int NVEC = TT / V;  // vectors of a tile
         constexpr int NG = NVEC / 32;  // groups of 32 vectors, in index order
-        constexpr int NP = NWARP - 1;  // filtering warps; group g belongs to warp 1 + g % NP
-        constexpr int KP = (NG + NP - 1) / NP;
-        static_assert(NG == 32 && KP * V <= 32, "one lane per group");
-        uint64_t* fullb = bars + kCondatStages;
-        uint64_t* startb = bars + 2 * kCondatStages;  // the scan is done with the first tile
-        if (wid > 0) {
-            const int pw = wid - 1;
-            for (int64_t i = 0; i < ring.count; i++) {
-                const int stg = (int)(i % kCondatStages);
-                // before J starts every element passes: the filters wait for the threshold of the
-                // scan's first tile instead of passing whole tiles to it
-                if (i == 1) mbar_wait(startb, (ring.parity >> kStartBit) & 1u, err, limit_ns, CQK_TIMEOUT);
-                mbar_wait(&ring.bar[stg], (ring.parity >> stg) & 1u, err, limit_ns, CQK_TIMEOUT);
-                ring.parity ^= 1u << stg;
+        static_assert(NG == 32 && V <= 32 && kMaxScan < S, "one lane per group; a scan warp steps by less than the ring");
+        const int NP = NWARP - nscan;  // filtering warps; group g belongs to filter g % NP
+        uint64_t* fullb = bars + S;
+        uint64_t* startb = bars + 2 * S;  // [k]: scan k is done with its first tile
+        const unsigned base = ring.parity;
+        if (threadIdx.x == 0)
+            for (int k = 0; k < S; k++)
+                if (k < ring.count) ring.issue(ring.tile(k, false), k, src);
+        if (wid >= nscan) {
+            const int pw = wid - nscan;
+            // stage, chunk and phase parities advance with i (no divisions in the loop)
+            int stg = 0, k = 0;
+            unsigned phs = base;  // bit s: parity of stage s's next phase
+            for (int64_t i = 0; i < ring.count; i++, stg = stg + 1 == S ? 0 : stg + 1, k = k + 1 == nscan ? 0 : k + 1) {
+                const unsigned ph = (phs >> stg) & 1u;
+                phs ^= 1u << stg;
+                // before J starts every element passes: the filters wait for the threshold of
+                // chunk k's first tile before filtering its second
+                if (i >= nscan && i < 2 * nscan)
+                    mbar_wait(&startb[k], (base >> (kStartBit + k)) & 1u, err, limit_ns, CQK_TIMEOUT);
+                mbar_wait(&ring.bar[stg], ph, err, limit_ns, CQK_TIMEOUT);
                 const int64_t c = ring.tile(i, false);
                 const int64_t sb0 = ring.b0(c), sb1 = ring.b1(c);
                 const T* stage = ring.stage(stg, 0);
-                const unsigned long long tb = *reinterpret_cast<volatile unsigned long long*>(&s.tb);
-                const float trd = *reinterpret_cast<volatile float*>(&s.trd);
+                const unsigned long long tb = *reinterpret_cast<volatile unsigned long long*>(&s.tb[k]);
+                const float trd = *reinterpret_cast<volatile float*>(&s.trd[k]);
                 bool may = !(sb0 == c * TT && sb1 == (c + 1) * TT);  // a partial tile: exact filter
-                if (!may) {
-#pragma unroll
-                    for (int k = 0; k < KP; k++) {
-                        const int gi = k * NP + pw;
-                        if (gi < NG)
-                            may |= condat_prefilter<T, L1>(stage, xb, sp, c, gi * 32 + lane, aligned, tb, trd);
-                    }
-                }
+                if (!may)
+                    for (int gi = pw; gi < NG; gi += NP)
+                        may |= condat_prefilter<T, L1>(stage, xb, sp, c, gi * 32 + lane, aligned, tb, trd);
                 unsigned* mk = s.pmsk[stg];
                 if (__any_sync(0xffffffffu, may)) {
                     const GtThreshold g{tb, (tb >> 63) != 0ull};
-#pragma unroll
-                    for (int k = 0; k < KP; k++) {
-                        const int gi = k * NP + pw;
-                        if (gi >= NG) break;
+                    for (int gi = pw; gi < NG; gi += NP) {
                         const int ql = gi * 32 + lane;
                         T v[V];
                         bool ok[V];
@@ -676,69 +676,76 @@ __device__ void condat_block(const T* __restrict__ y, const T* __restrict__ xb, 
                         }
                     }
                 } else if (lane == 0) {
+                    for (int gi = pw; gi < NG; gi += NP)
 #pragma unroll
-                    for (int k = 0; k < KP; k++) {
-                        const int gi = k * NP + pw;
-                        if (gi < NG)
-#pragma unroll
-                            for (int j = 0; j < V; j++) mk[gi * V + j] = 0u;
-                    }
+                        for (int j = 0; j < V; j++) mk[gi * V + j] = 0u;
                 }
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&fullb[stg]);  // release: the ballots of this warp
+                // release: the ballots of this warp (the barrier counts NWARP - 1 arrivals: the
+                // first filter also arrives for the scan warps beyond the first)
+                if (lane == 0) mbar_arrive_cnt(&fullb[stg], pw == 0 ? (unsigned)nscan : 1u);
             }
         } else {
-            for (int64_t i = 0; i < ring.count; i++) {
-                const int stg = (int)(i % kCondatStages);
-                // the stage of tile i - 1 is free: its filters signalled and its scan is done
-                if (lane == 0 && i + kCondatStages - 1 < ring.count)
-                    ring.issue(ring.tile(i + kCondatStages - 1, false), (int)((i + kCondatStages - 1) % kCondatStages),
-                               src);
-                __syncwarp();
-                mbar_wait(&fullb[stg], (ring.parity >> stg) & 1u, err, limit_ns, CQK_TIMEOUT);
-                mbar_wait(&ring.bar[stg], (ring.parity >> stg) & 1u, err, limit_ns, CQK_TIMEOUT);
-                ring.parity ^= 1u << stg;
+            const int k = wid;
+            int stg = k;          // i mod S (k < nscan <= kMaxScan < S)
+            unsigned flip = 0u;   // (i / S) mod 2
+            for (int64_t i = k; i < ring.count; i += nscan) {
+                const unsigned ph = ((base >> stg) ^ flip) & 1u;
+                mbar_wait(&fullb[stg], ph, err, limit_ns, CQK_TIMEOUT);
+                mbar_wait(&ring.bar[stg], ph, err, limit_ns, CQK_TIMEOUT);
                 const unsigned* mk = s.pmsk[stg];
                 unsigned gany = 0;
 #pragma unroll
                 for (int j = 0; j < V; j++) gany |= mk[lane * V + j];
                 const unsigned groups = __ballot_sync(0xffffffffu, gany != 0u);
-                if (!groups) {
-                    if (i == 0 && lane == 0) mbar_arrive(startb);
-                    continue;
-                }
-                const int64_t c = ring.tile(i, false);
-                const int64_t sb0 = ring.b0(c), sb1 = ring.b1(c);
-                const T* stage = ring.stage(stg, 0);
-                const bool whole = sb0 == c * TT && sb1 == (c + 1) * TT;  // the stage holds every element
-                for (unsigned gs = groups; gs; gs &= gs - 1) {
-                    const int gi = __ffs(gs) - 1;
-                    const int ql = gi * 32 + lane;
-                    T v[V];
-                    bool ok[V];
-                    if (whole) {
-                        using VT = typename VecOf<T>::type;
-                        const VT w = reinterpret_cast<const VT*>(stage)[ql];
+                if (groups) {
+                    const int64_t c = ring.tile(i, false);
+                    const int64_t sb0 = ring.b0(c), sb1 = ring.b1(c);
+                    const T* stage = ring.stage(stg, 0);
+                    const bool whole = sb0 == c * TT && sb1 == (c + 1) * TT;  // the stage holds every element
+                    for (unsigned gs = groups; gs; gs &= gs - 1) {
+                        const int gi = __ffs(gs) - 1;
+                        const int ql = gi * 32 + lane;
+                        T v[V];
+                        bool ok[V];
+                        if (whole) {
+                            using VT = typename VecOf<T>::type;
+                            const VT w = reinterpret_cast<const VT*>(stage)[ql];
 #pragma unroll
-                        for (int j = 0; j < V; j++) v[j] = reinterpret_cast<const T*>(&w)[j];
-                    } else {
-                        tile_vec<T>(y, sp, stage, true, c, ql, sb0, sb1, v, ok);
+                            for (int j = 0; j < V; j++) v[j] = reinterpret_cast<const T*>(&w)[j];
+                        } else {
+                            tile_vec<T>(y, sp, stage, true, c, ql, sb0, sb1, v, ok);
+                        }
+#pragma unroll
+                        for (int j = 0; j < V; j++) ok[j] = ((mk[gi * V + j] >> lane) & 1u) != 0u;
+                        condat_slab<T, L1>(v, ok, (c * NVEC + ql) * V, r, st);
                     }
-#pragma unroll
-                    for (int j = 0; j < V; j++) ok[j] = ((mk[gi * V + j] >> lane) & 1u) != 0u;
-                    condat_slab<T, L1>(v, ok, (c * NVEC + ql) * V, r, st);
+                    if (lane == 0 && st.nJ > 0) {
+                        *reinterpret_cast<volatile float*>(&s.trd[k]) = condat_filter_rd(st);
+                        *reinterpret_cast<volatile unsigned long long*>(&s.tb[k]) = st.glo.bits;
+                    }
                 }
-                if (lane == 0 && st.nJ > 0) {
-                    *reinterpret_cast<volatile float*>(&s.trd) = condat_filter_rd(st);
-                    *reinterpret_cast<volatile unsigned long long*>(&s.tb) = st.glo.bits;
+                __syncwarp();
+                if (lane == 0) {
+                    if (i == k) mbar_arrive(&startb[k]);  // release: the published threshold
+                    // the stage is free (its filters signalled, its scan is done): the next tile
+                    if (i + S < ring.count) ring.issue(ring.tile(i + S, false), stg, src);
                 }
-                if (i == 0) {
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(startb);  // release: the published threshold
+                stg += nscan;
+                if (stg >= S) {
+                    stg -= S;
+                    flip ^= 1u;
                 }
             }
         }
-        if (ring.count > 0) ring.parity ^= 1u << kStartBit;  // (every thread: one phase per call)
+        // every thread: the phases completed in this call (one per tile of each stage, one per
+        // chunk with a tile on its start barrier)
+        unsigned p = base;
+        for (int k = 0; k < S; k++)
+            if (k < ring.count) p ^= (unsigned)(((ring.count - 1 - k) / S + 1) & 1) << k;
+        for (int k = 0; k < nscan; k++)
+            if (k < ring.count) p ^= 1u << (kStartBit + k);
+        ring.parity = p;
         __syncthreads();
     } else {
         // data not 16-byte aligned: no staging; per tile the exact filter of the whole block,
@@ -768,22 +775,24 @@ __device__ void condat_block(const T* __restrict__ y, const T* __restrict__ xb, 
                     condat_slab<T, L1>(v, ok, (c * (TT / V) + ql) * V, r, st);
                 }
                 if (lane == 0 && st.nJ > 0) {
-                    s.tb = st.glo.bits;
-                    s.trd = condat_filter_rd(st);
+                    s.tb[0] = st.glo.bits;
+                    s.trd[0] = condat_filter_rd(st);
                 }
             }
             __syncthreads();
         }
     }
     parity = ring.parity;
-    // final loop of Alg. 2 over J~ (warp 0)
-    if (wid == 0 && st.nJ > 0) {
-        if (st.jt_end <= kJList) {
+    // final loop of Alg. 2 over J~ (scan warp k: its chunk)
+    if (wid < nscan && st.nJ > 0) {
+        if (st.jt_end <= st.cap) {
             __syncwarp();
             condat_final_list<L1>(st.list, st.jt_end, r, st);
         } else if (st.rs >= 0) {
-            const int64_t c0 = sp.lo / TT;
-            for (int64_t c = c0 + member; c * TT <= st.rs; c += nchunk) {
+            // the chunk's tiles up to the last restart: block tiles i = wid, wid + nscan, ...
+            for (int64_t i = wid; i < ring.count; i += nscan) {
+                const int64_t c = ring.tile(i, false);
+                if (c * TT > st.rs) break;
                 for (int sl = 0; sl < TT / V / 32; sl++) {
                     const int64_t q = c * (TT / V) + sl * 32 + lane;
                     T vals[V];
@@ -1159,13 +1168,24 @@ __device__ __forceinline__ void simplex_solve(const SimplexArgs& A, const Grp& g
         // a partition into many small chunks multiplies, and larger chunks give a better
         // lambda_0), at most one per block
         const int nchunk = (int)min((int64_t)G, max((int64_t)1, (n + A.condat_chunk - 1) / A.condat_chunk));
+        // chunks per block: the scan of a chunk is one warp's dependency chain, so a block that
+        // alone holds a short instance splits it over four scan warps.  Each doubling of the
+        // chunks loosens the union's lambda_0 by about one Newton step (measured on ragged FP32
+        // batches: 3.4 -> 4.5 -> 5.3 steps), which only instances of 4 to 15 tiles recover
+        // (0.37 -> 0.32 ms on 531 instances of 16K-64K elements; 1.8 -> 2.9 ms on 553 of
+        // 256K-1M)
+        int nscan = 1;
+        if (condat && aligned) {
+            const int64_t tiles = (n + condat_tile<T>() - 1) / condat_tile<T>();
+            nscan = A.scan_warps > 0 ? A.scan_warps : (G == 1 && tiles >= 4 && tiles < 16 ? 4 : 1);
+        }
         if (condat) {
             double Sw = 0.0;
             long long nJw = 0;
             condat_block<T, L1>(y, warm ? static_cast<const T*>(A.xbar) : nullptr, sp, aligned, r, gp.member,
-                                       nchunk, smem, bars, ring_parity, &gp.hdr->error, A.limit_ns, sacc, Sw, nJw);
-            q[1] = threadIdx.x == 0 ? Sw : 0.0;
-            q[2] = threadIdx.x == 0 ? (double)nJw : 0.0;
+                                nchunk, nscan, smem, bars, ring_parity, &gp.hdr->error, A.limit_ns, sacc, Sw, nJw);
+            q[1] = lane == 0 ? Sw : 0.0;  // each scan warp's chunk (zero elsewhere)
+            q[2] = lane == 0 ? (double)nJw : 0.0;
             passes++;
         }
         bad = sacc.bad;
@@ -1199,13 +1219,13 @@ __device__ __forceinline__ void simplex_solve(const SimplexArgs& A, const Grp& g
         if (condat && red[2] > 0.0) {
             lam0 = (r - red[1]) / red[2];  // eq. (lambdaJ) on the union of the chunks' J
             condat_start = true;
-            nchunks = (int)nchunk;
+            nchunks = (int)nchunk * nscan;
             tile = condat_tile<T>();
         } else if (condat) {
             // warm start with an empty J_+ (no element of the estimate's support): Sec. 3.3
             const double y1 = (double)y[sp.lo];
             lam0 = fmax(r / (double)n, L1 ? -fabs(y1) : -y1);
-            nchunks = (int)nchunk;
+            nchunks = (int)nchunk * nscan;
             tile = condat_tile<T>();
         } else if (A.init == CQK_INIT_GIVEN) {
             lam0 = fmax(A.lambda0, -red[3]);  // Alg. 4, line 1
@@ -1398,7 +1418,7 @@ __device__ void simplex_warp_solve(const SimplexArgs& A, const Span& sp, double*
         passes++;
     } else {
         CondatState st;
-        condat_init(st, list);
+        condat_init(st, list, kWarpList);
         for (int64_t q0 = (qlo / 32) * 32; q0 < qhi; q0 += 32) {
             const int64_t q = q0 + lane;
             T v[V];
@@ -1541,7 +1561,7 @@ __device__ __forceinline__ void init_condat_bars(uint64_t* bars) {
             mbar_init(&bars[k], 1);                           // the stage's bulk copy
             mbar_init(&bars[kCondatStages + k], NWARP - 1);  // the filtering warps (pipelined Alg. 2)
         }
-        mbar_init(&bars[2 * kCondatStages], 1);  // the scan's first tile (pipelined Alg. 2)
+        for (int k = 0; k < kMaxScan; k++) mbar_init(&bars[2 * kCondatStages + k], 1);  // scan k's first tile
         fence_barrier_init();
     }
     __syncthreads();
@@ -1550,7 +1570,7 @@ __device__ __forceinline__ void init_condat_bars(uint64_t* bars) {
 template <typename T, bool L1>
 __global__ void __launch_bounds__(NT, 2) simplex_kernel(SimplexArgs A) {
     extern __shared__ __align__(128) unsigned char dyn_smem[];
-    __shared__ uint64_t bars[2 * kCondatStages + 1];
+    __shared__ uint64_t bars[2 * kCondatStages + kMaxScan];
     unsigned parity = 0;
     init_condat_bars(bars);
     Grp gp;
@@ -1577,7 +1597,7 @@ struct SimplexBatchArgs {
 template <typename T, bool L1>
 __global__ void __launch_bounds__(NT, 2) simplex_batched_kernel(SimplexBatchArgs P) {
     extern __shared__ __align__(128) unsigned char dyn_smem[];
-    __shared__ uint64_t bars[2 * kCondatStages + 1];
+    __shared__ uint64_t bars[2 * kCondatStages + kMaxScan];
     unsigned parity = 0;
     init_condat_bars(bars);
     while (true) {
@@ -1643,6 +1663,7 @@ int launch_simplex_batched(int64_t B, const int64_t* offsets, int dtype, const v
     A.limit_ns = o.limit_ns;
     A.fault_inject = o.fault_inject;
     A.condat_chunk = o.condat_chunk;
+    A.scan_warps = o.scan_warps;
     A.xbar = o.xbar;
     const bool xbar_misaligned = o.init == CQK_INIT_WARM && ((uintptr_t)o.xbar % 16) != 0;
     A.aligned = ((((uintptr_t)y) | ((uintptr_t)x)) % 16 == 0 && !xbar_misaligned) ? 1 : 0;
@@ -1695,6 +1716,7 @@ int launch_simplex(int64_t n, int dtype, const void* y, double r, int l1, void* 
     A.limit_ns = o.limit_ns;
     A.fault_inject = o.fault_inject;
     A.condat_chunk = o.condat_chunk;
+    A.scan_warps = o.scan_warps;
     A.xbar = o.xbar;
     const bool xbar_misaligned = o.init == CQK_INIT_WARM && ((uintptr_t)o.xbar % 16) != 0;
     A.hdr = static_cast<WsHeader*>(ws);

@@ -16,11 +16,11 @@ pytestmark = pytest.mark.gpu
 DEV = "cuda"
 
 
-def _check(y, r, l1, dtype=torch.float64):
+def _check(y, r, l1, dtype=torch.float64, **kw):
     yt = torch.from_numpy(y).to(dtype)
     y64 = np64(yt)
     fn = api.project_l1 if l1 else api.project_simplex
-    x, info, _ = fn(yt.to(DEV), r, init=api.Init.CONDAT)
+    x, info, _ = fn(yt.to(DEV), r, init=api.Init.CONDAT, **kw)
     assert info.status == api.Status.OK, info
     if l1:
         lam, xstar, inside = oracle.project_l1(y64, r)
@@ -59,3 +59,43 @@ def test_condat_large_radius_and_scale(l1):
     y = rng.normal(size=300_000) * 1e30
     _check(y, 3e31, l1)
     _check(rng.uniform(size=300_000), 50.0, l1)
+
+
+@pytest.mark.parametrize("l1", [False, True])
+@pytest.mark.parametrize("scan_warps", [1, 2, 4])
+@pytest.mark.parametrize("n,blocks", [(9000, 1), (70001, 1), (300000, 3), (2_000_003, 0)])
+def test_condat_scan_warps_partition(n, blocks, scan_warps, l1):
+    # each block deals its tiles to scan_warps chunks: the partition has blocks * scan_warps
+    # chunks of round-robin tiles, which the oracle reproduces from info.nchunks
+    rng = np.random.default_rng(n + scan_warps)
+    y = rng.normal(size=n) * 2.0
+    for dtype in (torch.float64, torch.float32):
+        _check(y, 1.0, l1, dtype, scan_warps=scan_warps, max_blocks=blocks)
+
+
+def test_condat_scan_warps_batched():
+    lens = [9000, 1, 40000, 0, 70001, 517, 200000]
+    off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    n = int(off[-1])
+    y = np.random.default_rng(3).normal(size=n)
+    r = torch.ones(len(lens), dtype=torch.float64)
+    for l1 in (False, True):
+        fn = api.project_l1_batched if l1 else api.project_simplex_batched
+        for sw in (0, 1, 2, 4):
+            x, infos, _ = fn(torch.from_numpy(y).to(DEV), torch.from_numpy(off), r, init=api.Init.CONDAT,
+                             scan_warps=sw, warp_elems=-1)
+            xs = np64(x)
+            for k, m in enumerate(lens):
+                if m == 0:
+                    continue
+                lo, hi = int(off[k]), int(off[k + 1])
+                assert infos[k].status == api.Status.OK, (k, sw, infos[k])
+                if l1:
+                    lam, xstar, inside = oracle.project_l1(y[lo:hi], 1.0)
+                else:
+                    (lam, xstar), inside = oracle.project_simplex_sort(y[lo:hi], 1.0), False
+                assert_x_close(xs[lo:hi], xstar, torch.float64, f"instance {k} scan_warps {sw}")
+                if not inside:
+                    l0, S, C = oracle.condat_chunks(y[lo:hi], 1.0, infos[k].tile, infos[k].nchunks, l1=l1,
+                                                    shift=lo % infos[k].tile)
+                    assert math.isclose(infos[k].lambda0, l0, rel_tol=1e-13, abs_tol=1e-300), (k, sw)
