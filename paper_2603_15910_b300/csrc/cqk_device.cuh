@@ -209,6 +209,16 @@ __device__ __forceinline__ df split_f64_finite(double x) {
     return {fhi, flo};
 }
 
+// split_f64_finite for positive values inside the df operating range (no zero test)
+__device__ __forceinline__ df split_f64_pos(double x) {
+    const unsigned lo = (unsigned)__double2loint(x);
+    const unsigned hi = (unsigned)__double2hiint(x);
+    const unsigned fh = ((hi - (896u << 20)) << 3) | (lo >> 29);
+    const unsigned base = (fh & 0xFF800000u) - (23u << 23);
+    const float flo = __fsub_rn(__uint_as_float(base | ((lo >> 6) & 0x7FFFFFu)), __uint_as_float(base));
+    return {__uint_as_float(fh), flo};
+}
+
 // Lazily normalised df accumulator: the high part is kept exact with TwoSum, the low parts
 // are summed in float and folded in when the accumulator is flushed (a few dozen terms at
 // most), which costs 8 FP32 operations per term instead of the 11 of df_add.

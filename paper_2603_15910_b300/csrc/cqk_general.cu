@@ -64,22 +64,29 @@ struct GeneralArgs {
 constexpr int kFlushEvery = 8;  // sweep iterations (kGenU vectors each) between flushes
 constexpr int kGenU = 2;        // 16-byte vectors per array in flight per lane
 constexpr unsigned kFlagWide = 2u;  // some FP64 value lies outside the df operating range
+// absf: sum |b_i x_i| of the Newton passes after the first, where it only scales the tolerance
+// of stopping criterion 1: summed in float between flushes (relative error below 2^-19 with
+// kFlushEvery tiles of 4 elements per thread).  The stand-alone phi evaluation, the first
+// pass and the final pass (the reported sum) keep the double-float sum.
 struct EvalAcc {
     LazyDf phi, absbx, sfree;
+    float absf;
     double phi64, absbx64, sfree64, satl, satu;
     long long nfree;
     bool bad, wide;
     __device__ void init() {
         phi = absbx = sfree = LazyDf{0.0f, 0.0f};
+        absf = 0.0f;
         phi64 = absbx64 = sfree64 = satl = satu = 0.0;
         nfree = 0;
         bad = wide = false;
     }
     __device__ void flush() {
         phi64 += lazy_value(phi);
-        absbx64 += lazy_value(absbx);
+        absbx64 += lazy_value(absbx) + (double)absf;
         sfree64 += lazy_value(sfree);
         phi = absbx = sfree = LazyDf{0.0f, 0.0f};
+        absf = 0.0f;
     }
 };
 
@@ -234,8 +241,8 @@ __device__ __forceinline__ void eval_vec(const GeneralArgs& A, const T (&va)[Vec
                 df Ad, Bd, Dd, Ld, Ud;
                 if constexpr (FAST) {
                     Ad = split_f64_finite(a);
-                    Bd = split_f64_finite(b);
-                    Dd = split_f64_finite(d);
+                    Bd = split_f64_pos(b);  // b, d > 0 inside the range (checked in the first pass)
+                    Dd = split_f64_pos(d);
                     Ld = split_f64(l);
                     Ud = split_f64(u);
                 } else {
@@ -283,7 +290,8 @@ __device__ __forceinline__ void eval_vec(const GeneralArgs& A, const T (&va)[Vec
             fr[j] = cl.c == 0;
             if (!write_x) {
                 lazy_add(acc.phi, bx);
-                lazy_add(acc.absbx, bx.hi < 0.0f ? df_neg(bx) : bx);
+                if constexpr (FAST) acc.absf += fabsf(bx.hi);  // (a tolerance scale: see EvalAcc)
+                else lazy_add(acc.absbx, bx.hi < 0.0f ? df_neg(bx) : bx);
                 lazy_add(acc.sfree, fr[j] ? beta[j] : df_make(0.0f));
             }
             tiem |= ((cl.tieL && !cl.tieU) ? 1u : 0u) << (2 * j);
