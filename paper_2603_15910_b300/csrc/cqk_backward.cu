@@ -18,6 +18,7 @@
 #include <string.h>
 
 #include "cqk_batch.cuh"
+#include "cqk_stage.cuh"
 
 namespace cqk {
 namespace {
@@ -399,8 +400,170 @@ __device__ __forceinline__ void bwd_instance(const BwdArgs& A, const Grp& gp, in
     }
 }
 
+// The simplex adjoint with the forward mask on 16-byte aligned data: g streams through
+// kBwdStages shared-memory stages of 16 KB by bulk copies (tiles of the span dealt round robin
+// to the group's blocks), so that each block keeps 48 KB in flight instead of the few vectors
+// its registers hold.  Pass 1 sums g over F, pass 2 (tiles in reverse order, the last ones
+// still in L2) writes gy = g - mean_F(g) on F and 0 off F.  The arithmetic per element is the
+// one of bwd_instance.
+constexpr int kBwdStages = 4;
+constexpr size_t kBwdSmem = (size_t)kBwdStages * 16384;
+
+template <typename T>
+__device__ void bwd_simplex_staged(const BwdArgs& A, const Grp& gp, int64_t inst, T* smem, uint64_t* bars,
+                                   unsigned& parity) {
+    constexpr int V = VecOf<T>::V;
+    constexpr int TT = 16384 / (int)sizeof(T);
+    constexpr int VPT = TT / V / NT;  // vectors per thread and tile
+    constexpr int S = kBwdStages;
+    using VT = typename VecOf<T>::type;
+    static_assert(VPT * V * NT == TT, "tile layout");
+    __shared__ double sh[kPartialQ][NWARP];
+    __shared__ double bc[kPartialQ];
+    const Span sp = gp.sp;
+    const T* __restrict__ g = static_cast<const T*>(A.g);
+    const T* src[1] = {g};
+    TileRing<T, 1, TT> ring;
+    ring.setup(sp.lo, sp.hi, smem, bars, gp.member, gp.g);
+    ring.parity = parity;
+    int* err = gp.hdr ? &gp.hdr->error : nullptr;
+    int dummy_err = 0;
+    if (!err) err = &dummy_err;
+
+    // the V values of vector ql of tile c (stage when the bulk copy delivered it, else global)
+    auto vec_of = [&](const T* stage, int64_t c, int ql, int64_t sb0, int64_t sb1, T (&v)[V], bool (&ok)[V]) {
+        const int64_t q = c * (TT / V) + ql;
+        if (q * V >= sb0 && (q + 1) * V <= sb1) {
+            const VT w = reinterpret_cast<const VT*>(stage)[ql];
+#pragma unroll
+            for (int j = 0; j < V; j++) {
+                v[j] = reinterpret_cast<const T*>(&w)[j];
+                ok[j] = true;
+            }
+        } else {
+            load_vec<T>(g, sp, q, false, v, ok);
+        }
+    };
+    // one sweep over the block's tiles: f(stage, c, sb0, sb1, i, mask words) per tile, all
+    // threads; the mask words of a tile are loaded before its stage is waited for
+    auto sweep = [&](bool rev, auto&& f) {
+        if (threadIdx.x == 0)
+            for (int k = 0; k < S - 1; k++)
+                if (k < ring.count) ring.issue(ring.tile(k, rev), k, src);
+        int stg = 0;
+        for (int64_t i = 0; i < ring.count; i++, stg = stg + 1 == S ? 0 : stg + 1) {
+            if (threadIdx.x == 0 && i + S - 1 < ring.count) {
+                const int s2 = stg == 0 ? S - 1 : stg - 1;  // (i + S - 1) mod S
+                ring.issue(ring.tile(i + S - 1, rev), s2, src);
+            }
+            const int64_t c = ring.tile(i, rev);
+            uint32_t mw[VPT];
+#pragma unroll
+            for (int k = 0; k < VPT; k++) mw[k] = mask_word<T>(A, sp, c * (TT / V) + k * NT + (int)threadIdx.x);
+            mbar_wait(&ring.bar[stg], (ring.parity >> stg) & 1u, err, A.limit_ns, CQK_TIMEOUT);
+            ring.parity ^= 1u << stg;
+            f(ring.stage(stg, 0), c, ring.b0(c), ring.b1(c), i, mw);
+            __syncthreads();  // the stage is refilled only after every thread has read it
+        }
+    };
+
+    // ---- pass 1: sum_F g and |F|
+    LazyDf Sl{0.0f, 0.0f};
+    double S64 = 0.0, Q64 = 0.0;
+    long long nF = 0;
+    sweep(false, [&](const T* stage, int64_t c, int64_t sb0, int64_t sb1, int64_t i, const uint32_t (&mw)[VPT]) {
+        if ((i & 7) == 7) {
+            S64 += lazy_value(Sl);
+            Sl = LazyDf{0.0f, 0.0f};
+        }
+#pragma unroll
+        for (int k = 0; k < VPT; k++) {
+            const int ql = k * NT + (int)threadIdx.x;
+            const int64_t q = c * (TT / V) + ql;
+            T v[V];
+            bool ok[V];
+            vec_of(stage, c, ql, sb0, sb1, v, ok);
+            const unsigned fb = (mw[k] >> ((q * V) & 31)) & ((1u << V) - 1u);
+#pragma unroll
+            for (int j = 0; j < V; j++) {
+                if (!ok[j] || !((fb >> j) & 1u)) continue;
+                if (!in_df_range<T>(v[j])) {
+                    bwd_sum_exact((double)v[j], 0.0, 1.0, 1.0, kBwdSimplex, S64, Q64);
+                    continue;
+                }
+                lazy_add(Sl, to_df<T>(v[j]));
+                nF++;
+            }
+        }
+    });
+    double pv[2] = {lazy_value(Sl) + S64, (double)nF + Q64};
+    double red[2];
+    block_sum<2>(pv, sh);
+    write_partials<2>(gp.part, gp.member, gp.g, 0, pv);
+    const unsigned target = (unsigned)gp.g + (A.fault_inject ? 1u : 0u);
+    if (!group_barrier(gp, target, A.limit_ns, A.fault_inject != 0)) {
+        if (threadIdx.x == 0 && A.status) A.status[inst] = CQK_TIMEOUT;
+        parity = ring.parity;
+        return;
+    }
+    grid_reduce<2>(gp.part, gp.g, 0, -1, red, sh, bc);
+    const bool nondiff = !(red[1] > 0.0);
+    const double mu = nondiff ? 0.0 : red[0] / red[1];
+    const df M = df_from_f64(mu);
+    const bool par_ok = fabs(mu) <= 1.152921504606847e18;  // 2^60
+
+    // ---- pass 2: gy
+    T* __restrict__ gy = static_cast<T*>(A.ga);
+    sweep(true, [&](const T* stage, int64_t c, int64_t sb0, int64_t sb1, int64_t, const uint32_t (&mw)[VPT]) {
+#pragma unroll
+        for (int k = 0; k < VPT; k++) {
+            const int ql = k * NT + (int)threadIdx.x;
+            const int64_t q = c * (TT / V) + ql;
+            T v[V];
+            bool ok[V];
+            vec_of(stage, c, ql, sb0, sb1, v, ok);
+            const unsigned fb = (mw[k] >> ((q * V) & 31)) & ((1u << V) - 1u);
+            T oa[V];
+#pragma unroll
+            for (int j = 0; j < V; j++) {
+                const bool fr = (fb >> j) & 1u;
+                oa[j] = T(0);
+                if (!ok[j] || !fr) continue;
+                if (par_ok && in_df_range<T>(v[j])) {
+                    oa[j] = from_df<T>(df_add(to_df<T>(v[j]), df_neg(M)));
+                } else {
+                    double o5[5];
+                    bwd_map_exact((double)v[j], 0.0, 1.0, 1.0, true, false, mu, 0.0, kBwdSimplex, o5);
+                    oa[j] = (T)o5[0];
+                }
+            }
+            if (gy) store_vec<T>(gy, sp, q, A.aligned != 0, oa);
+        }
+    });
+    parity = ring.parity;
+    if (gp.member == 0 && threadIdx.x == 0) {
+        if (A.gr) A.gr[inst] = mu;
+        if (A.status) {
+            const int e = gp.hdr ? *(volatile int*)&gp.hdr->error : 0;
+            A.status[inst] = e ? e : (nondiff ? CQK_NONDIFF : CQK_OK);
+        }
+    }
+}
+
 template <typename T, int KIND, bool BATCHED, bool NOX>
 __global__ void __launch_bounds__(NT, 2) backward_kernel(BwdArgs A) {
+    // the staged simplex adjoint (NOX on aligned data): stages and their mbarriers
+    extern __shared__ __align__(128) unsigned char dyn_smem[];
+    __shared__ uint64_t bars[NOX ? kBwdStages : 1];
+    unsigned parity = 0;
+    const bool staged = NOX && A.aligned != 0;
+    if (NOX) {
+        if (threadIdx.x == 0) {
+            for (int k = 0; k < kBwdStages; k++) mbar_init(&bars[k], 1);
+            fence_barrier_init();
+        }
+        __syncthreads();
+    }
     if constexpr (!BATCHED) {
         Grp gp;
         gp.member = blockIdx.x;
@@ -408,7 +571,8 @@ __global__ void __launch_bounds__(NT, 2) backward_kernel(BwdArgs A) {
         gp.sp = Span{0, A.n};
         gp.hdr = A.hdr;
         gp.part = A.part;
-        bwd_instance<T, KIND, NOX>(A, gp, 0);
+        if (staged) bwd_simplex_staged<T>(A, gp, 0, reinterpret_cast<T*>(dyn_smem), bars, parity);
+        else bwd_instance<T, KIND, NOX>(A, gp, 0);
         return;
     } else {
         while (true) {
@@ -443,7 +607,8 @@ __global__ void __launch_bounds__(NT, 2) backward_kernel(BwdArgs A) {
                 }
                 continue;
             }
-            bwd_instance<T, KIND, NOX>(A, gp, sl.inst);
+            if (staged) bwd_simplex_staged<T>(A, gp, sl.inst, reinterpret_cast<T*>(dyn_smem), bars, parity);
+            else bwd_instance<T, KIND, NOX>(A, gp, sl.inst);
         }
     }
 }
@@ -497,13 +662,23 @@ int launch_backward(int kind, int64_t B, const int64_t* offsets, int64_t n, int 
                                      : pick_kernel<float, kBwdL1>(batched);
     }
     const int64_t vec = dtype == CQK_F64 ? 2 : 4;
+    // the staged simplex adjoint takes kBwdSmem of dynamic shared memory (requested for every
+    // NOX launch: the kernel decides on alignment at run time)
+    const size_t smem = nox ? kBwdSmem : 0;
     int grid;
     cudaError_t e;
+    if (smem) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) {
+            set_last_cuda_error(e);
+            return CQK_CUDA_ERROR;
+        }
+    }
     if (batched) {
         A.offsets = offsets;
         A.B = B;
         A.R = BatchRefs::at(ws, B);
-        grid = persistent_grid(kern, NT, 0, INT64_MAX / 2, o.max_blocks);
+        grid = persistent_grid(kern, NT, smem, INT64_MAX / 2, o.max_blocks);
         if (grid <= 0) return CQK_CUDA_ERROR;
         if ((int64_t)grid > B * kMaxGroup) grid = (int)(B * kMaxGroup);
         const int64_t per_block =
@@ -514,7 +689,7 @@ int launch_backward(int kind, int64_t B, const int64_t* offsets, int64_t n, int 
         A.n = n;
         A.hdr = static_cast<WsHeader*>(ws);
         A.part = reinterpret_cast<double*>(static_cast<char*>(ws) + sizeof(WsHeader));
-        grid = persistent_grid(kern, NT, 0, (n + vec - 1) / vec, o.max_blocks);
+        grid = persistent_grid(kern, NT, smem, (n + vec - 1) / vec, o.max_blocks);
         if (grid <= 0) return CQK_CUDA_ERROR;
         e = cudaMemsetAsync(ws, 0, sizeof(WsHeader), s);
         if (e != cudaSuccess) {
@@ -523,7 +698,7 @@ int launch_backward(int kind, int64_t B, const int64_t* offsets, int64_t n, int 
         }
     }
     void* args[] = {&A};
-    e = cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(NT), args, 0, s);
+    e = cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(NT), args, smem, s);
     if (e != cudaSuccess) {
         set_last_cuda_error(e);
         return CQK_CUDA_ERROR;
