@@ -64,6 +64,7 @@ struct GeneralArgs {
 constexpr int kFlushEvery = 8;  // sweep iterations (kGenU vectors each) between flushes
 constexpr int kGenU = 2;        // 16-byte vectors per array in flight per lane
 constexpr unsigned kFlagWide = 2u;  // some FP64 value lies outside the df operating range
+constexpr unsigned kFlagLuInf = 4u;  // some bound l_i or u_i is infinite
 // absf: sum |b_i x_i| of the Newton passes after the first, where it only scales the tolerance
 // of stopping criterion 1: summed in float between flushes (relative error below 2^-19 with
 // kFlushEvery tiles of 4 elements per thread).  The stand-alone phi evaluation, the first
@@ -73,13 +74,13 @@ struct EvalAcc {
     float absf;
     double phi64, absbx64, sfree64, satl, satu;
     long long nfree;
-    bool bad, wide;
+    bool bad, wide, luinf;
     __device__ void init() {
         phi = absbx = sfree = LazyDf{0.0f, 0.0f};
         absf = 0.0f;
         phi64 = absbx64 = sfree64 = satl = satu = 0.0;
         nfree = 0;
-        bad = wide = false;
+        bad = wide = luinf = false;
     }
     __device__ void flush() {
         phi64 += lazy_value(phi);
@@ -129,6 +130,7 @@ __device__ __noinline__ double elem_f64_exact(double a, double b, double d, doub
 // t = v/d, and the status of x_i(lambda) read off t against l, u (equivalent to v against
 // d l, d u for d > 0) with the tie band of the file header, scaled to x.
 // Returns x; bx = b x, beta = b^2/d.
+template <bool FIN>
 __device__ __forceinline__ df elem_df(df A, df B, df D, df Lo, df Up, df Lm, Cls& cl, df& bx, df& beta) {
     const df p = two_prod(Lm.hi, B.hi);
     const float e = fmaf(Lm.hi, B.lo, fmaf(Lm.lo, B.hi, p.lo));
@@ -138,7 +140,7 @@ __device__ __forceinline__ df elem_df(df A, df B, df D, df Lo, df Up, df Lm, Cls
     const float res = fmaf(-D.lo, r0, fmaf(-D.hi, r0, 1.0f));
     const df invd = fast_two_sum(r0, __fmul_rn(r0, res));
     const df t = df_mul(v, invd);
-    const bool linf = isinf(Lo.hi), uinf = isinf(Up.hi);
+    const bool linf = !FIN && isinf(Lo.hi), uinf = !FIN && isinf(Up.hi);  // FIN: finite bounds
     const float dL = __fadd_rn(__fsub_rn(t.hi, Lo.hi), __fsub_rn(t.lo, Lo.lo));
     const float dU = __fadd_rn(__fsub_rn(t.hi, Up.hi), __fsub_rn(t.lo, Up.lo));
     const float sc = __fmul_rn(__fadd_rn(fabsf(A.hi), fabsf(p.hi)), r0);  // (|a| + |lambda b|)/d
@@ -180,6 +182,7 @@ __device__ __forceinline__ bool bad_elem_f(float a, float b, float d, float l, f
 // MUFU reciprocal and one correction (~1 ulp); the status is read off t against l, u with a
 // tie band of 2^-20 relative (the float rounding of t); b x by TwoProd; b^2/d in float.
 constexpr float kTieRel32 = 9.5367431640625e-07f;  // 2^-20
+template <bool FIN>
 __device__ __forceinline__ float elem_f32(float a, float b, float d, float l, float u, df Lm, Cls& cl, df& bx,
                                           float& beta) {
     const df p = two_prod(Lm.hi, b);
@@ -189,7 +192,7 @@ __device__ __forceinline__ float elem_f32(float a, float b, float d, float l, fl
     const float r0 = rcp_approx(d);
     float t = __fmul_rn(vh, r0);
     t = fmaf(fmaf(-t, d, vh), r0, t);
-    const bool linf = isinf(l), uinf = isinf(u);
+    const bool linf = !FIN && isinf(l), uinf = !FIN && isinf(u);
     const float dL = __fsub_rn(t, l), dU = __fsub_rn(t, u);
     const float sc = __fmul_rn(__fadd_rn(fabsf(a), fabsf(p.hi)), r0);
     const bool tieL = !linf && fabsf(dL) <= kTieRel32 * (sc + fabsf(l));
@@ -214,7 +217,7 @@ __device__ __forceinline__ float elem_f32(float a, float b, float d, float l, fl
 // warp's first vector (a multiple of 32).
 // FAST: every FP64 value is known to be valid and inside the df operating range (checked in
 // the first pass), so the per-element checks are skipped.
-template <typename T, bool FAST>
+template <typename T, bool FAST, bool FIN>
 __device__ __forceinline__ void eval_vec(const GeneralArgs& A, const T (&va)[VecOf<T>::V], const T (&vb)[VecOf<T>::V],
                                          const T (&vd)[VecOf<T>::V], const T (&vl)[VecOf<T>::V],
                                          const T (&vu)[VecOf<T>::V], const bool (&ok)[VecOf<T>::V], int64_t q,
@@ -243,8 +246,8 @@ __device__ __forceinline__ void eval_vec(const GeneralArgs& A, const T (&va)[Vec
                     Ad = split_f64_finite(a);
                     Bd = split_f64_pos(b);  // b, d > 0 inside the range (checked in the first pass)
                     Dd = split_f64_pos(d);
-                    Ld = split_f64(l);
-                    Ud = split_f64(u);
+                    Ld = FIN ? split_f64_finite(l) : split_f64(l);  // FIN: no infinite bound (first pass)
+                    Ud = FIN ? split_f64_finite(u) : split_f64(u);
                 } else {
                     // operating range by exponent-field tests: b, d positive in [2^-60, 2^60];
                     // a 0 or in range; l, u 0, +-inf or in range.  In-range values are finite and
@@ -260,6 +263,7 @@ __device__ __forceinline__ void eval_vec(const GeneralArgs& A, const T (&va)[Vec
                     const bool inr = lam_ok && ((hb >> 20) - 963u) <= 120u && ((hd >> 20) - 963u) <= 120u &&
                                      (rng(ha) || zero(ha, la)) && (rng(hl) || zero(hl, ll) || inf(hl, ll)) &&
                                      (rng(hu) || zero(hu, lu) || inf(hu, lu));
+                    acc.luinf |= inf(hl, ll) || inf(hu, lu);
                     if (!inr) {
                         widem |= 1u << j;
                         acc.wide = true;
@@ -272,7 +276,7 @@ __device__ __forceinline__ void eval_vec(const GeneralArgs& A, const T (&va)[Vec
                     Ud = split_f64(u);
                     if (check) acc.bad |= df_lt(Ud, Ld);
                 }
-                const df xv = elem_df(Ad, Bd, Dd, Ld, Ud, Lm, cl, bx, beta[j]);
+                const df xv = elem_df<FIN>(Ad, Bd, Dd, Ld, Ud, Lm, cl, bx, beta[j]);
                 if (write_x) {
                     xo[j] = cl.c == 1 ? l : (cl.c == 2 ? u : 0.0);
                     freem |= (cl.c == 0 ? 1u : 0u) << j;
@@ -283,8 +287,9 @@ __device__ __forceinline__ void eval_vec(const GeneralArgs& A, const T (&va)[Vec
                 }
             } else {
                 if (!FAST && check) acc.bad |= bad_elem_f(a, b, d, l, u);
+                if (!FAST) acc.luinf |= isinf(l) || isinf(u);
                 float bt;
-                xo[j] = elem_f32(a, b, d, l, u, Lm, cl, bx, bt);
+                xo[j] = elem_f32<FIN>(a, b, d, l, u, Lm, cl, bx, bt);
                 beta[j] = df_make(bt);
             }
             fr[j] = cl.c == 0;
@@ -349,7 +354,7 @@ __device__ __forceinline__ void eval_vec(const GeneralArgs& A, const T (&va)[Vec
 }
 
 // ---- one pass over all elements with plain loads (arrays not 16-byte aligned)
-template <typename T, bool FAST>
+template <typename T, bool FAST, bool FIN>
 __device__ __forceinline__ void eval_pass_plain(const GeneralArgs& A, const Grp& gp, double lam, bool write_x,
                                                 bool check, bool rev, EvalAcc& acc) {
     constexpr int V = VecOf<T>::V;
@@ -385,7 +390,7 @@ __device__ __forceinline__ void eval_pass_plain(const GeneralArgs& A, const Grp&
         }
 #pragma unroll
         for (int w = 0; w < U; w++)
-            eval_vec<T, FAST>(A, va[w], vb[w], vd[w], vl[w], vu[w], ok[w], base + w * 32 + lane, base + w * 32, lam, Lm,
+            eval_vec<T, FAST, FIN>(A, va[w], vb[w], vd[w], vl[w], vu[w], ok[w], base + w * 32 + lane, base + w * 32, lam, Lm,
                               lam_ok, write_x, check, acc, sp);
     }
 }
@@ -394,7 +399,7 @@ __device__ __forceinline__ void eval_pass_plain(const GeneralArgs& A, const Grp&
 template <typename T>
 __host__ __device__ constexpr int stage_tile() { return 8192 / (int)sizeof(T); }  // elements per array per stage
 
-template <typename T, bool FAST>
+template <typename T, bool FAST, bool FIN>
 __device__ __forceinline__ bool eval_pass_staged(const GeneralArgs& A, const Grp& gp, double lam, bool write_x,
                                                  bool check, bool rev, EvalAcc& acc, T* smem, uint64_t* bars,
                                                  unsigned& parity, int* err) {
@@ -452,7 +457,7 @@ __device__ __forceinline__ bool eval_pass_staged(const GeneralArgs& A, const Grp
                 load_vec<T>(src[3], sp, q, false, vl, ok);
                 load_vec<T>(src[4], sp, q, false, vu, ok);
             }
-            eval_vec<T, FAST>(A, va, vb, vd, vl, vu, ok, q, qw, lam, Lm, lam_ok, write_x, check, acc, sp);
+            eval_vec<T, FAST, FIN>(A, va, vb, vd, vl, vu, ok, q, qw, lam, Lm, lam_ok, write_x, check, acc, sp);
         }
         __syncthreads();  // the stage is refilled only after every thread has read it
     }
@@ -461,12 +466,12 @@ __device__ __forceinline__ bool eval_pass_staged(const GeneralArgs& A, const Grp
 }
 
 // one pass over all elements, staged or plain
-template <typename T, bool FAST>
+template <typename T, bool FAST, bool FIN = false>
 __device__ __forceinline__ bool eval_pass(const GeneralArgs& A, const Grp& gp, double lam, bool write_x, bool check,
                                           bool rev, EvalAcc& acc, T* smem, uint64_t* bars, unsigned& parity,
                                           int* err) {
-    if (A.staged) return eval_pass_staged<T, FAST>(A, gp, lam, write_x, check, rev, acc, smem, bars, parity, err);
-    eval_pass_plain<T, FAST>(A, gp, lam, write_x, check, rev, acc);
+    if (A.staged) return eval_pass_staged<T, FAST, FIN>(A, gp, lam, write_x, check, rev, acc, smem, bars, parity, err);
+    eval_pass_plain<T, FAST, FIN>(A, gp, lam, write_x, check, rev, acc);
     return true;
 }
 
@@ -792,6 +797,7 @@ __device__ __forceinline__ void general_solve(const GeneralArgs& A, const Grp& g
     int status = CQK_OK, stop = CQK_STOP_NONE, k = 0;
     bool bad_input = false;
     bool wide_data = true;  // until the first pass has checked every value
+    bool fin_data = false;  // every bound finite (known after the first pass)
     for (k = 0;; k++) {
         if (k >= A.max_iter) {
             status = CQK_MAXITER;
@@ -799,12 +805,16 @@ __device__ __forceinline__ void general_solve(const GeneralArgs& A, const Grp& g
         }
         EvalAcc acc;
         acc.init();
-        if (k > 0 && !wide_data) eval_pass<T, true>(A, gp, lam, false, false, (k & 1) == 1, acc, smem, ring_bars, ring_parity, err);
+        if (k > 0 && !wide_data && fin_data)
+            eval_pass<T, true, true>(A, gp, lam, false, false, (k & 1) == 1, acc, smem, ring_bars, ring_parity, err);
+        else if (k > 0 && !wide_data)
+            eval_pass<T, true>(A, gp, lam, false, false, (k & 1) == 1, acc, smem, ring_bars, ring_parity, err);
         else eval_pass<T, false>(A, gp, lam, false, k == 0 && A.validate, (k & 1) == 1, acc, smem, ring_bars, ring_parity, err);
         acc.flush();
         passes++;
         if (__any_sync(0xffffffffu, acc.bad) && (threadIdx.x & 31) == 0) atomicOr(&gp.hdr->flags, kFlagBadInput);
         if (k == 0 && __any_sync(0xffffffffu, acc.wide) && (threadIdx.x & 31) == 0) atomicOr(&gp.hdr->flags, kFlagWide);
+        if (k == 0 && __any_sync(0xffffffffu, acc.luinf) && (threadIdx.x & 31) == 0) atomicOr(&gp.hdr->flags, kFlagLuInf);
         double pv[5] = {acc.phi64, acc.sfree64, acc.satl, acc.satu, acc.absbx64};
         block_sum<5>(pv, sh);
         write_partials<5>(gp.part, gp.member, G, par, pv);
@@ -812,7 +822,10 @@ __device__ __forceinline__ void general_solve(const GeneralArgs& A, const Grp& g
         double red[5];
         grid_reduce<5>(gp.part, G, par, -1, red, sh, bc);
         par ^= 1;
-        if (k == 0) wide_data = (__ldcg(&gp.hdr->flags) & kFlagWide) != 0;
+        if (k == 0) {
+            wide_data = (__ldcg(&gp.hdr->flags) & kFlagWide) != 0;
+            fin_data = (__ldcg(&gp.hdr->flags) & kFlagLuInf) == 0;
+        }
         if (k == 0 && A.validate && (__ldcg(&gp.hdr->flags) & kFlagBadInput)) {
             bad_input = true;
             status = CQK_BAD_INPUT;
@@ -930,7 +943,10 @@ __device__ __forceinline__ void general_solve(const GeneralArgs& A, const Grp& g
     EvalAcc acc;
     acc.init();
     if (!bad_input && status != CQK_INFEASIBLE) {
-        if (!wide_data) eval_pass<T, true>(A, gp, final_lam, true, false, (k & 1) == 1, acc, smem, ring_bars, ring_parity, err);
+        if (!wide_data && fin_data)
+            eval_pass<T, true, true>(A, gp, final_lam, true, false, (k & 1) == 1, acc, smem, ring_bars, ring_parity, err);
+        else if (!wide_data)
+            eval_pass<T, true>(A, gp, final_lam, true, false, (k & 1) == 1, acc, smem, ring_bars, ring_parity, err);
         else eval_pass<T, false>(A, gp, final_lam, true, false, (k & 1) == 1, acc, smem, ring_bars, ring_parity, err);
         passes++;
     }
