@@ -8,9 +8,9 @@
 //
 //   pass 0   start:  CQK_INIT_FORMULA  sum y and max y (l1: |y|) -> lambda_0 of
 //                                      eq. (CQKlambda0), clamped by line 1 of Alg. 4
-//                    CQK_INIT_CONDAT   Alg. 2 on every block's chunk (exact, see
-//                                      condat_block); lambda_0 from eq. (lambdaJ) on the
-//                                      union of the J's (Sec. 4)
+//                    CQK_INIT_CONDAT   Alg. 2 on every chunk of a partition by tiles (exact,
+//                                      see condat_block); lambda_0 from eq. (lambdaJ) on
+//                                      the union of the J's (Sec. 4)
 //   pass k   phi(lambda_k) = sum_{y_i > -lambda_k} (y_i + lambda_k),
 //            phi'_- = #{y_i > -lambda_k}, phi'_+ = #{y_i >= -lambda_k}
 //            (eq. (opt), eq. (phideriv) specialised as in the proof of Theorem 3.1)
@@ -112,24 +112,25 @@ __device__ __forceinline__ double sum_max(const SumAcc& a) {
     else return (double)a.mxf;
 }
 
-// ---- Alg. 2 on one block's chunk ----------------------------------------------------------
-// The chunk of block m (of W chunk blocks) is the set of tiles c = c0 + m, c0 + m + W, ...;
-// tile c holds elements [c*TILE, (c+1)*TILE) (16 KB), scanned in increasing index order.  The
-// tiles stream into shared memory by bulk copies (kCondatStages stages, bounded waits).
+// ---- Alg. 2 per chunk ---------------------------------------------------------------------
+// Tile c holds elements [c*TILE, (c+1)*TILE) (16 KB); the span's tiles are dealt round robin to
+// the chunks (W = blocks x scan warps per block), and each chunk is scanned in increasing index
+// order.  The tiles stream into shared memory by bulk copies (kCondatStages stages, bounded
+// waits).
 //
 // Exactness: both branches of the first loop of Alg. 2 lower lambda (adding j with
 // y_j + lambda > 0 gives lambda - (y_j + lambda)/(|J|+1); a restart gives r - y_j, below the
 // rejected lambda_{J u {j}}), so once J is started an element that fails the test fails it
-// for the rest of the scan.  All threads of the block therefore filter the tile with the
-// threshold of the multiplier current at the start of the tile (a superset of the elements
-// the scan can accept) and warp 0 runs the sequential scan over the passing elements only,
-// in index order: it takes the first passing element with the scalar update (the same FP64
-// operations as a sequential scan), re-tests the later ones, and publishes the new
+// for the rest of the scan.  A filter with any threshold the scan has already reached
+// therefore passes a superset of the elements the scan can accept: the filter warps test each
+// tile against the threshold the chunk's scan last published, and the chunk's scan warp runs
+// the sequential scan over the passing elements only, in index order: it takes the first
+// passing element with the scalar update, re-tests the later ones, and publishes the new
 // threshold.  Before J is started every element passes (the first element of the chunk
 // starts J unconditionally).  The final loop of Alg. 2 over J~ visits, in order, the elements
 // of J~ that pass the test with the current lambda.  J~ is the set of values accepted before
-// the last restart; warp 0 keeps every accepted value in acceptance (= index) order, so the
-// loop runs over that list.  When J~ outgrows the list, the loop is a re-scan of the chunk
+// the last restart; the scan warp keeps every accepted value in acceptance (= index) order, so
+// the loop runs over that list.  When J~ outgrows the list, the loop is a re-scan of the chunk
 // prefix before the last restart with the same test instead: every element there that is
 // not in J~ failed the test with a larger lambda and fails it again.
 template <typename T, bool L1>
