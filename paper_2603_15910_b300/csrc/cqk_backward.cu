@@ -14,7 +14,9 @@
 // map is not differentiable in r; mu = 0 and the status is CQK_NONDIFF.
 //
 // Two passes per instance: a map-reduce for (sum_F b g/d, Q), a group barrier, and a map
-// that writes the requested gradients.  Arithmetic is FP64 for both storage types.
+// that writes the requested gradients.  Arithmetic: double-float (~2^-44 relative) with an
+// exact FP64 path for values outside its range, for both storage types.  The simplex adjoint
+// with the forward mask streams g through shared-memory stages (bwd_simplex_staged).
 #include <string.h>
 
 #include "cqk_batch.cuh"

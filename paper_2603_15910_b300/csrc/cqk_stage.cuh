@@ -1,10 +1,11 @@
 // cqk_stage.cuh -- bulk-copy (TMA) staging of contiguous tiles into shared memory.
 //
-// A block walks its tiles (tile c = blockIdx.x + i*gridDim.x) with a ring of kStages shared
-// memory stages.  Thread 0 issues one cp.async.bulk per array and tile, completing on the
-// stage's mbarrier; the block computes on tile i while tile i + kStages - 1 is in flight.
-// This keeps the memory system busy during the long double-float compute phase of the
-// general map-reduce, which plain loads (consumed right after issue) could not.
+// A block of a group walks its tiles (tile c = first tile of the span + member + i*g) with a
+// ring of shared-memory stages.  One thread issues one cp.async.bulk per array and tile,
+// completing on the stage's mbarrier; the block computes on tile i while the next tiles are
+// in flight.  This keeps the memory system busy during the long double-float compute phase
+// of the general map-reduce, the scan of the Alg. 2 start and the simplex adjoint, which
+// plain loads (consumed right after issue, held in registers) could not.
 //
 // Rules kept here: every bulk copy starts and ends on 16-byte boundaries (arrays must be
 // 16-byte aligned; a tile's tail that is not a multiple of 16 bytes is read with ordinary
