@@ -63,7 +63,7 @@ def test_condat_large_radius_and_scale(l1):
 
 @pytest.mark.parametrize("l1", [False, True])
 @pytest.mark.parametrize("scan_warps", [1, 2, 4])
-@pytest.mark.parametrize("n,blocks", [(9000, 1), (70001, 1), (300000, 3), (2_000_003, 0)])
+@pytest.mark.parametrize("n,blocks", [(100, 1), (3000, 1), (9000, 1), (70001, 1), (300000, 3), (2_000_003, 0)])
 def test_condat_scan_warps_partition(n, blocks, scan_warps, l1):
     # each block deals its tiles to scan_warps chunks: the partition has blocks * scan_warps
     # chunks of round-robin tiles, which the oracle reproduces from info.nchunks
@@ -99,3 +99,18 @@ def test_condat_scan_warps_batched():
                     l0, S, C = oracle.condat_chunks(y[lo:hi], 1.0, infos[k].tile, infos[k].nchunks, l1=l1,
                                                     shift=lo % infos[k].tile)
                     assert math.isclose(infos[k].lambda0, l0, rel_tol=1e-13, abs_tol=1e-300), (k, sw)
+
+
+@pytest.mark.parametrize("scan_warps", [2, 4])
+def test_condat_scan_warps_warm_start(scan_warps):
+    # the warm start's support filter with several chunks per block
+    n = 150001
+    y = np.random.default_rng(21).normal(size=n)
+    lam, xs = oracle.project_simplex_sort(y + 0.05 * np.random.default_rng(3).normal(size=n), 1.0)
+    xbar = torch.from_numpy(xs).to(DEV)
+    x, info, _ = api.project_simplex(torch.from_numpy(y).to(DEV), 1.0, init=api.Init.WARM, xbar=xbar,
+                                     scan_warps=scan_warps, max_blocks=1)
+    assert info.status == api.Status.OK
+    assert_x_close(np64(x), oracle.project_simplex_sort(y, 1.0)[1], torch.float64)
+    l0, S, C = oracle.condat_chunks_warm(y, xs, 1.0, info.tile, info.nchunks)
+    assert math.isclose(info.lambda0, l0, rel_tol=1e-13, abs_tol=1e-15), (info.lambda0, l0, info.nchunks)
