@@ -184,16 +184,23 @@ class ClockSampler:
 
 # ------------------------------------------------------------------------------ our arm
 def kernel_sources_sha256():
+    """Hash of the kernel sources with comments and blank space removed: a profile's counters
+    stay valid across edits of comments only, and not across any change of code."""
     import glob
     import hashlib
+    import re
     pkg = os.path.join(ROOT, "paper_2603_15910_b300", "csrc")
     files = sorted(glob.glob(os.path.join(pkg, "*.cu")) + glob.glob(os.path.join(pkg, "*.cuh")) +
                    glob.glob(os.path.join(pkg, "*.h"))) + [os.path.join(ROOT, "include", "cqk.h")]
+    # comments (outside string literals) and runs of blank space
+    token = re.compile(r'"(?:\\.|[^"\\])*"|//[^\n]*|/\*.*?\*/|\s+', re.S)
     h = hashlib.sha256()
     for f in files:
         h.update(os.path.basename(f).encode())
-        with open(f, "rb") as fh:
-            h.update(fh.read())
+        with open(f, encoding="utf-8") as fh:
+            src = fh.read()
+        code = token.sub(lambda m: m.group(0) if m.group(0).startswith('"') else " ", src)
+        h.update(code.encode())
     return h.hexdigest()
 
 
