@@ -200,7 +200,7 @@ def kernel_sources_sha256():
         with open(f, encoding="utf-8") as fh:
             src = fh.read()
         code = token.sub(lambda m: m.group(0) if m.group(0).startswith('"') else " ", src)
-        h.update(code.encode())
+        h.update(re.sub(" +", " ", code).encode())
     return h.hexdigest()
 
 
