@@ -178,9 +178,16 @@ struct CondatShared {
 // the restart test lambda < r - y — is taken from the product when it holds for every value
 // within kLamUlps units of it (integer compares of order keys), and from the exact quotient
 // otherwise (out of line, rare).  The decisions, hence J, J~, |J| and S, are those of the
-// FP64 scan.  (A double-float version of the step measured ~800 cycles in one warp, an FP64
-// one with a correctly rounded reciprocal ~1160.)
+// FP64 scan.  The test thresholds are kept as order keys (klo, khi): v > c for every c within
+// the margin iff key(v) > khi, and v <= c for all of them iff key(v) <= klo, since for any two
+// bit patterns v > c (FP64, c != -0) iff key(v) > key(c).  On the critical path of one step
+// are then two FP64 operations (t, then the product) and a few integer ones; S + y and
+// r - (S + y) are formed beside them, before the decision.  (A double-float version of the
+// step measured ~800 cycles in one warp, an FP64 one with a correctly rounded reciprocal
+// ~1160.)
 constexpr long long kLamUlps = 512;
+constexpr long long kKeyNegInf = -0x7FF0000000000000ll - 1;  // order_key(-inf)
+constexpr long long kKeyPosInf = 0x7FF0000000000000ll;       // order_key(+inf)
 
 struct CondatState {
     double S;     // the FP64 sum of J in scan order
@@ -192,7 +199,7 @@ struct CondatState {
     // approximation, within kLamUlps of the key of lambda (exact when en == 0)
     double t;
     long long en, lk;
-    GtThreshold glo, ghi;  // v <= glo: certainly fails; v > ghi: certainly passes
+    long long klo, khi;  // key(v) <= klo: v certainly fails; key(v) > khi: certainly passes
     double* list;  // accepted values in acceptance order (the first cap of them)
     int cap, cnt, jt_end;
 };
@@ -206,24 +213,37 @@ __device__ __forceinline__ void condat_init(CondatState& st, double* list, int c
     st.t = 0.0;
     st.en = 0;
     st.lk = 0;
-    st.glo = make_gt(-INFINITY);  // before J starts every element passes
-    st.ghi = make_gt(-INFINITY);
+    st.klo = kKeyNegInf;  // before J starts every element passes
+    st.khi = kKeyNegInf;
     st.list = list;
     st.cap = cap;
     st.cnt = 0;
     st.jt_end = 0;
 }
 
-// ~1/n for 1 <= n < 2^24: the float reciprocal and one Newton correction (error below
-// 2^-46 relative), as a double (the float parts converted on the integer pipe)
+// 1/k correctly rounded for 1 <= k < kRecipN (entry 0 unused), folded by the compiler from
+// IEEE division; read with a warp-uniform index (constant cache broadcast)
+constexpr int kRecipN = 4096;
+struct RecipTable {
+    double v[kRecipN];
+    constexpr RecipTable() : v() {
+        for (int k = 1; k < kRecipN; k++) v[k] = 1.0 / (double)k;
+    }
+};
+__constant__ RecipTable kRecip = RecipTable();
+
+// ~1/n for 1 <= n < 2^24 (relative error below 2^-46): the table, else the float reciprocal
+// and one Newton correction as a double (the float parts converted on the integer pipe)
 __device__ __forceinline__ double condat_recip(long long n) {
+    if (n < kRecipN) return kRecip.v[n];
     const float nf = (float)(int)n;
     const float r0 = __frcp_rn(nf);
     const float e0 = fmaf(-nf, r0, 1.0f);
     return f32_to_f64_bits(r0) + f32_to_f64_bits(__fmul_rn(r0, e0));
 }
 
-// the thresholds of the tests from the key of lambda, +-m keys (l1: c = max{0, -lambda})
+// the keys of the test thresholds from the key of lambda, +-m keys (l1: c = max{0, -lambda});
+// the key -1 (c = -0) becomes the key of +0, as FP64 compares
 template <bool L1>
 __device__ __forceinline__ void condat_thresholds(CondatState& st, long long m) {
     // c = -lambda: key(-x) = -key(x) - 1; the larger keys of lambda give the smaller c
@@ -231,9 +251,18 @@ __device__ __forceinline__ void condat_thresholds(CondatState& st, long long m) 
     if (L1) {
         klo = klo < 0 ? 0 : klo;
         khi = khi < 0 ? 0 : khi;
+    } else {
+        klo = klo == -1 ? 0 : klo;
+        khi = khi == -1 ? 0 : khi;
     }
-    st.glo = make_gt(from_order_key(klo));
-    st.ghi = make_gt(from_order_key(khi));
+    st.klo = klo;
+    st.khi = khi;
+}
+
+// the bit pattern of the threshold klo (a GtThreshold for the block filters)
+__device__ __forceinline__ unsigned long long condat_lo_bits(const CondatState& st) {
+    const long long k = st.klo;
+    return k >= 0 ? (unsigned long long)k : 0x8000000000000000ull - (unsigned long long)(k + 1);
 }
 
 // the approximation's neighbourhood stays inside the finite range (else FP64 decides)
@@ -248,8 +277,8 @@ __device__ __forceinline__ void condat_set_lambda(CondatState& st, double lam_ap
     if (st.en == 0) {
         condat_thresholds<L1>(st, 0);
     } else if (!condat_lam_ok(lam_approx) || st.en >= (1ll << 24)) {  // no certain decision
-        st.glo = make_gt(-INFINITY);
-        st.ghi = make_gt(INFINITY);
+        st.klo = kKeyNegInf;
+        st.khi = kKeyPosInf;
     } else {
         condat_thresholds<L1>(st, kLamUlps);
     }
@@ -271,10 +300,10 @@ __device__ __noinline__ bool condat_exact_less(double t, long long en, double rm
 // the test v > c(lambda) of the FP64 scan (v = y_j, l1: |y_j|)
 template <bool L1>
 __device__ __forceinline__ bool condat_gt(double v, const CondatState& st, double r) {
-    const unsigned long long vb = opaque_bits(v);
-    if (gt_bits(vb, st.ghi)) return true;
-    if (!gt_bits(vb, st.glo)) return false;
-    return condat_exact_gt<L1>(vb, st.t, st.en);  // rare
+    const long long kv = order_key(v);
+    if (kv > st.khi) return true;
+    if (kv <= st.klo) return false;
+    return condat_exact_gt<L1>(opaque_bits(v), st.t, st.en);  // rare
 }
 
 __device__ __forceinline__ void condat_record(CondatState& st, double v) {
@@ -301,6 +330,8 @@ __device__ __forceinline__ void condat_take(CondatState& st, double r, double y,
     const double t = st.rmS - y;
     const double lam = t * st.w1;
     const double rmy = r - y;
+    const double S1 = st.S + y;  // the addition's S and r - S, beside the decision
+    const double rmS1 = r - S1;
     const double w2 = condat_recip(st.nJ + 2);  // for the step after an addition
     const long long lk = order_key(lam), ky = order_key(rmy);
     // restart test lambda < r - y, from the approximation unless within its uncertainty
@@ -310,8 +341,8 @@ __device__ __forceinline__ void condat_take(CondatState& st, double r, double y,
     else if (sure && lk - kLamUlps >= ky) acc = false;
     else acc = condat_exact_less(t, st.nJ + 1, rmy);  // rare
     if (acc) {
-        st.S += y;
-        st.rmS = r - st.S;
+        st.S = S1;
+        st.rmS = rmS1;
         st.nJ += 1;
         st.w1 = w2;
         st.t = t;
@@ -339,94 +370,152 @@ __device__ __forceinline__ void condat_add(CondatState& st, double r, double y) 
 }
 
 // the block filter's threshold for FP32 data: a float at or below every c the scan can still
-// use (the FP64 data take the bit pattern st.glo)
+// use (the FP64 data take the bit pattern of klo)
 __device__ __forceinline__ float condat_filter_rd(const CondatState& st) {
-    return __double2float_rd(__longlong_as_double((long long)st.glo.bits));
+    return __double2float_rd(__longlong_as_double((long long)condat_lo_bits(st)));
+}
+
+// The next survivor in index order (lane, j) of the masks m[j] (warp-uniform): its lane and
+// j, and the bit cleared; false when none is left.
+template <int V>
+__device__ __forceinline__ bool condat_next(unsigned (&m)[V], int& L, int& jn) {
+    unsigned any = 0;
+#pragma unroll
+    for (int j = 0; j < V; j++) any |= m[j];
+    if (!any) return false;
+    L = __ffs(any) - 1;
+    jn = 0;
+#pragma unroll
+    for (int j = V - 1; j >= 0; j--)
+        if ((m[j] >> L) & 1u) jn = j;
+#pragma unroll
+    for (int j = 0; j < V; j++)
+        if (j == jn) m[j] &= m[j] - 1u;  // L is the lowest bit of m[jn]
+    return true;
 }
 
 // Warp 0: the first loop of Alg. 2 over one group of 32 vectors in index order (lane, j);
-// okv marks the elements that passed the block's filter.
+// okv marks the elements that passed the block's filter.  The survivors of the test against
+// the lambda of the group's start are visited in order, each tested again against the lambda
+// current when it is reached (c(lambda) only grows, so this is the scan's own test), with the
+// next survivor's value fetched while the current step runs.
 template <typename T, bool L1>
 __device__ __forceinline__ void condat_slab(const T (&vals)[VecOf<T>::V], const bool (&okv)[VecOf<T>::V],
                                             int64_t eidx0, double r, CondatState& st) {
     constexpr int V = VecOf<T>::V;
     const int lane = threadIdx.x & 31;
+    const int64_t e0 = eidx0 - (int64_t)lane * V;  // element (lane, j) of the group is e0 + lane*V + j
     double av[V];
 #pragma unroll
     for (int j = 0; j < V; j++) {
         const double dv = (double)vals[j];
         av[j] = L1 ? __longlong_as_double((long long)(opaque_bits(dv) & 0x7FFFFFFFFFFFFFFFull)) : dv;
     }
-    bool pass[V];
+    unsigned m[V];
     if (st.nJ == 0) {
         // the first element of the chunk starts J unconditionally (first line of Alg. 2)
-        unsigned any_ok = 0, mo[V];
 #pragma unroll
-        for (int j = 0; j < V; j++) {
-            mo[j] = __ballot_sync(0xffffffffu, okv[j]);
-            any_ok |= mo[j];
-        }
-        if (!any_ok) return;
-        const int L0 = __ffs(any_ok) - 1;
-        int j0 = 0;
-#pragma unroll
-        for (int j = V - 1; j >= 0; j--)
-            if ((mo[j] >> L0) & 1u) j0 = j;
+        for (int j = 0; j < V; j++) m[j] = __ballot_sync(0xffffffffu, okv[j]);
+        int L0, j0;
+        if (!condat_next<V>(m, L0, j0)) return;
         const double y0 = __shfl_sync(0xffffffffu, pick(av, j0), L0);
-        st.rs = __shfl_sync(0xffffffffu, eidx0, L0) + j0;
+        st.rs = e0 + L0 * V + j0;
         condat_start_j<L1>(st, r, y0);
         condat_record(st, y0);
 #pragma unroll
         for (int j = 0; j < V; j++) {
             const bool after = (lane > L0) || (lane == L0 && j > j0);
-            pass[j] = okv[j] && after && condat_gt<L1>(av[j], st, r);
+            m[j] = __ballot_sync(0xffffffffu, okv[j] && after && condat_gt<L1>(av[j], st, r));
         }
     } else {
 #pragma unroll
-        for (int j = 0; j < V; j++) pass[j] = okv[j] && condat_gt<L1>(av[j], st, r);
+        for (int j = 0; j < V; j++) m[j] = __ballot_sync(0xffffffffu, okv[j] && condat_gt<L1>(av[j], st, r));
     }
-    while (true) {
+    int L, jn;
+    bool have = condat_next<V>(m, L, jn);
+    double v = 0.0;
+    if (have) v = __shfl_sync(0xffffffffu, pick(av, jn), L);
+    while (have) {
+        const int64_t e = e0 + L * V + jn;
+        const double y = v;
+        have = condat_next<V>(m, L, jn);
+        if (have) v = __shfl_sync(0xffffffffu, pick(av, jn), L);
+        if (condat_gt<L1>(y, st, r)) condat_take<L1>(st, r, y, e);
+    }
+}
+
+// The scan warp over one whole staged tile, group by group in index order (bit lane of
+// mk[g*V + j] = the filters' verdict on element (g*32 + lane)*V + j of the tile).  A group with
+// many survivors (the tiles filtered before J had a threshold) goes through condat_slab, whose
+// lanes test the whole group at once; the few survivors of any other group are visited one
+// by one, their values loaded from the stage by every lane (one address) and tested against
+// the lambda current when each is reached (the first one of the chunk starts J).  ebase =
+// index of the tile's first element.
+constexpr int kScanSparse = 4;  // survivors of a group visited one by one
+template <typename T, bool L1>
+__device__ __forceinline__ void condat_scan_tile(const T* stage, const unsigned* mk, unsigned groups, int64_t ebase,
+                                                 double r, CondatState& st) {
+    constexpr int V = VecOf<T>::V;
+    const int lane = threadIdx.x & 31;
+    for (unsigned gs = groups; gs; gs &= gs - 1) {
+        const int gi = __ffs(gs) - 1;
         unsigned m[V];
-        unsigned any = 0;
+        int cnt = 0;
 #pragma unroll
         for (int j = 0; j < V; j++) {
-            m[j] = __ballot_sync(0xffffffffu, pass[j]);
-            any |= m[j];
+            m[j] = mk[gi * V + j];
+            cnt += __popc(m[j]);
         }
-        if (!any) break;
-        const int Lf = __ffs(any) - 1;
-        int jf = 0;
+        if (cnt > kScanSparse) {
+            using VT = typename VecOf<T>::type;
+            const VT w = reinterpret_cast<const VT*>(stage)[gi * 32 + lane];
+            T v[V];
+            bool ok[V];
 #pragma unroll
-        for (int j = V - 1; j >= 0; j--)
-            if ((m[j] >> Lf) & 1u) jf = j;
-        const double yv = __shfl_sync(0xffffffffu, pick(av, jf), Lf);
-        const int64_t e = __shfl_sync(0xffffffffu, eidx0, Lf) + jf;
-        condat_take<L1>(st, r, yv, e);
-#pragma unroll
-        for (int j = 0; j < V; j++) {
-            const bool after = (lane > Lf) || (lane == Lf && j > jf);
-            pass[j] = pass[j] && after && condat_gt<L1>(av[j], st, r);
+            for (int j = 0; j < V; j++) {
+                v[j] = reinterpret_cast<const T*>(&w)[j];
+                ok[j] = ((m[j] >> lane) & 1u) != 0u;
+            }
+            condat_slab<T, L1>(v, ok, ebase + (int64_t)(gi * 32 + lane) * V, r, st);
+            continue;
+        }
+        int L, j;
+        while (condat_next<V>(m, L, j)) {
+            const int q = gi * 32 + L;
+            const int64_t e = ebase + (int64_t)q * V + j;
+            double y = (double)stage[q * V + j];
+            if (L1) y = __longlong_as_double((long long)(opaque_bits(y) & 0x7FFFFFFFFFFFFFFFull));
+            if (st.nJ == 0) {  // the first element of the chunk starts J (first line of Alg. 2)
+                st.rs = e;
+                condat_start_j<L1>(st, r, y);
+                condat_record(st, y);
+            } else if (condat_gt<L1>(y, st, r)) {
+                condat_take<L1>(st, r, y, e);
+            }
         }
     }
 }
 
 // warp 0: the final loop of Alg. 2 over the first n entries of the J~ list, 32 at a time: every
-// lane tests its entry against the current lambda, and the passing entries are added in list
-// order, the later ones re-tested after each addition (an addition only raises c(lambda), so
-// an entry that fails stays out)
+// lane tests its entry against the current lambda, and the passing entries are visited in list
+// order, each tested again when it is reached (an addition only raises c(lambda), so an entry
+// that fails stays out)
 template <bool L1>
 __device__ __forceinline__ void condat_final_list(const double* list, int n, double r, CondatState& st) {
     const int lane = threadIdx.x & 31;
     for (int base = 0; base < n; base += 32) {
         const int e = base + lane;
         const double val = e < n ? list[e] : 0.0;
-        bool pass = e < n && condat_gt<L1>(val, st, r);
-        while (true) {
-            const unsigned m = __ballot_sync(0xffffffffu, pass);
-            if (!m) break;
-            const int Lf = __ffs(m) - 1;
-            condat_add<L1>(st, r, __shfl_sync(0xffffffffu, val, Lf));
-            pass = pass && lane > Lf && condat_gt<L1>(val, st, r);
+        unsigned m[1] = {__ballot_sync(0xffffffffu, e < n && condat_gt<L1>(val, st, r))};
+        int L, j0;
+        bool have = condat_next<1>(m, L, j0);
+        double v = 0.0;
+        if (have) v = __shfl_sync(0xffffffffu, val, L);
+        while (have) {
+            const double y = v;
+            have = condat_next<1>(m, L, j0);
+            if (have) v = __shfl_sync(0xffffffffu, val, L);
+            if (condat_gt<L1>(y, st, r)) condat_add<L1>(st, r, y);
         }
     }
 }
@@ -703,34 +792,33 @@ __device__ void condat_block(const T* __restrict__ y, const T* __restrict__ xb, 
                     const int64_t c = ring.tile(i, false);
                     const int64_t sb0 = ring.b0(c), sb1 = ring.b1(c);
                     const T* stage = ring.stage(stg, 0);
-                    const bool whole = sb0 == c * TT && sb1 == (c + 1) * TT;  // the stage holds every element
-                    for (unsigned gs = groups; gs; gs &= gs - 1) {
-                        const int gi = __ffs(gs) - 1;
-                        const int ql = gi * 32 + lane;
-                        T v[V];
-                        bool ok[V];
-                        if (whole) {
-                            using VT = typename VecOf<T>::type;
-                            const VT w = reinterpret_cast<const VT*>(stage)[ql];
-#pragma unroll
-                            for (int j = 0; j < V; j++) v[j] = reinterpret_cast<const T*>(&w)[j];
-                        } else {
+                    if (sb0 == c * TT && sb1 == (c + 1) * TT) {  // the stage holds every element
+                        condat_scan_tile<T, L1>(stage, mk, groups, c * TT, r, st);
+                    } else {
+                        for (unsigned gs = groups; gs; gs &= gs - 1) {
+                            const int gi = __ffs(gs) - 1;
+                            const int ql = gi * 32 + lane;
+                            T v[V];
+                            bool ok[V];
                             tile_vec<T>(y, sp, stage, true, c, ql, sb0, sb1, v, ok);
-                        }
 #pragma unroll
-                        for (int j = 0; j < V; j++) ok[j] = ((mk[gi * V + j] >> lane) & 1u) != 0u;
-                        condat_slab<T, L1>(v, ok, (c * NVEC + ql) * V, r, st);
-                    }
-                    if (lane == 0 && st.nJ > 0) {
-                        *reinterpret_cast<volatile float*>(&s.trd[k]) = condat_filter_rd(st);
-                        *reinterpret_cast<volatile unsigned long long*>(&s.tb[k]) = st.glo.bits;
+                            for (int j = 0; j < V; j++) ok[j] = ((mk[gi * V + j] >> lane) & 1u) != 0u;
+                            condat_slab<T, L1>(v, ok, (c * NVEC + ql) * V, r, st);
+                        }
                     }
                 }
                 __syncwarp();
                 if (lane == 0) {
-                    if (i == k) mbar_arrive(&startb[k]);  // release: the published threshold
                     // the stage is free (its filters signalled, its scan is done): the next tile
                     if (i + S < ring.count) ring.issue(ring.tile(i + S, false), stg, src);
+                    // the threshold the filters use for this type of data
+                    if (groups && st.nJ > 0) {
+                        if constexpr (sizeof(T) == 8)
+                            *reinterpret_cast<volatile unsigned long long*>(&s.tb[k]) = condat_lo_bits(st);
+                        else
+                            *reinterpret_cast<volatile float*>(&s.trd[k]) = condat_filter_rd(st);
+                    }
+                    if (i == k) mbar_arrive(&startb[k]);  // release: the published threshold
                 }
                 stg += nscan;
                 if (stg >= S) {
@@ -776,7 +864,7 @@ __device__ void condat_block(const T* __restrict__ y, const T* __restrict__ xb, 
                     condat_slab<T, L1>(v, ok, (c * (TT / V) + ql) * V, r, st);
                 }
                 if (lane == 0 && st.nJ > 0) {
-                    s.tb[0] = st.glo.bits;
+                    s.tb[0] = condat_lo_bits(st);
                     s.trd[0] = condat_filter_rd(st);
                 }
             }
