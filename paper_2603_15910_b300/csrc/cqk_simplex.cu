@@ -158,13 +158,31 @@ constexpr int kJList = 1024;  // accepted values kept for the final loop
 constexpr int kStartBit = 16;  // bit of the first start barrier's phase in the ring parity word
 constexpr int kMaxScan = 4;    // scan warps (chunks) per block in the pipelined Alg. 2
 
+constexpr int kQueue = 128;     // survivors queued between the walking and the taking warp
+constexpr int kSplitTiles = 64; // tiles of a block's chunk from which the scan is split in two
+
 struct CondatShared {
     unsigned msk[NWARP][16];  // filter ballots of each warp, (k, j) -> bit lane
     unsigned pmsk[kCondatStages][32 * 4];  // pipelined filter: ballots of group g, (g, j) -> bit lane
     double list[kJList];
     unsigned long long tb[kMaxScan];  // the published test thresholds (FP64 data: bit patterns)
     float trd[kMaxScan];              // (FP32 data)
+    // one chunk per block: the survivors in index order, written by the walking warp (values
+    // as the scan uses them, element indices), taken by the scanning warp; counters only grow
+    double qv[kQueue];
+    long long qe[kQueue];
+    unsigned qtail, qhead, qdone, qabort;
+    long long qklo;  // the scan's current klo (certain failures are not queued)
 };
+
+__device__ __forceinline__ unsigned ld_acquire_cta(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.cta.shared::cta.b32 %0, [%1];" : "=r"(v) : "r"(smem_addr(p)) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_cta(unsigned* p, unsigned v) {
+    asm volatile("st.release.cta.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(p)), "r"(v) : "memory");
+}
 
 // ---- the scalar recurrence of Alg. 2 --------------------------------------------------------
 // The scan is one long dependency chain (lambda_{k+1} from lambda_k) run by one warp, so its
@@ -701,6 +719,10 @@ __device__ void condat_block(const T* __restrict__ y, const T* __restrict__ xb, 
         s.tb[threadIdx.x] = make_gt(-INFINITY).bits;  // the sign bit of the pattern is the sign of the threshold
         s.trd[threadIdx.x] = -INFINITY;
     }
+    if (threadIdx.x == 0) {
+        s.qtail = s.qhead = s.qdone = s.qabort = 0u;
+        s.qklo = kKeyNegInf;
+    }
     TileRing<T, 1, TT> ring;
     ring.setup(sp.lo, sp.hi, smem, bars, member, nchunk);
     if (member >= nchunk) ring.count = 0;
@@ -716,15 +738,20 @@ __device__ void condat_block(const T* __restrict__ y, const T* __restrict__ xb, 
         constexpr int NVEC = TT / V;  // vectors of a tile
         constexpr int NG = NVEC / 32;  // groups of 32 vectors, in index order
         static_assert(NG == 32 && V <= 32 && kMaxScan < S, "one lane per group; a scan warp steps by less than the ring");
-        const int NP = NWARP - nscan;  // filtering warps; group g belongs to filter g % NP
+        // one chunk per block of at least kSplitTiles tiles: warp 1 walks the tiles after the
+        // first (survivors into the queue, refills), warp 0 scans the first tile, then takes the
+        // queued survivors (shorter chunks keep seven filters)
+        const bool split = nscan == 1 && ring.count >= kSplitTiles;
+        const int nfw = split ? 2 : nscan;  // warps before the filters
+        const int NP = NWARP - nfw;         // filtering warps; group g belongs to filter g % NP
         uint64_t* fullb = bars + S;
         uint64_t* startb = bars + 2 * S;  // [k]: scan k is done with its first tile
         const unsigned base = ring.parity;
         if (threadIdx.x == 0)
             for (int k = 0; k < S; k++)
                 if (k < ring.count) ring.issue(ring.tile(k, false), k, src);
-        if (wid >= nscan) {
-            const int pw = wid - nscan;
+        if (wid >= nfw) {
+            const int pw = wid - nfw;
             // stage, chunk and phase parities advance with i (no divisions in the loop)
             int stg = 0, k = 0;
             unsigned phs = base;  // bit s: parity of stage s's next phase
@@ -772,8 +799,199 @@ __device__ void condat_block(const T* __restrict__ y, const T* __restrict__ xb, 
                 }
                 __syncwarp();
                 // release: the ballots of this warp (the barrier counts NWARP - 1 arrivals: the
-                // first filter also arrives for the scan warps beyond the first)
-                if (lane == 0) mbar_arrive_cnt(&fullb[stg], pw == 0 ? (unsigned)nscan : 1u);
+                // first filter also arrives for the warps before the filters beyond the first)
+                if (lane == 0) mbar_arrive_cnt(&fullb[stg], pw == 0 ? (unsigned)nfw : 1u);
+            }
+        } else if (split && wid == 1) {
+            // the walking warp: tiles i = 1, 2, ... (stage i mod S); the survivors of each group
+            // that are not certain failures against the scan's current threshold go to the queue
+            // in index order; the stage is refilled as soon as its survivors are queued
+            const unsigned lt = (1u << lane) - 1u;
+            unsigned tail = 0u, head = 0u;
+            int stg = 1 % S;
+            unsigned flip = 0u;
+            for (int64_t i = 1; i < ring.count; i++) {
+                const unsigned ph = ((base >> stg) ^ flip) & 1u;
+                mbar_wait(&fullb[stg], ph, err, limit_ns, CQK_TIMEOUT);
+                mbar_wait(&ring.bar[stg], ph, err, limit_ns, CQK_TIMEOUT);
+                const unsigned* mk = s.pmsk[stg];
+                unsigned gany = 0;
+#pragma unroll
+                for (int j = 0; j < V; j++) gany |= mk[lane * V + j];
+                const unsigned groups = __ballot_sync(0xffffffffu, gany != 0u);
+                if (groups) {
+                    const int64_t c = ring.tile(i, false);
+                    const int64_t sb0 = ring.b0(c), sb1 = ring.b1(c);
+                    const T* stage = ring.stage(stg, 0);
+                    const bool whole = sb0 == c * TT && sb1 == (c + 1) * TT;
+                    const long long qklo = *reinterpret_cast<volatile long long*>(&s.qklo);
+                    for (unsigned gs = groups; gs; gs &= gs - 1) {
+                        const int gi = __ffs(gs) - 1;
+                        const int ql = gi * 32 + lane;
+                        T v[V];
+                        bool ok[V];
+                        if (whole) {
+                            using VT = typename VecOf<T>::type;
+                            const VT w = reinterpret_cast<const VT*>(stage)[ql];
+#pragma unroll
+                            for (int j = 0; j < V; j++) v[j] = reinterpret_cast<const T*>(&w)[j];
+                        } else {
+                            tile_vec<T>(y, sp, stage, true, c, ql, sb0, sb1, v, ok);
+                        }
+                        double av[V];
+                        unsigned b[V];
+                        int before = 0, cnt = 0;
+#pragma unroll
+                        for (int j = 0; j < V; j++) {
+                            const double dv = (double)v[j];
+                            av[j] = L1 ? __longlong_as_double((long long)(opaque_bits(dv) & 0x7FFFFFFFFFFFFFFFull)) : dv;
+                            const bool p = ((mk[gi * V + j] >> lane) & 1u) && order_key(av[j]) > qklo;
+                            b[j] = __ballot_sync(0xffffffffu, p);
+                            before += __popc(b[j] & lt);
+                            cnt += __popc(b[j]);
+                        }
+                        if (!cnt) continue;
+                        // room for cnt entries (bounded wait for the scanning warp)
+                        if (tail + (unsigned)cnt - head > (unsigned)kQueue) {
+                            // the entries queued so far become visible, then the wait for room
+                            // (lane 0 reads, the warp decides together)
+                            __syncwarp();
+                            if (lane == 0) st_release_cta(&s.qtail, tail);
+                            const unsigned long long t0 = globaltimer_ns();
+                            while (true) {
+                                head = __shfl_sync(0xffffffffu, lane == 0 ? ld_acquire_cta(&s.qhead) : 0u, 0);
+                                if (tail + (unsigned)cnt - head <= (unsigned)kQueue) break;
+                                const bool quit = lane == 0 && (*reinterpret_cast<volatile unsigned*>(&s.qabort) != 0u ||
+                                                                globaltimer_ns() - t0 > limit_ns);
+                                if (__any_sync(0xffffffffu, quit)) {
+                                    if (lane == 0) {
+                                        atomicExch(err, CQK_TIMEOUT);
+                                        s.qabort = 1u;
+                                    }
+                                    break;
+                                }
+                                __nanosleep(64);
+                            }
+                        }
+                        unsigned pos = tail + (unsigned)before;
+                        const int64_t e0 = (c * NVEC + ql) * V;
+#pragma unroll
+                        for (int j = 0; j < V; j++) {
+                            if ((b[j] >> lane) & 1u) {
+                                s.qv[pos % kQueue] = av[j];
+                                s.qe[pos % kQueue] = e0 + j;
+                                pos++;
+                            }
+                        }
+                        tail += (unsigned)cnt;
+                    }
+                    __syncwarp();
+                    if (lane == 0) st_release_cta(&s.qtail, tail);  // the tile's survivors
+                }
+                __syncwarp();
+                // the stage is free (its filters signalled, its survivors are queued): the next tile
+                if (lane == 0 && i + S < ring.count) ring.issue(ring.tile(i + S, false), stg, src);
+                if (++stg == S) {
+                    stg = 0;
+                    flip ^= 1u;
+                }
+            }
+            __syncwarp();
+            if (lane == 0) st_release_cta(&s.qdone, 1u);
+        } else if (split) {
+            // the scanning warp: the first tile from its stage, then the queue
+            if (ring.count > 0) {
+                const unsigned ph = base & 1u;
+                mbar_wait(&fullb[0], ph, err, limit_ns, CQK_TIMEOUT);
+                mbar_wait(&ring.bar[0], ph, err, limit_ns, CQK_TIMEOUT);
+                const unsigned* mk = s.pmsk[0];
+                unsigned gany = 0;
+#pragma unroll
+                for (int j = 0; j < V; j++) gany |= mk[lane * V + j];
+                const unsigned groups = __ballot_sync(0xffffffffu, gany != 0u);
+                if (groups) {
+                    const int64_t c = ring.tile(0, false);
+                    const int64_t sb0 = ring.b0(c), sb1 = ring.b1(c);
+                    const T* stage = ring.stage(0, 0);
+                    if (sb0 == c * TT && sb1 == (c + 1) * TT) {
+                        condat_scan_tile<T, L1>(stage, mk, groups, c * TT, r, st);
+                    } else {
+                        for (unsigned gs = groups; gs; gs &= gs - 1) {
+                            const int gi = __ffs(gs) - 1;
+                            const int ql = gi * 32 + lane;
+                            T v[V];
+                            bool ok[V];
+                            tile_vec<T>(y, sp, stage, true, c, ql, sb0, sb1, v, ok);
+#pragma unroll
+                            for (int j = 0; j < V; j++) ok[j] = ((mk[gi * V + j] >> lane) & 1u) != 0u;
+                            condat_slab<T, L1>(v, ok, (c * NVEC + ql) * V, r, st);
+                        }
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) {
+                    if (S < ring.count) ring.issue(ring.tile(S, false), 0, src);
+                    if (st.nJ > 0) {
+                        *reinterpret_cast<volatile long long*>(&s.qklo) = st.klo;
+                        if constexpr (sizeof(T) == 8)
+                            *reinterpret_cast<volatile unsigned long long*>(&s.tb[0]) = condat_lo_bits(st);
+                        else
+                            *reinterpret_cast<volatile float*>(&s.trd[0]) = condat_filter_rd(st);
+                    }
+                    mbar_arrive(&startb[0]);  // release: the published threshold
+                }
+            }
+            unsigned head = 0u;
+            unsigned long long t0 = 0ull;
+            while (ring.count > 1) {
+                // (lane 0 reads, the warp decides together)
+                unsigned tail = __shfl_sync(0xffffffffu, lane == 0 ? ld_acquire_cta(&s.qtail) : 0u, 0);
+                if (tail == head) {
+                    const unsigned done = __shfl_sync(0xffffffffu, lane == 0 ? ld_acquire_cta(&s.qdone) : 0u, 0);
+                    if (done) {
+                        tail = __shfl_sync(0xffffffffu, lane == 0 ? ld_acquire_cta(&s.qtail) : 0u, 0);
+                        if (tail == head) break;
+                    } else {
+                        // bounded wait for the walking warp
+                        const unsigned long long now = globaltimer_ns();
+                        if (t0 == 0ull) t0 = now;
+                        const bool quit = lane == 0 && (now - t0 > limit_ns ||
+                                                        *reinterpret_cast<volatile unsigned*>(&s.qabort) != 0u);
+                        if (__any_sync(0xffffffffu, quit)) {
+                            if (lane == 0) {
+                                atomicExch(err, CQK_TIMEOUT);
+                                s.qabort = 1u;
+                            }
+                            break;
+                        }
+                        __nanosleep(32);
+                        continue;
+                    }
+                }
+                t0 = 0ull;
+                const long long klo0 = st.klo;
+                for (; head != tail; head++) {
+                    const double yq = s.qv[head % kQueue];
+                    const long long e = s.qe[head % kQueue];
+                    if (st.nJ == 0) {  // the first element of the chunk starts J (first line of Alg. 2)
+                        st.rs = e;
+                        condat_start_j<L1>(st, r, yq);
+                        condat_record(st, yq);
+                    } else if (condat_gt<L1>(yq, st, r)) {
+                        condat_take<L1>(st, r, yq, e);
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) {
+                    st_release_cta(&s.qhead, head);
+                    if (st.nJ > 0 && st.klo != klo0) {
+                        *reinterpret_cast<volatile long long*>(&s.qklo) = st.klo;
+                        if constexpr (sizeof(T) == 8)
+                            *reinterpret_cast<volatile unsigned long long*>(&s.tb[0]) = condat_lo_bits(st);
+                        else
+                            *reinterpret_cast<volatile float*>(&s.trd[0]) = condat_filter_rd(st);
+                    }
+                }
             }
         } else {
             const int k = wid;

@@ -114,3 +114,39 @@ def test_condat_scan_warps_warm_start(scan_warps):
     assert_x_close(np64(x), oracle.project_simplex_sort(y, 1.0)[1], torch.float64)
     l0, S, C = oracle.condat_chunks_warm(y, xs, 1.0, info.tile, info.nchunks)
     assert math.isclose(info.lambda0, l0, rel_tol=1e-13, abs_tol=1e-15), (info.lambda0, l0, info.nchunks)
+
+
+@pytest.mark.parametrize("l1", [False, True])
+@pytest.mark.parametrize("n,blocks", [(300_000, 1), (2_000_003, 4), (1_048_576 + 17, 2)])
+def test_condat_split_scan(n, blocks, l1):
+    # chunks of 64 tiles or more: one warp walks the tiles and queues the survivors, another
+    # takes them; lambda_0 must still be the oracle's chunked Alg. 2, in FP64 and FP32 storage
+    rng = np.random.default_rng(n + blocks)
+    y = rng.normal(size=n) * 3.0
+    for dtype in (torch.float64, torch.float32):
+        _check(y, 1.0, l1, dtype, max_blocks=blocks)
+
+
+@pytest.mark.parametrize("l1", [False, True])
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_condat_split_scan_survivor_flood(l1, dtype):
+    # integer ties and an ascending run: tiles with far more survivors than the queue holds,
+    # so the walking warp waits for room; exact-tie decisions go to the FP64 quotient
+    rng = np.random.default_rng(11)
+    y = rng.integers(-3, 4, size=600_000).astype(np.float64)
+    _check(y, 2.0, l1, dtype, max_blocks=1)
+    z = np.linspace(-5.0, 5.0, 400_000)
+    _check(z, 1.0, l1, dtype, max_blocks=1)
+
+
+def test_condat_split_scan_warm_start():
+    # the warm start's support filter on split chunks
+    n = 400_001
+    y = np.random.default_rng(23).normal(size=n)
+    lam, xs = oracle.project_simplex_sort(y + 0.05 * np.random.default_rng(4).normal(size=n), 1.0)
+    xbar = torch.from_numpy(xs).to(DEV)
+    x, info, _ = api.project_simplex(torch.from_numpy(y).to(DEV), 1.0, init=api.Init.WARM, xbar=xbar, max_blocks=2)
+    assert info.status == api.Status.OK
+    assert_x_close(np64(x), oracle.project_simplex_sort(y, 1.0)[1], torch.float64)
+    l0, S, C = oracle.condat_chunks_warm(y, xs, 1.0, info.tile, info.nchunks)
+    assert math.isclose(info.lambda0, l0, rel_tol=1e-13, abs_tol=1e-15), (info.lambda0, l0, info.nchunks)
