@@ -1568,6 +1568,10 @@ __device__ __forceinline__ void simplex_solve(const SimplexArgs& A, const Grp& g
         }
     }
     bool bad_input = A.validate && (__ldcg(&gp.hdr->flags) & kFlagBadInput);
+    // Compiler barriers between the start, the Newton loop and the final pass: without them the
+    // l1-ball kernel's code came out ~80 us slower per solve at n = 1e8 (the simplex kernel's
+    // did not change), though every phase computes the same.
+    asm volatile("" ::: "memory");
 
     // ------------------------------------------------------------------ Newton loop (Alg. 4)
     // thread 0 keeps the bracket and the stopping logic; every thread keeps lambda
@@ -1663,6 +1667,7 @@ __device__ __forceinline__ void simplex_solve(const SimplexArgs& A, const Grp& g
     }
 
     // ------------------------------------------------------------------ final pass: x, mask
+    asm volatile("" ::: "memory");
     double sx = 0.0;
     df sx32 = df_make(0.0f);
     long long nz = 0;
