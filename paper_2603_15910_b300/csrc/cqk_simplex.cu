@@ -124,10 +124,11 @@ __device__ __forceinline__ double sum_max(const SumAcc& a) {
 // for the rest of the scan.  A filter with any threshold the scan has already reached
 // therefore passes a superset of the elements the scan can accept: the filter warps test each
 // tile against the threshold the chunk's scan last published, and the chunk's scan warp runs
-// the sequential scan over the passing elements only, in index order: it takes the first
-// passing element with the scalar update, re-tests the later ones, and publishes the new
-// threshold.  Before J is started every element passes (the first element of the chunk
-// starts J unconditionally).  The final loop of Alg. 2 over J~ visits, in order, the elements
+// the sequential scan over the passing elements only, in index order, testing each against
+// the lambda current when it is reached, and publishes the new threshold.  (A block chunk of
+// kSplitTiles tiles or more gives the walk over the passing elements and the scan to two
+// warps joined by a queue in index order; the scan is the same.)  Before J is started every
+// element passes (the first element of the chunk starts J unconditionally).  The final loop of Alg. 2 over J~ visits, in order, the elements
 // of J~ that pass the test with the current lambda.  J~ is the set of values accepted before
 // the last restart; the scan warp keeps every accepted value in acceptance (= index) order, so
 // the loop runs over that list.  When J~ outgrows the list, the loop is a re-scan of the chunk
