@@ -1282,9 +1282,10 @@ __device__ __forceinline__ bool alg4_update(Alg4State& a, int k, double lam, dou
     return done;
 }
 
-// per-block totals of a pass (fixed order) -> partials slot `par`, and into blk (thread 0);
-// a one-block group (solo) keeps them in registers only.  The counts are summed as doubles
-// (integers below 2^53, so exactly).
+// per-block totals of a pass (fixed order) -> partials slot `par`, and into blk (warp 0); a
+// one-block group (solo) keeps them in registers only.  The sum is an FP64 butterfly over the
+// warps; the two counts are integers, stored as 64-bit integer bit patterns in their double
+// slots and summed as integers (B300's FP64 pipe is the scarce unit here).
 __device__ __forceinline__ void write_pass_partials(const Grp& gp, int par, double acc, unsigned cm, unsigned ct,
                                                     double (*sh)[NWARP], bool solo, double (&blk)[3]) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -1293,18 +1294,59 @@ __device__ __forceinline__ void write_pass_partials(const Grp& gp, int par, doub
     ct = __reduce_add_sync(0xffffffffu, ct);
     if (lane == 0) {
         sh[0][wid] = acc;
-        sh[1][wid] = (double)cm;
-        sh[2][wid] = (double)cm + (double)ct;
+        sh[1][wid] = __longlong_as_double((long long)cm);
+        sh[2][wid] = __longlong_as_double((long long)ct);
     }
     __syncthreads();
     if (threadIdx.x < 32) {
-        double pv[3];
-        warp0_combine<3>(sh, -1, pv);
-        if (!solo) write_partials<3>(gp.part, gp.member, gp.g, par, pv);
-        blk[0] = pv[0];
-        blk[1] = pv[1];
-        blk[2] = pv[2];
+        double sum = lane < NWARP ? sh[0][lane] : 0.0;
+#pragma unroll
+        for (int o = NWARP / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        // (64-bit: a one-block group over more than 2^32 elements)
+        unsigned long long c1 = lane < NWARP ? (unsigned long long)__double_as_longlong(sh[1][lane]) : 0ull;
+        unsigned long long c2 = lane < NWARP ? (unsigned long long)__double_as_longlong(sh[2][lane]) : 0ull;
+#pragma unroll
+        for (int o = NWARP / 2; o > 0; o >>= 1) {
+            c1 += __shfl_xor_sync(0xffffffffu, c1, o);
+            c2 += __shfl_xor_sync(0xffffffffu, c2, o);
+        }
+        const unsigned long long c12 = c1 + c2;
+        if (!solo && lane == 0) {
+            gp.part[((size_t)par * kPartialQ + 0) * gp.g + gp.member] = sum;
+            gp.part[((size_t)par * kPartialQ + 1) * gp.g + gp.member] = __longlong_as_double((long long)c1);
+            gp.part[((size_t)par * kPartialQ + 2) * gp.g + gp.member] = __longlong_as_double((long long)c12);
+        }
+        blk[0] = sum;
+        blk[1] = (double)c1;
+        blk[2] = (double)c12;
     }
+}
+
+// The group totals of a pass from the partials of write_pass_partials (warp 0; every block
+// computes the same values in the same order): lane l takes blocks l, l + 32, ... in turn,
+// then an FP64 butterfly for the sum and integer sums for the counts.
+__device__ __forceinline__ void grid_totals_pass(const double* part, int g, int par, double (&out)[3]) {
+    const int lane = threadIdx.x & 31;
+    const double* p0 = part + ((size_t)par * kPartialQ + 0) * g;
+    const double* p1 = part + ((size_t)par * kPartialQ + 1) * g;
+    const double* p2 = part + ((size_t)par * kPartialQ + 2) * g;
+    double sum = 0.0;
+    unsigned long long c1 = 0ull, c2 = 0ull;
+#pragma unroll 4
+    for (int b = lane; b < g; b += 32) {
+        sum += ld_cg(p0 + b);
+        c1 += (unsigned long long)__double_as_longlong(ld_cg(p1 + b));
+        c2 += (unsigned long long)__double_as_longlong(ld_cg(p2 + b));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        c1 += __shfl_xor_sync(0xffffffffu, c1, o);
+        c2 += __shfl_xor_sync(0xffffffffu, c2, o);
+    }
+    out[0] = sum;
+    out[1] = (double)c1;
+    out[2] = (double)c2;
 }
 
 // the final pass: x_i = max{0, y_i + lambda} (l1: sgn(y_i) max{0, |y_i| + lambda}; copy: x = y),
@@ -1620,7 +1662,7 @@ __device__ __forceinline__ void simplex_solve(const SimplexArgs& A, const Grp& g
                 bar_target += (unsigned)G;
             }
             double red[3] = {blk[0], blk[1], blk[2]};
-            if (!solo) grid_totals_warp0<3>(gp.part, G, par, -1, red, sh);
+            if (!solo && threadIdx.x < 32) grid_totals_pass(gp.part, G, par, red);
             {
                 if (threadIdx.x == 0) {
                     int done = 0, bad = 0, redo = 0;
