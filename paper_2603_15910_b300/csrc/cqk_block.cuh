@@ -230,31 +230,29 @@ __device__ __forceinline__ void block_sum(double (&v)[NQ], double (*sh)[NWARP]) 
 }
 
 // Totals of the group's g partials of pass parity `par` (sums, and a max for q == qmax), in
-// a fixed order; valid in every lane of warp 0.  Called by all threads; every block computes
-// the same bits.  The block's loads of the g partials are all in flight at once (g <= NT in
-// one round).
+// a fixed order; valid in every lane of warp 0, computed by warp 0 alone (the other threads
+// return at once): lane l takes blocks l, l + 32, ... in turn, then a butterfly.  Every block
+// computes the same bits.  (Loading the partials with every thread and reducing them with a
+// butterfly per warp issued ~8x the FP64 instructions, and the FP64 pipe is the scarce unit
+// on this GPU.)
 template <int NQ>
 __device__ __forceinline__ void grid_totals_warp0(const double* part, int g, int par, int qmax, double (&out)[NQ],
                                                   double (*sh)[NWARP]) {
+    (void)sh;
+    if (threadIdx.x >= 32) return;
     double v[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; q++) v[q] = (q == qmax) ? -INFINITY : 0.0;
-    for (int bIdx = threadIdx.x; bIdx < g; bIdx += NT) {
+#pragma unroll 4
+    for (int b = threadIdx.x; b < g; b += 32) {
         double t[NQ];
 #pragma unroll
-        for (int q = 0; q < NQ; q++) t[q] = ld_cg(part + ((size_t)par * kPartialQ + q) * g + bIdx);
+        for (int q = 0; q < NQ; q++) t[q] = ld_cg(part + ((size_t)par * kPartialQ + q) * g + b);
 #pragma unroll
         for (int q = 0; q < NQ; q++) v[q] = (q == qmax) ? fmax(v[q], t[q]) : v[q] + t[q];
     }
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-    for (int q = 0; q < NQ; q++) v[q] = (q == qmax) ? warp_max(v[q]) : warp_sum(v[q]);
-    if (lane == 0) {
-#pragma unroll
-        for (int q = 0; q < NQ; q++) sh[q][wid] = v[q];
-    }
-    __syncthreads();
-    if (threadIdx.x < 32) warp0_combine<NQ>(sh, qmax, out);
+    for (int q = 0; q < NQ; q++) out[q] = (q == qmax) ? warp_max(v[q]) : warp_sum(v[q]);
 }
 
 // Reduce the partials of the group's g blocks for pass parity `par` (sums, and a max for
