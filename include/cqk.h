@@ -103,7 +103,10 @@ typedef struct cqk_options {
     int64_t spin_limit_us;  /* bound on every device-wide wait, microseconds; default 2000000    */
     int32_t max_blocks;     /* 0 = automatic grid size; otherwise an upper bound                */
     int32_t fault_inject;   /* testing only: 1 = make every device-wide wait unsatisfiable so   */
-                            /* that the call ends with CQK_TIMEOUT after spin_limit_us          */
+                            /* that the call ends with CQK_TIMEOUT after spin_limit_us; 2 =     */
+                            /* (simplex / l1, CQK_INIT_CONDAT, block chunks of 64 tiles or      */
+                            /* more) the split Alg. 2 scan's queue is never published, so the   */
+                            /* scanning warp's wait ends with CQK_TIMEOUT after spin_limit_us   */
     int32_t group_elems;    /* batched calls: an instance of length m is solved by a group of    */
                             /* min(32, ceil(m / group_elems)) blocks; 0 (default): 1048576 for  */
                             /* simplex / l1 batches, 65536 for general ones                     */

@@ -199,7 +199,7 @@ def make_options(init=None, max_iter=100, lambda0=0.0, validate=True, final_step
         o.final_step = 1 if final_step else 0
     o.spin_limit_us = int(spin_limit_us)
     o.max_blocks = int(max_blocks)
-    o.fault_inject = 1 if fault_inject else 0
+    o.fault_inject = int(fault_inject)  # testing only: True / 1 device-wide waits, 2 the Alg. 2 scan queue
     o.group_elems = int(group_elems)
     o.condat_chunk = int(condat_chunk)
     o.xbar = xbar.data_ptr() if xbar is not None else None

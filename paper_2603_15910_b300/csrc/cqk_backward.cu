@@ -271,8 +271,8 @@ __device__ __forceinline__ void bwd_instance(const BwdArgs& A, const Grp& gp, in
     } else {
         block_sum<2>(pv, sh);
         write_partials<2>(gp.part, gp.member, gp.g, 0, pv);
-        const unsigned target = (unsigned)gp.g + (A.fault_inject ? 1u : 0u);
-        if (!group_barrier(gp, target, A.limit_ns, A.fault_inject != 0)) {
+        const unsigned target = (unsigned)gp.g + (A.fault_inject == 1 ? 1u : 0u);
+        if (!group_barrier(gp, target, A.limit_ns, A.fault_inject == 1)) {
             if (threadIdx.x == 0 && A.status) A.status[inst] = CQK_TIMEOUT;
             return;
         }
@@ -502,8 +502,8 @@ __device__ void bwd_simplex_staged(const BwdArgs& A, const Grp& gp, int64_t inst
     double red[2];
     block_sum<2>(pv, sh);
     write_partials<2>(gp.part, gp.member, gp.g, 0, pv);
-    const unsigned target = (unsigned)gp.g + (A.fault_inject ? 1u : 0u);
-    if (!group_barrier(gp, target, A.limit_ns, A.fault_inject != 0)) {
+    const unsigned target = (unsigned)gp.g + (A.fault_inject == 1 ? 1u : 0u);
+    if (!group_barrier(gp, target, A.limit_ns, A.fault_inject == 1)) {
         if (threadIdx.x == 0 && A.status) A.status[inst] = CQK_TIMEOUT;
         parity = ring.parity;
         return;

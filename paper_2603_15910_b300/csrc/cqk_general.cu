@@ -710,7 +710,7 @@ __device__ __forceinline__ void lambda0_warm_pass(const GeneralArgs& A, const Gr
 
 #define CQK_BARRIER_OR_LEAVE()                                                  \
     do {                                                                        \
-        if (!group_barrier(gp, bar_target, A.limit_ns, A.fault_inject != 0)) {     \
+        if (!group_barrier(gp, bar_target, A.limit_ns, A.fault_inject == 1)) {     \
             if (threadIdx.x == 0) A.info->status = CQK_TIMEOUT;                 \
             return;                                                             \
         }                                                                       \
@@ -726,7 +726,7 @@ __device__ __forceinline__ void general_solve(const GeneralArgs& A, const Grp& g
     __shared__ double sh[kPartialQ][NWARP];
     __shared__ double bc[kPartialQ];
     const int G = gp.g;
-    unsigned bar_target = (unsigned)G + (A.fault_inject ? 1u : 0u);
+    unsigned bar_target = (unsigned)G + (A.fault_inject == 1 ? 1u : 0u);
     int* err = &gp.hdr->error;
     const double r = A.r;
     int passes = 0, par = 0;

@@ -703,7 +703,8 @@ __device__ __forceinline__ bool condat_prefilter(const T* stage, const T* __rest
 template <typename T, bool L1>
 __device__ void condat_block(const T* __restrict__ y, const T* __restrict__ xb, const Span& sp, bool aligned,
                              double r, int member, int nchunk, int nscan, T* smem, uint64_t* bars, unsigned& parity,
-                             int* err, unsigned long long limit_ns, SumAcc& sacc, double& S_out, long long& nJ_out) {
+                             int* err, unsigned long long limit_ns, bool qfault, SumAcc& sacc, double& S_out,
+                             long long& nJ_out) {
     constexpr int V = VecOf<T>::V;
     constexpr int TT = condat_tile<T>();
     constexpr int KC = TT / V / NT;
@@ -857,7 +858,7 @@ __device__ void condat_block(const T* __restrict__ y, const T* __restrict__ xb, 
                             // the entries queued so far become visible, then the wait for room
                             // (lane 0 reads, the warp decides together)
                             __syncwarp();
-                            if (lane == 0) st_release_cta(&s.qtail, tail);
+                            if (lane == 0 && !qfault) st_release_cta(&s.qtail, tail);
                             const unsigned long long t0 = globaltimer_ns();
                             while (true) {
                                 head = __shfl_sync(0xffffffffu, lane == 0 ? ld_acquire_cta(&s.qhead) : 0u, 0);
@@ -887,7 +888,7 @@ __device__ void condat_block(const T* __restrict__ y, const T* __restrict__ xb, 
                         tail += (unsigned)cnt;
                     }
                     __syncwarp();
-                    if (lane == 0) st_release_cta(&s.qtail, tail);  // the tile's survivors
+                    if (lane == 0 && !qfault) st_release_cta(&s.qtail, tail);  // the tile's survivors
                 }
                 __syncwarp();
                 // the stage is free (its filters signalled, its survivors are queued): the next tile
@@ -898,7 +899,9 @@ __device__ void condat_block(const T* __restrict__ y, const T* __restrict__ xb, 
                 }
             }
             __syncwarp();
-            if (lane == 0) st_release_cta(&s.qdone, 1u);
+            // (qfault, testing only: nothing is published, and the scanning warp's bounded wait
+            // ends with CQK_TIMEOUT)
+            if (lane == 0 && !qfault) st_release_cta(&s.qdone, 1u);
         } else if (split) {
             // the scanning warp: the first tile from its stage, then the queue
             if (ring.count > 0) {
@@ -1492,7 +1495,7 @@ __device__ __forceinline__ void simplex_solve(const SimplexArgs& A, const Grp& g
     const int lane = threadIdx.x & 31;
     const int G = gp.g;
     const bool aligned = A.aligned != 0;
-    unsigned bar_target = (unsigned)G + (A.fault_inject ? 1u : 0u);
+    unsigned bar_target = (unsigned)G + (A.fault_inject == 1 ? 1u : 0u);
     const double r = A.r;
 
     // ------------------------------------------------------------------ pass 0: start
@@ -1533,7 +1536,8 @@ __device__ __forceinline__ void simplex_solve(const SimplexArgs& A, const Grp& g
             double Sw = 0.0;
             long long nJw = 0;
             condat_block<T, L1>(y, warm ? static_cast<const T*>(A.xbar) : nullptr, sp, aligned, r, gp.member,
-                                nchunk, nscan, smem, bars, ring_parity, &gp.hdr->error, A.limit_ns, sacc, Sw, nJw);
+                                nchunk, nscan, smem, bars, ring_parity, &gp.hdr->error, A.limit_ns,
+                                A.fault_inject == 2, sacc, Sw, nJw);
             q[1] = lane == 0 ? Sw : 0.0;  // each scan warp's chunk (zero elsewhere)
             q[2] = lane == 0 ? (double)nJw : 0.0;
             passes++;
@@ -1558,7 +1562,7 @@ __device__ __forceinline__ void simplex_solve(const SimplexArgs& A, const Grp& g
             write_partials<4>(gp.part, gp.member, G, 0, pv);
         }
         __syncthreads();
-        if (!group_barrier(gp, bar_target, A.limit_ns, A.fault_inject != 0)) {
+        if (!group_barrier(gp, bar_target, A.limit_ns, A.fault_inject == 1)) {
             if (threadIdx.x == 0) A.info->status = CQK_TIMEOUT;
             return;
         }
@@ -1598,7 +1602,7 @@ __device__ __forceinline__ void simplex_solve(const SimplexArgs& A, const Grp& g
                 double pv[1] = {s2.sum()};
                 block_sum<1>(pv, sh);
                 write_partials<1>(gp.part, gp.member, G, 1, pv);
-                if (!group_barrier(gp, bar_target, A.limit_ns, A.fault_inject != 0)) {
+                if (!group_barrier(gp, bar_target, A.limit_ns, A.fault_inject == 1)) {
                     if (threadIdx.x == 0) A.info->status = CQK_TIMEOUT;
                     return;
                 }
@@ -1651,11 +1655,11 @@ __device__ __forceinline__ void simplex_solve(const SimplexArgs& A, const Grp& g
                 atomicOr(&gp.hdr->flags, kFlagBadInput);
             // a one-block group needs neither the partials in memory nor a barrier: thread 0
             // already holds the totals (bit-identical to the one-partial grid sum)
-            const bool solo = G == 1 && !A.fault_inject;
+            const bool solo = G == 1 && A.fault_inject != 1;
             double blk[3];
             write_pass_partials(gp, par, pa.acc64, pa.cm, pa.ct, sh, solo, blk);
             if (!solo) {
-                if (!group_barrier(gp, bar_target, A.limit_ns, A.fault_inject != 0)) {
+                if (!group_barrier(gp, bar_target, A.limit_ns, A.fault_inject == 1)) {
                     if (threadIdx.x == 0) A.info->status = CQK_TIMEOUT;
                     return;
                 }

@@ -112,3 +112,18 @@ def test_timeout_status():
     assert info.status == api.Status.TIMEOUT
     x, info, _ = api.project_simplex(y, 1.0)
     assert info.status == api.Status.OK
+
+
+@pytest.mark.parametrize("l1", [False, True])
+def test_timeout_status_scan_queue(l1):
+    # a block chunk of 64 tiles or more: the walking warp queues nothing (fault_inject = 2), the
+    # scanning warp's bounded wait for the queue runs out, the call reports CQK_TIMEOUT and the
+    # context stays usable
+    y = W.simplex_normal(400_000, seed=4).to(DEV)
+    f = api.project_l1 if l1 else api.project_simplex
+    _, info, _ = f(y, 1.0, fault_inject=2, spin_limit_us=100000, max_blocks=1)
+    assert info.status == api.Status.TIMEOUT
+    x, info, _ = f(y, 1.0, max_blocks=1)
+    assert info.status == api.Status.OK
+    _, info, _ = f(y, 1.0, fault_inject=2, spin_limit_us=100000)  # chunks too short to split
+    assert info.status == api.Status.OK
