@@ -464,7 +464,7 @@ __device__ __forceinline__ void condat_slab(const T (&vals)[VecOf<T>::V], const 
 }
 
 // The scan warp over one whole staged tile, group by group in index order (bit lane of
-// mk[g*V + j] = the filters' verdict on element (g*32 + lane)*V + j of the tile).  A group with
+// mk[g*V + j] = the filters' result for element (g*32 + lane)*V + j of the tile).  A group with
 // many survivors (the tiles filtered before J had a threshold) goes through condat_slab, whose
 // lanes test the whole group at once; the few survivors of any other group are visited one
 // by one, their values loaded from the stage by every lane (one address) and tested against
