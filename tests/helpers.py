@@ -33,3 +33,24 @@ def mask_bits(mask, n):
     m = mask.cpu().numpy().view(np.uint32)
     bits = np.unpackbits(m.view(np.uint8), bitorder="little")[:n]
     return bits.astype(bool)
+
+
+def oracle_map(fn, items, workers=None):
+    """[fn(item) for item in items], run on a thread pool: the C oracle's calls release the
+    GIL (ctypes), so independent instances solve on all host cores."""
+    import os
+    from concurrent.futures import ThreadPoolExecutor
+    items = list(items)
+    workers = workers or max(1, min(len(items), len(os.sched_getaffinity(0))))
+    if workers == 1 or len(items) <= 1:
+        return [fn(it) for it in items]
+    with ThreadPoolExecutor(max_workers=workers) as pool:
+        return list(pool.map(fn, items))
+
+
+def rel_err_x(x, xstar):
+    """max |x - x*| / (1 + max |x*|) (the norm of the x tolerance)."""
+    x, xstar = np.asarray(x, dtype=np.float64), np.asarray(xstar, dtype=np.float64)
+    if x.size == 0:
+        return 0.0
+    return float(np.max(np.abs(x - xstar))) / (1.0 + float(np.max(np.abs(xstar))))
