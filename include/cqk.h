@@ -138,7 +138,13 @@ typedef struct cqk_info {
     int32_t passes;   /* passes over the data, all phases                                       */
     int32_t stop;     /* cqk_stop                                                               */
     int32_t nchunks;  /* CQK_INIT_CONDAT: number of chunks of the partition (0 otherwise)        */
-    int32_t tile;     /* CQK_INIT_CONDAT: variable i is in chunk (i / tile) % nchunks            */
+    int32_t tile;     /* CQK_INIT_CONDAT: elements per tile of the chunk partition.  A single   */
+                      /* call: variable i is in chunk (i / tile) % nchunks.  With scan_warps =  */
+                      /* s > 1, nchunks = blocks * s and block m deals its tiles m, m + blocks, */
+                      /* m + 2 blocks, ... in turn to its s chunks, which is the same rule.     */
+                      /* Batched calls shift the tiles by the instance's start: element         */
+                      /* offsets[k] + i of instance k is in chunk                               */
+                      /* ((i + offsets[k] % tile) / tile) % nchunks                             */
 } cqk_info;
 
 /* Fills *opt with the defaults listed above. */
@@ -264,7 +270,9 @@ int cqk_project_l1_batched(int32_t B, const int64_t* offsets_dev, int32_t dtype,
  *   status_dev       nullable device output, one int32 per instance: CQK_OK, CQK_NONDIFF
  *                    (F empty: mu = 0), CQK_TIMEOUT, or CQK_BAD_ARG (decreasing offsets)
  *   workspace        cqk_workspace_bytes(n_total, B, dtype) bytes, 256-byte aligned
- * Two passes over the data: a reduction for (sum_F b g/d, Q) and the map.  FP64 arithmetic.
+ * Two passes over the data: a reduction for (sum_F b g/d, Q) and the map.  Arithmetic: the
+ * sums and mu in FP64; per element double-float (a pair of floats, about 2^-44 relative) for
+ * values in [2^-60, 2^60] and exact FP64 outside that range; FP64 results rounded once.
  */
 int cqk_backward(int32_t B, const int64_t* offsets_dev, int64_t n, int32_t dtype, const void* g,
                  const void* x, const void* a, const void* b, const void* d, const void* l,
@@ -299,8 +307,10 @@ int cqk_backward_l1(int32_t B, const int64_t* offsets_dev, int64_t n, int32_t dt
  * every GPU loading the library holds until the process exits.  It calls no allocator.
  *   - The array holds partial sums for at most CQK_NOALLOC_MAX_BLOCKS blocks, so the grid is
  *     capped there; options->max_blocks above that limit is rejected with CQK_BAD_ARG.
- *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
- *     with that device current; make that first call before any stream capture.
+ *   - The first call in a CUDA context (normally: the first call on a device, in its primary
+ *     context) looks up the array's device address (cudaGetSymbolAddress) with that device
+ *     current and remembers it for that context; make that first call before any stream
+ *     capture.
  *   - Every call on a device shares the one array, and each call clears the part that must
  *     start at zero.  Calls whose executions overlap on the GPU (different streams, or
  *     several host threads) race on it: issue them in order on one stream.

@@ -253,6 +253,6 @@ const char* cqk_status_string(int status) {
 
 int cqk_last_cuda_error(void) { return g_last_cuda_error; }
 
-int cqk_version(void) { return 100; }
+int cqk_version(void) { return 200; }  // 0.2.0: cqk_project_simplex_noalloc added
 
 }  // extern "C"

@@ -21,12 +21,39 @@ static_assert(kNoAllocBytes == CQK_NOALLOC_SCRATCH_BYTES, "header constant out o
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
-// Device address of g_noalloc_scratch per device ordinal.  In host code the array's name is
-// only a host-side stand-in, so the address is looked up once per device, with that device
-// current, and passed to the kernel.
-constexpr int kMaxDevices = 64;
+// Device address of g_noalloc_scratch per CUDA context.  In host code the array's name is
+// only a host-side stand-in, so the address is looked up (cudaGetSymbolAddress) with the
+// device current, once per context -- normally once per device, in its primary context --
+// and passed to the kernel.  Keying on the context rather than the device ordinal keeps the
+// address right for a host that runs its own context on the device.  The current context is
+// read through the driver's cuCtxGetCurrent, reached via the runtime's entry-point query so
+// that the library does not link the driver library directly.
+typedef int (*CtxGetCurrentFn)(void**);
+struct Entry {
+    void* ctx;
+    int dev;
+    void* addr;
+};
+constexpr int kMaxEntries = 64;
 std::mutex g_mu;
-void* g_addr[kMaxDevices] = {nullptr};
+Entry g_tab[kMaxEntries];
+int g_count = 0, g_next = 0;
+CtxGetCurrentFn g_ctx_get = nullptr;
+bool g_ctx_resolved = false;
+
+void* current_context() {
+    if (!g_ctx_resolved) {
+        g_ctx_resolved = true;
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_ctx_get = reinterpret_cast<CtxGetCurrentFn>(fn);
+    }
+    void* ctx = nullptr;
+    if (g_ctx_get && g_ctx_get(&ctx) != 0) ctx = nullptr;
+    return ctx;
+}
 
 int scratch_address(void** out) {
     int dev = 0;
@@ -35,18 +62,26 @@ int scratch_address(void** out) {
         cqk::set_last_cuda_error(e);
         return CQK_CUDA_ERROR;
     }
-    if (dev < 0 || dev >= kMaxDevices) return CQK_BAD_ARG;
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_addr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) {
-            cqk::set_last_cuda_error(e);
-            return CQK_CUDA_ERROR;
-        }
-        g_addr[dev] = p;
+    void* ctx = current_context();
+    if (ctx)
+        for (int i = 0; i < g_count; i++)
+            if (g_tab[i].ctx == ctx && g_tab[i].dev == dev) {
+                *out = g_tab[i].addr;
+                return CQK_OK;
+            }
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) {
+        cqk::set_last_cuda_error(e);
+        return CQK_CUDA_ERROR;
     }
-    *out = g_addr[dev];
+    if (!ctx) ctx = current_context();  // the lookup made the device's primary context current
+    if (ctx) {  // without a context handle the address is looked up on every call
+        Entry& slot = g_count < kMaxEntries ? g_tab[g_count++] : g_tab[g_next++ % kMaxEntries];
+        slot = Entry{ctx, dev, p};
+    }
+    *out = p;
     return CQK_OK;
 }
 

@@ -36,7 +36,7 @@ def test_library_builds_loads_and_exports_every_symbol():
 def test_host_only_calls():
     from paper_2603_15910_b300 import api
     lib = api.library()
-    assert lib.cqk_version() >= 100
+    assert lib.cqk_version() >= 200
     assert lib.cqk_status_string(0) == b"ok" and lib.cqk_status_string(5) == b"timeout"
     assert lib.cqk_workspace_bytes(10**8, 1, 0) > 0
     assert lib.cqk_workspace_bytes(-1, 1, 0) == 0
