@@ -37,6 +37,18 @@
 #include <stdlib.h>
 #include <string.h>
 
+/*
+ * Threads of the loops over all n variables (the phi evaluations of eq. (opt) and
+ * eq. (phideriv), eq. (CQKlambda0), the breakpoint search, the per-chunk Alg. 2 scans of
+ * Sec. 4).  1, the default, is the plain sequential oracle that every test uses.  More
+ * threads (when compiled with OpenMP) give the paper's CPU Jacobi form of the same method
+ * (Sec. 4: the map-reduce split over threads), used only to time the all-core CPU
+ * baseline; the rounding order of the sums then depends on the thread count.
+ */
+static int g_threads = 1;
+void cqko_set_threads(int t) { g_threads = t > 1 ? t : 1; }
+int cqko_get_threads(void) { return g_threads; }
+
 /* status values returned by the oracle (its own numbering) */
 #define ORC_OK 0
 #define ORC_INFEASIBLE 1
@@ -78,6 +90,7 @@ static double brk_upper(double a, double b, double d, double u) { return (d * u 
 void cqko_phi(int64_t n, const double* a, const double* b, const double* d, const double* l,
               const double* u, double lam, double* out) {
     long double phi = 0.0L, dp = 0.0L, dm = 0.0L, absbx = 0.0L;
+#pragma omp parallel for num_threads(g_threads) if (g_threads > 1) reduction(+ : phi, dp, dm, absbx)
     for (int64_t i = 0; i < n; i++) {
         double xi = x_i(lam, a[i], b[i], d[i], l[i], u[i]);
         double lo = brk_lower(a[i], b[i], d[i], l[i]);
@@ -97,6 +110,7 @@ void cqko_phi(int64_t n, const double* a, const double* b, const double* d, cons
 /* eq. (CQKlambda0) with J = {1..n}: lambda_0 = (r - s)/q, s = sum b_i a_i/d_i, q = sum b_i^2/d_i. */
 double cqko_lambda0(int64_t n, const double* a, const double* b, const double* d, double r) {
     long double s = 0.0L, q = 0.0L;
+#pragma omp parallel for num_threads(g_threads) if (g_threads > 1) reduction(+ : s, q)
     for (int64_t i = 0; i < n; i++) {
         s += (long double)(b[i] * a[i] / d[i]);
         q += (long double)(b[i] * b[i] / d[i]);
@@ -133,15 +147,27 @@ double cqko_lambda0_warm(int64_t n, const double* a, const double* b, const doub
 double cqko_breakpoint(int64_t n, const double* a, const double* b, const double* d,
                        const double* l, const double* u, double lam, int dir, int* found) {
     double best = dir > 0 ? INFINITY : -INFINITY;
-    *found = 0;
-    for (int64_t i = 0; i < n; i++) {
-        double c[2] = {brk_lower(a[i], b[i], d[i], l[i]), brk_upper(a[i], b[i], d[i], u[i])};
-        for (int k = 0; k < 2; k++) {
-            if (!isfinite(c[k])) continue;
-            if (dir > 0 && c[k] > lam && c[k] < best) { best = c[k]; *found = 1; }
-            if (dir < 0 && c[k] < lam && c[k] > best) { best = c[k]; *found = 1; }
+    int any = 0;
+#pragma omp parallel num_threads(g_threads) if (g_threads > 1)
+    {
+        double tbest = dir > 0 ? INFINITY : -INFINITY;
+        int tfound = 0;
+#pragma omp for nowait
+        for (int64_t i = 0; i < n; i++) {
+            double c[2] = {brk_lower(a[i], b[i], d[i], l[i]), brk_upper(a[i], b[i], d[i], u[i])};
+            for (int k = 0; k < 2; k++) {
+                if (!isfinite(c[k])) continue;
+                if (dir > 0 && c[k] > lam && c[k] < tbest) { tbest = c[k]; tfound = 1; }
+                if (dir < 0 && c[k] < lam && c[k] > tbest) { tbest = c[k]; tfound = 1; }
+            }
+        }
+#pragma omp critical
+        {
+            if (tfound && (!any || (dir > 0 ? tbest < best : tbest > best))) best = tbest;
+            any |= tfound;
         }
     }
+    *found = any;
     return *found ? best : 0.0;
 }
 
@@ -404,23 +430,27 @@ double cqko_condat_chunks(int64_t n, const double* y, double r, int l1, int64_t 
                           int64_t nchunks, int64_t shift, double* usum, int64_t* ucount) {
     int64_t ntiles = (n + shift + tile - 1) / tile;
     int64_t maxp = ((ntiles + nchunks - 1) / nchunks) * tile;
-    int64_t* idx = (int64_t*)malloc(sizeof(int64_t) * (size_t)(maxp > 0 ? maxp : 1));
-    int64_t* scratch = (int64_t*)malloc(sizeof(int64_t) * (size_t)(2 * (maxp > 0 ? maxp : 1)));
     long double S = 0.0L;
     int64_t C = 0;
-    for (int64_t c = 0; c < nchunks; c++) {
-        int64_t p = 0;
-        for (int64_t t = c; t < ntiles; t += nchunks)
-            for (int64_t i = t * tile - shift; i < (t + 1) * tile - shift && i < n; i++)
-                if (i >= 0) idx[p++] = i;
-        if (p == 0) continue;
-        double js; int64_t jc;
-        cqko_condat_init(y, idx, p, r, l1, &js, &jc, scratch, NULL);
-        S += js;
-        C += jc;
+#pragma omp parallel num_threads(g_threads) if (g_threads > 1) reduction(+ : S, C)
+    {
+        int64_t* idx = (int64_t*)malloc(sizeof(int64_t) * (size_t)(maxp > 0 ? maxp : 1));
+        int64_t* scratch = (int64_t*)malloc(sizeof(int64_t) * (size_t)(2 * (maxp > 0 ? maxp : 1)));
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t c = 0; c < nchunks; c++) {
+            int64_t p = 0;
+            for (int64_t t = c; t < ntiles; t += nchunks)
+                for (int64_t i = t * tile - shift; i < (t + 1) * tile - shift && i < n; i++)
+                    if (i >= 0) idx[p++] = i;
+            if (p == 0) continue;
+            double js; int64_t jc;
+            cqko_condat_init(y, idx, p, r, l1, &js, &jc, scratch, NULL);
+            S += js;
+            C += jc;
+        }
+        free(idx);
+        free(scratch);
     }
-    free(idx);
-    free(scratch);
     *usum = (double)S;
     *ucount = C;
     return (double)(((long double)r - S) / (long double)C);
@@ -508,6 +538,7 @@ double cqko_condat(int64_t n, const double* y, double r, double* x) {
 static void phi_simplex(int64_t n, const double* y, int l1, double lam, double* out) {
     long double phi = 0.0L;
     int64_t dp = 0, dm = 0;
+#pragma omp parallel for num_threads(g_threads) if (g_threads > 1) reduction(+ : phi, dp, dm)
     for (int64_t i = 0; i < n; i++) {
         double yi = yv(y, i, l1);
         phi += (long double)fmax(0.0, yi + lam);
@@ -531,6 +562,7 @@ static void phi_simplex(int64_t n, const double* y, int l1, double lam, double* 
 int cqko_newton_simplex(int64_t n, const double* y, double r, int l1, double lam0, int max_iter,
                         double eps34, double* lam_out, int* evals, int* stop, double* trace) {
     double ymin = INFINITY;
+#pragma omp parallel for num_threads(g_threads) if (g_threads > 1) reduction(min : ymin)
     for (int64_t i = 0; i < n; i++) { double v = -yv(y, i, l1); if (v < ymin) ymin = v; }
     double lam = fmax(lam0, ymin);
     double lower = -INFINITY, upper = INFINITY;

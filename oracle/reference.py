@@ -35,7 +35,7 @@ def build(force: bool = False) -> str:
             os.makedirs(_BUILD, exist_ok=True)
             tmp = _SO + f".{os.getpid()}.tmp"
             subprocess.check_call(
-                ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+                ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared",
                  "-o", tmp, _SRC, "-lm"])
             os.replace(tmp, _SO)
     return _SO
@@ -77,6 +77,18 @@ def _load():
         lib.cqko_project_simplex_sort.restype = dbl
         _lib = lib
     return _lib
+
+
+def set_threads(t: int) -> int:
+    """Threads of the oracle's loops over all variables; 1 (the default) is the plain sequential
+    oracle.  More threads run the same algorithms with OpenMP-parallel map-reduce passes (the
+    paper's CPU Jacobi form), for the all-core CPU baseline only.  Returns the previous value."""
+    lib = _load()
+    lib.cqko_set_threads.argtypes = [ctypes.c_int]
+    lib.cqko_get_threads.restype = ctypes.c_int
+    prev = int(lib.cqko_get_threads())
+    lib.cqko_set_threads(int(t))
+    return prev
 
 
 def _f64(x):
