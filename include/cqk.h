@@ -122,7 +122,15 @@ typedef struct cqk_options {
                             /* many warps side by side (the partition then has nchunks =         */
                             /* blocks * scan_warps, a looser union start); 0 (default): 4 for a  */
                             /* one-block instance of 4 to 15 tiles of 16 KB, else 1             */
-    int32_t reserved[2];
+    int32_t block_threads;  /* batched calls: threads per block of the persistent kernel.  0       */
+                            /* (default) = 256; 128 or 512 for cqk_solve_batched (general) and   */
+                            /* the batched adjoints; the batched projections and every single-   */
+                            /* instance call run 256 (other values: CQK_BAD_ARG)                 */
+    int32_t unroll;         /* batched calls: 16-byte vectors in flight per lane of the streaming */
+                            /* loops.  0 (default): the full setting (projections 8, adjoints    */
+                            /* 4-6, general 2 and two vectors per thread of a bulk-copy stage);  */
+                            /* 1: half of that, with 256 threads per block.  Single-instance     */
+                            /* calls: 0 only (other values: CQK_BAD_ARG)                         */
 } cqk_options;
 
 /* Written on the device by every solve. */

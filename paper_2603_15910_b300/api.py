@@ -60,7 +60,8 @@ class _Options(ctypes.Structure):
         ("xbar", ctypes.c_void_p),
         ("warp_elems", ctypes.c_int32),
         ("scan_warps", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 2),
+        ("block_threads", ctypes.c_int32),
+        ("unroll", ctypes.c_int32),
     ]
 
 
@@ -188,7 +189,7 @@ def stream_handle(stream=None):
 
 def make_options(init=None, max_iter=100, lambda0=0.0, validate=True, final_step=None, spin_limit_us=2_000_000,
                  max_blocks=0, fault_inject=False, group_elems=0, condat_chunk=0, xbar=None,
-                 warp_elems=0, scan_warps=0) -> _Options:
+                 warp_elems=0, scan_warps=0, block_threads=0, unroll=0) -> _Options:
     o = _Options()
     library().cqk_default_options(ctypes.byref(o))
     o.max_iter = int(max_iter)
@@ -205,7 +206,29 @@ def make_options(init=None, max_iter=100, lambda0=0.0, validate=True, final_step
     o.xbar = xbar.data_ptr() if xbar is not None else None
     o.warp_elems = int(warp_elems)
     o.scan_warps = int(scan_warps)
+    o.block_threads = int(block_threads)
+    o.unroll = int(unroll)
     return o
+
+
+_TUNABLE = ("group_elems", "warp_elems", "condat_chunk", "block_threads", "unroll", "max_blocks")
+
+
+def _with_tuning(kind, dtype, offsets, kw, use_tuning):
+    """The launch options of a batched call: the caller's, or -- when the caller sets none of the
+    work-split options and the autotuner (tune.py) has a tuning for a batch of this signature --
+    the tuned ones.  Looking a tuning up reads the offsets on the host (one synchronisation);
+    nothing is looked up while no tuning exists."""
+    if not use_tuning or any(k in kw for k in _TUNABLE):
+        return kw
+    from . import tune
+    if not tune.has_tunings():
+        return kw
+    best = tune.tuned_options(kind, dtype, offsets)
+    if best:
+        kw = dict(kw)
+        kw.update(best)
+    return kw
 
 
 class Workspace:
@@ -344,11 +367,14 @@ def _batch_finish(host, x, mask, ws, B, sync):
 
 def solve_batched(a, b, d, l, u, offsets, r, *, init=Init.FORMULA, max_iter=100, lambda0=0.0, validate=True,
                   final_step=None, out=None, want_mask=False, ws: Workspace | None = None, stream=None, sync=True,
-                  **kw):
+                  use_tuning=True, **kw):
     """B general CQK instances in one launch (cqk_solve_batched): instance k is the element
     range offsets[k]:offsets[k+1] of the concatenated a, b, d, l, u, with right-hand side
-    r[k].  Returns (x, infos, mask); infos is a list of B Info (None with sync=False)."""
+    r[k].  Returns (x, infos, mask); infos is a list of B Info (None with sync=False).
+    With use_tuning (default) and none of the work-split options given, a tuning of this
+    batch shape remembered by tune.py is applied."""
     host, dev, (a, b, d, l, u), offsets, r, B, n = _batch_args([a, b, d, l, u], offsets, r)
+    kw = _with_tuning("general", a.dtype, offsets, kw, use_tuning)
     x = out if out is not None else torch.empty_like(a)
     mask = torch.zeros((n + 31) // 32, dtype=torch.int32, device=dev) if want_mask else None
     ws = ws or Workspace(n, max(B, 1), a.dtype, dev)
@@ -360,8 +386,10 @@ def solve_batched(a, b, d, l, u, offsets, r, *, init=Init.FORMULA, max_iter=100,
     return _batch_finish(host, x, mask, ws, B, sync)
 
 
-def _project_batched(name, y, offsets, r, init, max_iter, lambda0, validate, out, want_mask, ws, stream, sync, kw):
+def _project_batched(name, y, offsets, r, init, max_iter, lambda0, validate, out, want_mask, ws, stream, sync, kw,
+                     use_tuning=True):
     host, dev, (y,), offsets, r, B, n = _batch_args([y], offsets, r)
+    kw = _with_tuning("l1" if "l1" in name else "simplex", y.dtype, offsets, kw, use_tuning)
     x = out if out is not None else torch.empty_like(y)
     mask = torch.zeros((n + 31) // 32, dtype=torch.int32, device=dev) if want_mask else None
     ws = ws or Workspace(n, max(B, 1), y.dtype, dev)
@@ -373,28 +401,32 @@ def _project_batched(name, y, offsets, r, init, max_iter, lambda0, validate, out
 
 
 def project_simplex_batched(y, offsets, r, *, init=Init.CONDAT, max_iter=100, lambda0=0.0, validate=True, out=None,
-                            want_mask=False, ws: Workspace | None = None, stream=None, sync=True, **kw):
-    """B simplex projections in one launch (cqk_project_simplex_batched)."""
+                            want_mask=False, ws: Workspace | None = None, stream=None, sync=True, use_tuning=True,
+                            **kw):
+    """B simplex projections in one launch (cqk_project_simplex_batched); use_tuning as for
+    solve_batched."""
     return _project_batched("cqk_project_simplex_batched", y, offsets, r, init, max_iter, lambda0, validate, out,
-                            want_mask, ws, stream, sync, kw)
+                            want_mask, ws, stream, sync, kw, use_tuning)
 
 
 def project_l1_batched(y, offsets, r, *, init=Init.CONDAT, max_iter=100, lambda0=0.0, validate=True, out=None,
-                       want_mask=False, ws: Workspace | None = None, stream=None, sync=True, **kw):
-    """B l1-ball projections in one launch (cqk_project_l1_batched)."""
+                       want_mask=False, ws: Workspace | None = None, stream=None, sync=True, use_tuning=True, **kw):
+    """B l1-ball projections in one launch (cqk_project_l1_batched); use_tuning as for
+    solve_batched."""
     return _project_batched("cqk_project_l1_batched", y, offsets, r, init, max_iter, lambda0, validate, out,
-                            want_mask, ws, stream, sync, kw)
+                            want_mask, ws, stream, sync, kw, use_tuning)
 
 
 def backward(kind, g, x, info, *, a=None, b=None, d=None, l=None, u=None, mask=None, offsets=None,
-             want=("a", "b", "d", "l", "u"), ws: Workspace | None = None, stream=None, **kw):
+             want=("a", "b", "d", "l", "u"), ws: Workspace | None = None, stream=None, use_tuning=True, **kw):
     """Adjoint of a solve (cqk_backward, cqk_backward_simplex, cqk_backward_l1).
 
     kind: "general", "simplex" or "l1".  g, x (and a, b, d, l, u for "general") are device
     tensors of one dtype; info is the forward's info buffer (the Workspace.info tensor or a
     copy of it, one cqk_info per instance); offsets (device int64, B + 1) selects a batch.
     Returns dict with the requested gradients ("a".."u"; "y" for the projections), "r"
-    (float64 tensor, one per instance) and "status" (int32 tensor).  No host synchronisation."""
+    (float64 tensor, one per instance) and "status" (int32 tensor).  No host synchronisation
+    (except for the lookup of a remembered tuning of a batch, see solve_batched)."""
     _check_device(g, x)
     n = x.numel()
     B = 1 if offsets is None else offsets.numel() - 1
@@ -402,6 +434,8 @@ def backward(kind, g, x, info, *, a=None, b=None, d=None, l=None, u=None, mask=N
     gr = torch.empty(max(B, 1), dtype=torch.float64, device=x.device)
     status = torch.empty(max(B, 1), dtype=torch.int32, device=x.device)
     ws = ws or Workspace(n, max(B, 1), x.dtype, x.device)
+    if offsets is not None:
+        kw = _with_tuning(kind + "_bwd", x.dtype, offsets, kw, use_tuning)
     opt = make_options(**kw)
     lib = library()
     if kind == "general":

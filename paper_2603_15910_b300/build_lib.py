@@ -27,8 +27,29 @@ NVCC_FLAGS = [
 ]
 
 
+# Builds of the batched kernels besides the default one (suffix, preprocessor definitions,
+# translation units): 128 and 512 threads per block for the general batch and the adjoints,
+# and the half-unroll build of every batched kernel.  The autotuner chooses among them through
+# cqk_options.block_threads and cqk_options.unroll.
+VARIANTS = [
+    ("_t128", ["-DCQK_NT=128"], ["cqk_batched.cu", "cqk_general.cu", "cqk_backward.cu"]),
+    ("_t512", ["-DCQK_NT=512"], ["cqk_batched.cu", "cqk_general.cu", "cqk_backward.cu"]),
+    ("_u", ["-DCQK_UNROLL_HALF"], ["cqk_batched.cu", "cqk_simplex.cu", "cqk_general.cu", "cqk_backward.cu"]),
+]
+
+
 def sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+
+
+def units():
+    """(source, object, extra flags) of every translation unit of the library."""
+    out = [(src, os.path.join(BUILD, os.path.basename(src) + ".o"), []) for src in sources()]
+    for sfx, defs, files in VARIANTS:
+        for f in files:
+            out.append((os.path.join(CSRC, f), os.path.join(BUILD, f + sfx + ".o"),
+                        [*defs, f"-DCQK_VARIANT={sfx}", "-DCQK_BATCH_ONLY"]))
+    return out
 
 
 def _stale():
@@ -46,9 +67,8 @@ def build(force=False, verbose=False):
     nvcc = os.environ.get("NVCC", "nvcc")
     os.makedirs(BUILD, exist_ok=True)
     cmds, objs = [], []
-    for src in sources():
-        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
-        cmds.append([nvcc, *NVCC_FLAGS, "-I", INCLUDE, "-I", CSRC, "-c", src, "-o", obj])
+    for src, obj, extra in units():
+        cmds.append([nvcc, *NVCC_FLAGS, *extra, "-I", INCLUDE, "-I", CSRC, "-c", src, "-o", obj])
         objs.append(obj)
 
     def compile_one(cmd):

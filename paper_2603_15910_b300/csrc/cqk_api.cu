@@ -44,6 +44,8 @@ Opts resolve_options(const cqk_options* opt, int dtype, int default_init) {
     }
     // scan_warps: 0 (automatic) or 1, 2, 4 (other positive values round down to one of these)
     o.scan_warps = d.scan_warps >= 4 ? 4 : d.scan_warps >= 2 ? 2 : d.scan_warps >= 1 ? 1 : 0;
+    o.block_threads = d.block_threads == 0 ? 256 : d.block_threads;  // checked by the entry points
+    o.unroll_half = d.unroll;
     return o;
 }
 
@@ -71,6 +73,20 @@ int persistent_grid(const void* kernel, int threads, size_t smem, int64_t work_i
 }  // namespace cqk
 
 using namespace cqk;
+
+// Single-instance calls have one build of each kernel (256 threads, full unroll).
+static bool single_variant_ok(const Opts& o) { return o.block_threads == 256 && o.unroll_half == 0; }
+
+// The build of the batched kernels selected by (block_threads, unroll): the default build, the
+// 128- and 512-thread builds (general batches and adjoints only) or the half-unroll build.
+enum Variant { kVarDefault, kVarT128, kVarT512, kVarHalf, kVarNone };
+static Variant pick_variant(const Opts& o, bool projection_forward) {
+    if (o.unroll_half == 0 && o.block_threads == 256) return kVarDefault;
+    if (o.unroll_half == 1 && o.block_threads == 256) return kVarHalf;
+    if (o.unroll_half == 0 && !projection_forward && o.block_threads == 128) return kVarT128;
+    if (o.unroll_half == 0 && !projection_forward && o.block_threads == 512) return kVarT512;
+    return kVarNone;
+}
 
 static bool ws_ok(const void* ws, size_t bytes, size_t need) { return ws && bytes >= need && ((uintptr_t)ws % 256) == 0; }
 
@@ -103,6 +119,7 @@ int cqk_solve(int64_t n, int32_t dtype, const void* a, const void* b, const void
     if (!ws_ok(workspace, ws_bytes, kSingleWsBytes)) return CQK_BAD_ARG;
     if (r != r) return CQK_BAD_ARG;
     Opts o = resolve_options(opt, dtype, CQK_INIT_FORMULA);
+    if (!single_variant_ok(o)) return CQK_BAD_ARG;
     if (o.init != CQK_INIT_FORMULA && o.init != CQK_INIT_GIVEN && o.init != CQK_INIT_WARM) return CQK_BAD_ARG;
     if (o.init == CQK_INIT_WARM && !o.xbar && n > 0) return CQK_BAD_ARG;
     if (n == 0) {
@@ -133,6 +150,7 @@ static int project(int64_t n, int32_t dtype, const void* y, double r, void* x, u
     if (x == y) return CQK_BAD_ARG;
     if (!ws_ok(ws, ws_bytes, kSingleWsBytes)) return CQK_BAD_ARG;
     Opts o = resolve_options(opt, dtype, CQK_INIT_CONDAT);
+    if (!single_variant_ok(o)) return CQK_BAD_ARG;
     if (o.init != CQK_INIT_FORMULA && o.init != CQK_INIT_CONDAT && o.init != CQK_INIT_GIVEN && o.init != CQK_INIT_WARM)
         return CQK_BAD_ARG;
     if (o.init == CQK_INIT_WARM && !o.xbar) return CQK_BAD_ARG;
@@ -161,13 +179,22 @@ static int batched(int32_t B, const int64_t* offsets, int32_t dtype, const void*
     if (!ws_ok(ws, ws_bytes, batch_ws_bytes(B))) return CQK_BAD_ARG;
     Opts o = resolve_options(opt, dtype, kind == 0 ? CQK_INIT_FORMULA : CQK_INIT_CONDAT);
     if (o.init == CQK_INIT_WARM && !o.xbar) return CQK_BAD_ARG;
+    const Variant v = pick_variant(o, kind != 0);
+    if (v == kVarNone) return CQK_BAD_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
     if (kind == 0) {
         if (o.init != CQK_INIT_FORMULA && o.init != CQK_INIT_GIVEN && o.init != CQK_INIT_WARM) return CQK_BAD_ARG;
-        return launch_general_batched(B, offsets, dtype, a, b, d, l, u, r, x, mask, info, o, ws, (cudaStream_t)stream);
+        switch (v) {
+            case kVarT128: return launch_general_batched_t128(B, offsets, dtype, a, b, d, l, u, r, x, mask, info, o, ws, s);
+            case kVarT512: return launch_general_batched_t512(B, offsets, dtype, a, b, d, l, u, r, x, mask, info, o, ws, s);
+            case kVarHalf: return launch_general_batched_u(B, offsets, dtype, a, b, d, l, u, r, x, mask, info, o, ws, s);
+            default: return launch_general_batched(B, offsets, dtype, a, b, d, l, u, r, x, mask, info, o, ws, s);
+        }
     }
     if (o.init != CQK_INIT_FORMULA && o.init != CQK_INIT_CONDAT && o.init != CQK_INIT_GIVEN && o.init != CQK_INIT_WARM)
         return CQK_BAD_ARG;
-    return launch_simplex_batched(B, offsets, dtype, a, r, kind == 2, x, mask, info, o, ws, (cudaStream_t)stream);
+    if (v == kVarHalf) return launch_simplex_batched_u(B, offsets, dtype, a, r, kind == 2, x, mask, info, o, ws, s);
+    return launch_simplex_batched(B, offsets, dtype, a, r, kind == 2, x, mask, info, o, ws, s);
 }
 
 int cqk_solve_batched(int32_t B, const int64_t* offsets_dev, int32_t dtype, const void* a, const void* b,
@@ -207,8 +234,23 @@ static int backward(int kind, int32_t B, const int64_t* offsets, int64_t n, int3
     const size_t need = offsets ? batch_ws_bytes(B) : kSingleWsBytes;
     if (!ws_ok(ws, ws_bytes, need)) return CQK_BAD_ARG;
     Opts o = resolve_options(opt, dtype, CQK_INIT_FORMULA);
-    return launch_backward(kind, B, offsets, n, dtype, g, x, a, b, d, l, u, mask, info, ga, gb, gd, gl, gu, gr,
-                           status, o, ws, (cudaStream_t)stream);
+    const Variant v = offsets ? pick_variant(o, false) : (single_variant_ok(o) ? kVarDefault : kVarNone);
+    cudaStream_t s = (cudaStream_t)stream;
+    switch (v) {
+        case kVarNone: return CQK_BAD_ARG;
+        case kVarT128:
+            return launch_backward_t128(kind, B, offsets, n, dtype, g, x, a, b, d, l, u, mask, info, ga, gb, gd, gl,
+                                        gu, gr, status, o, ws, s);
+        case kVarT512:
+            return launch_backward_t512(kind, B, offsets, n, dtype, g, x, a, b, d, l, u, mask, info, ga, gb, gd, gl,
+                                        gu, gr, status, o, ws, s);
+        case kVarHalf:
+            return launch_backward_u(kind, B, offsets, n, dtype, g, x, a, b, d, l, u, mask, info, ga, gb, gd, gl, gu,
+                                     gr, status, o, ws, s);
+        default:
+            return launch_backward(kind, B, offsets, n, dtype, g, x, a, b, d, l, u, mask, info, ga, gb, gd, gl, gu,
+                                   gr, status, o, ws, s);
+    }
 }
 
 int cqk_backward(int32_t B, const int64_t* offsets_dev, int64_t n, int32_t dtype, const void* g, const void* x,
@@ -253,6 +295,6 @@ const char* cqk_status_string(int status) {
 
 int cqk_last_cuda_error(void) { return g_last_cuda_error; }
 
-int cqk_version(void) { return 200; }  // 0.2.0: cqk_project_simplex_noalloc added
+int cqk_version(void) { return 300; }  // 0.3.0: options block_threads and unroll
 
 }  // extern "C"

@@ -25,8 +25,15 @@
 namespace cqk {
 namespace {
 
-constexpr int kBwdU = 4;      // 16-byte vectors per array in flight per lane (projections: g and x)
-constexpr int kBwdUNoX = 6;   // the simplex with the forward mask: g alone
+// 16-byte vectors per array in flight per lane (projections: g and x; the simplex with the
+// forward mask: g alone); the half-unroll build keeps half as many
+#ifdef CQK_UNROLL_HALF
+constexpr int kBwdU = 2;
+constexpr int kBwdUNoX = 3;
+#else
+constexpr int kBwdU = 4;
+constexpr int kBwdUNoX = 6;
+#endif
 constexpr int kBwdUGen = 1;  // general: 6 arrays, and the register budget of the double-float map
 
 enum BwdKind { kBwdGeneral = 0, kBwdSimplex = 1, kBwdL1 = 2 };
@@ -553,7 +560,7 @@ __device__ void bwd_simplex_staged(const BwdArgs& A, const Grp& gp, int64_t inst
 }
 
 template <typename T, int KIND, bool BATCHED, bool NOX>
-__global__ void __launch_bounds__(NT, 2) backward_kernel(BwdArgs A) {
+__global__ void __launch_bounds__(NT, kMinBlocksPerSM) backward_kernel(BwdArgs A) {
     // the staged simplex adjoint (NOX on aligned data): stages and their mbarriers
     extern __shared__ __align__(128) unsigned char dyn_smem[];
     __shared__ uint64_t bars[NOX ? kBwdStages : 1];
@@ -617,12 +624,16 @@ __global__ void __launch_bounds__(NT, 2) backward_kernel(BwdArgs A) {
 
 template <typename T, int KIND, bool NOX = false>
 const void* pick_kernel(bool batched) {
+#ifdef CQK_BATCH_ONLY
+    return batched ? (const void*)backward_kernel<T, KIND, true, NOX> : nullptr;  // variant builds: batches only
+#else
     return batched ? (const void*)backward_kernel<T, KIND, true, NOX> : (const void*)backward_kernel<T, KIND, false, NOX>;
+#endif
 }
 
 }  // namespace
 
-int launch_backward(int kind, int64_t B, const int64_t* offsets, int64_t n, int dtype, const void* g, const void* x,
+int CQK_VFN(launch_backward)(int kind, int64_t B, const int64_t* offsets, int64_t n, int dtype, const void* g, const void* x,
                     const void* a, const void* b, const void* d, const void* l, const void* u, const uint32_t* mask,
                     const cqk_info* info, void* ga, void* gb, void* gd, void* gl, void* gu, double* gr,
                     int32_t* status, const Opts& o, void* ws, cudaStream_t s) {
@@ -663,6 +674,7 @@ int launch_backward(int kind, int64_t B, const int64_t* offsets, int64_t n, int 
                                             : pick_kernel<float, kBwdSimplex>(batched))
                                      : pick_kernel<float, kBwdL1>(batched);
     }
+    if (!kern) return CQK_BAD_ARG;
     const int64_t vec = dtype == CQK_F64 ? 2 : 4;
     // the staged simplex adjoint takes kBwdSmem of dynamic shared memory (requested for every
     // NOX launch: the kernel decides on alignment at run time)
@@ -685,7 +697,7 @@ int launch_backward(int kind, int64_t B, const int64_t* offsets, int64_t n, int 
         if ((int64_t)grid > B * kMaxGroup) grid = (int)(B * kMaxGroup);
         const int64_t per_block =
             o.group_elems > 0 ? o.group_elems : (kind == kBwdGeneral ? kBackwardGroupElems : kSimplexGroupElems);
-        const int rc = plan_batch(offsets, B, per_block, grid, ws, s, kind == kBwdGeneral ? 0 : o.warp_log2);
+        const int rc = CQK_VFN(plan_batch)(offsets, B, per_block, grid, ws, s, kind == kBwdGeneral ? 0 : o.warp_log2);
         if (rc != CQK_OK) return rc;
     } else {
         A.n = n;

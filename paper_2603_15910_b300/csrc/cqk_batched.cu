@@ -103,9 +103,11 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(const int64_t* __res
 
 }  // namespace
 
+#ifndef CQK_BATCH_ONLY
 size_t batch_ws_bytes(int64_t B) { return batch_layout(B).total; }
+#endif
 
-int plan_batch(const int64_t* offsets_dev, int64_t B, int64_t per_block, int gmax, void* ws, cudaStream_t s,
+int CQK_VFN(plan_batch)(const int64_t* offsets_dev, int64_t B, int64_t per_block, int gmax, void* ws, cudaStream_t s,
                int small_log2) {
     const BatchLayout L = batch_layout(B);
     cudaError_t e = cudaMemsetAsync(ws, 0, L.order, s);  // batch header + per-instance headers

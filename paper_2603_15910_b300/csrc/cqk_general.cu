@@ -62,7 +62,15 @@ struct GeneralArgs {
 // FP64 ones every kFlushEvery sweep iterations, bounding the df summation error by
 // ~16*V*2^-46 of the flushed partial sums.
 constexpr int kFlushEvery = 8;  // sweep iterations (kGenU vectors each) between flushes
-constexpr int kGenU = 2;        // 16-byte vectors per array in flight per lane
+// 16-byte vectors per array in flight per lane (unaligned data), and bytes per array of one
+// bulk-copy stage (aligned data: 2 vectors per thread and array, 1 in the half-unroll build)
+#ifdef CQK_UNROLL_HALF
+constexpr int kGenU = 1;
+constexpr int kGenTileBytes = 16 * NT;
+#else
+constexpr int kGenU = 2;
+constexpr int kGenTileBytes = 32 * NT;
+#endif
 constexpr unsigned kFlagWide = 2u;  // some FP64 value lies outside the df operating range
 constexpr unsigned kFlagLuInf = 4u;  // some bound l_i or u_i is infinite
 // absf: sum |b_i x_i| of the Newton passes after the first, where it only scales the tolerance
@@ -397,7 +405,7 @@ __device__ __forceinline__ void eval_pass_plain(const GeneralArgs& A, const Grp&
 
 // ---- one pass with the arrays staged through shared memory by bulk copies (TileRing)
 template <typename T>
-__host__ __device__ constexpr int stage_tile() { return 8192 / (int)sizeof(T); }  // elements per array per stage
+__host__ __device__ constexpr int stage_tile() { return kGenTileBytes / (int)sizeof(T); }  // elements per array per stage
 
 template <typename T, bool FAST, bool FIN>
 __device__ __forceinline__ bool eval_pass_staged(const GeneralArgs& A, const Grp& gp, double lam, bool write_x,
@@ -971,8 +979,9 @@ __device__ __forceinline__ void general_solve(const GeneralArgs& A, const Grp& g
     }
 }
 
+#ifndef CQK_BATCH_ONLY
 template <typename T>
-__global__ void __launch_bounds__(NT, 2) general_kernel(GeneralArgs A) {
+__global__ void __launch_bounds__(NT, kMinBlocksPerSM) general_kernel(GeneralArgs A) {
     extern __shared__ __align__(128) unsigned char dyn_smem[];
     __shared__ uint64_t ring_bars[kStages];
     unsigned ring_parity = 0;
@@ -992,6 +1001,8 @@ __global__ void __launch_bounds__(NT, 2) general_kernel(GeneralArgs A) {
     general_solve<T>(A, gp, reinterpret_cast<T*>(dyn_smem), ring_bars, ring_parity);
 }
 
+#endif  // CQK_BATCH_ONLY
+
 // A batch: blocks take (instance, member) slots from the queue until it is empty; the bulk
 // copy stages and their phase bits carry over from one instance to the next.
 struct GeneralBatchArgs {
@@ -1004,7 +1015,7 @@ struct GeneralBatchArgs {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(NT, 2) general_batched_kernel(GeneralBatchArgs P) {
+__global__ void __launch_bounds__(NT, kMinBlocksPerSM) general_batched_kernel(GeneralBatchArgs P) {
     extern __shared__ __align__(128) unsigned char dyn_smem[];
     __shared__ uint64_t ring_bars[kStages];
     unsigned ring_parity = 0;
@@ -1055,8 +1066,9 @@ GeneralArgs make_args(int64_t n, const void* a, const void* b, const void* d, co
     return A;
 }
 
-constexpr size_t kStagedSmem = (size_t)kStages * 5 * 8192;  // bytes of dynamic shared memory
+constexpr size_t kStagedSmem = (size_t)kStages * 5 * kGenTileBytes;  // bytes of dynamic shared memory
 
+#ifndef CQK_BATCH_ONLY
 int launch(GeneralArgs A, int dtype, int max_blocks, cudaStream_t s, void* ws) {
     const void* kern = dtype == CQK_F64 ? (const void*)general_kernel<double> : (const void*)general_kernel<float>;
     const int64_t vec = dtype == CQK_F64 ? 2 : 4;
@@ -1085,8 +1097,11 @@ int launch(GeneralArgs A, int dtype, int max_blocks, cudaStream_t s, void* ws) {
     return CQK_OK;
 }
 
+#endif  // CQK_BATCH_ONLY
+
 }  // namespace
 
+#ifndef CQK_BATCH_ONLY
 int launch_general(int64_t n, int dtype, const void* a, const void* b, const void* d, const void* l, const void* u,
                    double r, void* x, uint32_t* mask, cqk_info* info, const Opts& o, void* ws, cudaStream_t s) {
     GeneralArgs A = make_args(n, a, b, d, l, u, x, ws, dtype);
@@ -1105,7 +1120,9 @@ int launch_general(int64_t n, int dtype, const void* a, const void* b, const voi
     return launch(A, dtype, o.max_blocks, s, ws);
 }
 
-int launch_general_batched(int64_t B, const int64_t* offsets, int dtype, const void* a, const void* b,
+#endif  // CQK_BATCH_ONLY
+
+int CQK_VFN(launch_general_batched)(int64_t B, const int64_t* offsets, int dtype, const void* a, const void* b,
                            const void* d, const void* l, const void* u, const double* r, void* x, uint32_t* mask,
                            cqk_info* info, const Opts& o, void* ws, cudaStream_t s) {
     GeneralBatchArgs P;
@@ -1144,7 +1161,7 @@ int launch_general_batched(int64_t B, const int64_t* offsets, int dtype, const v
     if (grid <= 0) return CQK_CUDA_ERROR;
     if ((int64_t)grid > B * kMaxGroup) grid = (int)(B * kMaxGroup);
     const int64_t per_block = o.group_elems > 0 ? o.group_elems : kGeneralGroupElems;
-    int rc = plan_batch(offsets, B, per_block, grid, ws, s);
+    int rc = CQK_VFN(plan_batch)(offsets, B, per_block, grid, ws, s);
     if (rc != CQK_OK) return rc;
     void* args[] = {&P};
     cudaError_t e = cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(NT), args, smem, s);
@@ -1155,6 +1172,7 @@ int launch_general_batched(int64_t B, const int64_t* offsets, int dtype, const v
     return CQK_OK;
 }
 
+#ifndef CQK_BATCH_ONLY
 int launch_phi(int64_t n, int dtype, const void* a, const void* b, const void* d, const void* l, const void* u,
                double lambda, void* x, double* out, void* ws, cudaStream_t s) {
     GeneralArgs A = make_args(n, a, b, d, l, u, x, ws, dtype);
@@ -1164,5 +1182,7 @@ int launch_phi(int64_t n, int dtype, const void* a, const void* b, const void* d
     A.limit_ns = 2000000000ull;
     return launch(A, dtype, 0, s, ws);
 }
+
+#endif  // CQK_BATCH_ONLY
 
 }  // namespace cqk

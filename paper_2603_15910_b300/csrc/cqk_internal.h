@@ -6,6 +6,21 @@
 
 #include "cqk.h"
 
+// Kernel variants.  The batched kernels are compiled more than once, each build with its own
+// block size (CQK_NT threads per block) or per-lane unroll (CQK_UNROLL_HALF: half of the
+// vectors in flight per lane of the streaming loops); a variant build defines CQK_VARIANT to
+// the suffix of its launchers (launch_general_batched_t512, ...) and CQK_BATCH_ONLY, which
+// leaves out the single-instance kernels.  The default build (no suffix) has every kernel.
+#ifndef CQK_NT
+#define CQK_NT 256
+#endif
+#ifndef CQK_VARIANT
+#define CQK_VARIANT
+#endif
+#define CQK_CAT2(a, b) a##b
+#define CQK_CAT(a, b) CQK_CAT2(a, b)
+#define CQK_VFN(name) CQK_CAT(name, CQK_VARIANT)
+
 namespace cqk {
 
 // machine epsilon^{3/4} of the stopping criteria (Sec. 4)
@@ -22,7 +37,11 @@ struct WsHeader {
 };
 static_assert(sizeof(WsHeader) == 256, "header must be 256 bytes");
 
-constexpr int kBlockThreads = 256;
+constexpr int kBlockThreads = CQK_NT;
+static_assert(kBlockThreads == 128 || kBlockThreads == 256 || kBlockThreads == 512, "block size");
+// blocks per SM the kernels are compiled for: 512 threads per SM (16 warps) at every block size,
+// so every variant has the register budget of the 256-thread build (128 per thread)
+constexpr int kMinBlocksPerSM = 512 / kBlockThreads;
 constexpr int kMaxBlocks = 148 * 8;  // upper bound of any persistent grid
 constexpr int kPartialQ = 8;         // doubles per block per pass
 constexpr unsigned kFlagBadInput = 1u;
@@ -45,11 +64,15 @@ struct Opts {
     const void* xbar;      // CQK_INIT_WARM: primal estimate
     int warp_log2;         // batched projections: instances shorter than 2^warp_log2 take one warp (0: none)
     int scan_warps;        // pipelined Alg. 2: chunks (scan warps) per block; 0 = automatic
+    int block_threads;     // batched kernels: threads per block (128, 256 or 512)
+    int unroll_half;       // batched kernels: 1 = the half-unroll build
 };
 
 Opts resolve_options(const cqk_options* opt, int dtype, int default_init);
 void set_last_cuda_error(cudaError_t e);
 
+// Launchers.  Each is defined by the default build; the batched ones (and the adjoint) also by
+// the variant builds under the suffixes listed in CQK_FOR_VARIANTS.
 int launch_simplex(int64_t n, int dtype, const void* y, double r, int l1, void* x, uint32_t* mask,
                    cqk_info* info, const Opts& o, void* ws, cudaStream_t s);
 int launch_general(int64_t n, int dtype, const void* a, const void* b, const void* d, const void* l,
@@ -64,19 +87,30 @@ constexpr int64_t kGeneralGroupElems = 1 << 16;
 constexpr int64_t kCondatChunkElems = 512;
 constexpr int64_t kBackwardGroupElems = 1 << 15;  // general adjoint (projections: kSimplexGroupElems)
 size_t batch_ws_bytes(int64_t B);
-int plan_batch(const int64_t* offsets_dev, int64_t B, int64_t per_block, int gmax, void* ws, cudaStream_t s,
-               int small_log2 = 0);
-int launch_simplex_batched(int64_t B, const int64_t* offsets, int dtype, const void* y, const double* r, int l1,
-                           void* x, uint32_t* mask, cqk_info* info, const Opts& o, void* ws, cudaStream_t s);
-int launch_general_batched(int64_t B, const int64_t* offsets, int dtype, const void* a, const void* b,
-                           const void* d, const void* l, const void* u, const double* r, void* x, uint32_t* mask,
-                           cqk_info* info, const Opts& o, void* ws, cudaStream_t s);
 
-// backward (kind 0 general, 1 simplex, 2 l1 ball); offsets == nullptr: one instance of n
-int launch_backward(int kind, int64_t B, const int64_t* offsets, int64_t n, int dtype, const void* g, const void* x,
-                    const void* a, const void* b, const void* d, const void* l, const void* u, const uint32_t* mask,
-                    const cqk_info* info, void* ga, void* gb, void* gd, void* gl, void* gu, double* gr,
-                    int32_t* status, const Opts& o, void* ws, cudaStream_t s);
+// Batched launchers and the adjoint, declared for the default build (suffix empty) and every
+// variant build: _t128 and _t512 (128 / 512 threads per block; general batches and adjoints),
+// _u (256 threads, half unroll; every batched kernel).  The planner is built with each, since
+// the warp packs of small instances hold one instance per warp of the block.
+#define CQK_DECLARE_BATCHED(sfx)                                                                                   \
+    int plan_batch##sfx(const int64_t* offsets_dev, int64_t B, int64_t per_block, int gmax, void* ws,               \
+                        cudaStream_t s, int small_log2 = 0);                                                        \
+    int launch_simplex_batched##sfx(int64_t B, const int64_t* offsets, int dtype, const void* y, const double* r,  \
+                                    int l1, void* x, uint32_t* mask, cqk_info* info, const Opts& o, void* ws,       \
+                                    cudaStream_t s);                                                                \
+    int launch_general_batched##sfx(int64_t B, const int64_t* offsets, int dtype, const void* a, const void* b,     \
+                                    const void* d, const void* l, const void* u, const double* r, void* x,          \
+                                    uint32_t* mask, cqk_info* info, const Opts& o, void* ws, cudaStream_t s);      \
+    /* backward (kind 0 general, 1 simplex, 2 l1 ball); offsets == nullptr: one instance of n */                   \
+    int launch_backward##sfx(int kind, int64_t B, const int64_t* offsets, int64_t n, int dtype, const void* g,     \
+                             const void* x, const void* a, const void* b, const void* d, const void* l,            \
+                             const void* u, const uint32_t* mask, const cqk_info* info, void* ga, void* gb,        \
+                             void* gd, void* gl, void* gu, double* gr, int32_t* status, const Opts& o, void* ws,   \
+                             cudaStream_t s);
+CQK_DECLARE_BATCHED()
+CQK_DECLARE_BATCHED(_t128)
+CQK_DECLARE_BATCHED(_t512)
+CQK_DECLARE_BATCHED(_u)
 
 // number of co-resident blocks for a cooperative kernel, capped by max_blocks and by the work
 int persistent_grid(const void* kernel, int threads, size_t smem, int64_t work_items, int max_blocks);

@@ -94,6 +94,7 @@ extern "C" int cqk_project_simplex_noalloc(int64_t n, int32_t dtype, const void*
     if (!(r > 0.0) || !(r < INFINITY) || x == y) return CQK_BAD_ARG;
     cqk::Opts o = cqk::resolve_options(opt, dtype, CQK_INIT_CONDAT);
     if (o.init != CQK_INIT_FORMULA && o.init != CQK_INIT_CONDAT && o.init != CQK_INIT_GIVEN) return CQK_BAD_ARG;
+    if (o.block_threads != 256 || o.unroll_half != 0) return CQK_BAD_ARG;  // one build of the kernel
     // the static scratch holds partial sums for at most kNoAllocMaxBlocks blocks
     if (o.max_blocks > kNoAllocMaxBlocks) return CQK_BAD_ARG;
     if (o.max_blocks == 0) o.max_blocks = kNoAllocMaxBlocks;

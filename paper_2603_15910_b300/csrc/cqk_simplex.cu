@@ -29,7 +29,13 @@
 namespace cqk {
 namespace {
 
-constexpr int kStreamU = 8;  // 16-byte vectors in flight per lane in the streaming passes
+// 16-byte vectors in flight per lane in the streaming passes (half-unroll build: 4)
+#ifdef CQK_UNROLL_HALF
+constexpr int kStreamU = 4;
+#else
+constexpr int kStreamU = 8;
+#endif
+static_assert(NT == 256, "the pipelined Alg. 2 start gives its 8 warps fixed roles");
 
 
 struct SimplexArgs {
@@ -1926,8 +1932,9 @@ __device__ __forceinline__ void init_condat_bars(uint64_t* bars) {
     __syncthreads();
 }
 
+#ifndef CQK_BATCH_ONLY
 template <typename T, bool L1>
-__global__ void __launch_bounds__(NT, 2) simplex_kernel(SimplexArgs A) {
+__global__ void __launch_bounds__(NT, kMinBlocksPerSM) simplex_kernel(SimplexArgs A) {
     extern __shared__ __align__(128) unsigned char dyn_smem[];
     __shared__ uint64_t bars[2 * kCondatStages + kMaxScan];
     unsigned parity = 0;
@@ -1940,6 +1947,8 @@ __global__ void __launch_bounds__(NT, 2) simplex_kernel(SimplexArgs A) {
     gp.part = A.part;
     simplex_solve<T, L1>(A, gp, reinterpret_cast<T*>(dyn_smem), bars, parity);
 }
+
+#endif  // CQK_BATCH_ONLY
 
 // A batch: blocks take (instance, member) slots from the queue until it is empty; every
 // instance is the span [offsets[i], offsets[i+1]) of y and x, with its own r, info, header
@@ -1954,7 +1963,7 @@ struct SimplexBatchArgs {
 };
 
 template <typename T, bool L1>
-__global__ void __launch_bounds__(NT, 2) simplex_batched_kernel(SimplexBatchArgs P) {
+__global__ void __launch_bounds__(NT, kMinBlocksPerSM) simplex_batched_kernel(SimplexBatchArgs P) {
     extern __shared__ __align__(128) unsigned char dyn_smem[];
     __shared__ uint64_t bars[2 * kCondatStages + kMaxScan];
     unsigned parity = 0;
@@ -2005,7 +2014,7 @@ __global__ void __launch_bounds__(NT, 2) simplex_batched_kernel(SimplexBatchArgs
 
 }  // namespace
 
-int launch_simplex_batched(int64_t B, const int64_t* offsets, int dtype, const void* y, const double* r, int l1,
+int CQK_VFN(launch_simplex_batched)(int64_t B, const int64_t* offsets, int dtype, const void* y, const double* r, int l1,
                            void* x, uint32_t* mask, cqk_info* info, const Opts& o, void* ws, cudaStream_t s) {
     SimplexBatchArgs P;
     memset(&P, 0, sizeof(P));
@@ -2046,7 +2055,7 @@ int launch_simplex_batched(int64_t B, const int64_t* offsets, int dtype, const v
     if ((int64_t)grid > B * kMaxGroup) grid = (int)(B * kMaxGroup);
     const int64_t per_block = o.group_elems > 0 ? o.group_elems : kSimplexGroupElems;
     // instances shorter than 2^warp_log2 are solved one per warp
-    int rc = plan_batch(offsets, B, per_block, grid, ws, s, o.warp_log2);
+    int rc = CQK_VFN(plan_batch)(offsets, B, per_block, grid, ws, s, o.warp_log2);
     if (rc != CQK_OK) return rc;
     void* args[] = {&P};
     e = cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(NT), args, kCondatSmem, s);
@@ -2057,6 +2066,7 @@ int launch_simplex_batched(int64_t B, const int64_t* offsets, int dtype, const v
     return CQK_OK;
 }
 
+#ifndef CQK_BATCH_ONLY
 int launch_simplex(int64_t n, int dtype, const void* y, double r, int l1, void* x, uint32_t* mask,
                    cqk_info* info, const Opts& o, void* ws, cudaStream_t s) {
     SimplexArgs A;
@@ -2107,5 +2117,7 @@ int launch_simplex(int64_t n, int dtype, const void* y, double r, int l1, void* 
     }
     return CQK_OK;
 }
+
+#endif  // CQK_BATCH_ONLY
 
 }  // namespace cqk

@@ -208,3 +208,97 @@ def test_batched_config_shape_simplex_f32():
         lo, hi = int(off[k]), int(off[k + 1])
         lam, xstar = oracle.project_simplex_sort(ys[lo:hi], 1.0)
         assert_x_close(xs[lo:hi], xstar, torch.float32, f"instance {k}")
+
+
+BUILDS = [(256, 0), (128, 0), (512, 0), (256, 1)]
+
+
+@pytest.mark.parametrize("block_threads,unroll", BUILDS)
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_batched_general_builds_match_oracle(block_threads, unroll, dtype):
+    # every build of the batched general kernel and its adjoint (block size, per-lane unroll),
+    # with multi-block groups (small group_elems) and one-block instances
+    lens = _lengths(31, 24, 30000)
+    parts = [W.uncorrelated_box(m, seed=300 + k, dtype=dtype) for k, m in enumerate(lens)]
+    cat = {key: torch.cat([p[key] for p in parts]).to(DEV) for key in ("a", "b", "d", "l", "u")}
+    r = np.array([p["r"] for p in parts], dtype=np.float64)
+    r[1] = 0.0
+    off = torch.from_numpy(_offsets(lens)).to(DEV)
+    n = int(off[-1])
+    g = torch.randn(n, generator=torch.Generator().manual_seed(3), dtype=torch.float64).to(dtype).to(DEV)
+    for ge in (0, 2048):
+        opts = dict(block_threads=block_threads, unroll=unroll, group_elems=ge)
+        ws = api.Workspace(n, len(lens), dtype)
+        x, infos, mask = api.solve_batched(*(cat[k] for k in "abdlu"), off, torch.from_numpy(r), want_mask=True, ws=ws,
+                                           **opts)
+        out = api.backward("general", g, x, ws.info, offsets=off, mask=mask, **{k: cat[k] for k in "abdlu"}, **opts)
+        xs, gr = np64(x), out["r"].cpu().numpy()
+        bits = mask_bits(mask, n)
+        for k, m in enumerate(lens):
+            lo, hi = int(off[k]), int(off[k + 1])
+            what = f"build {block_threads}/{unroll} ge={ge} instance {k} (m={m})"
+            if m == 0:
+                assert infos[k].status == api.Status.OK, what
+                continue
+            host = [np64(cat[q][lo:hi]) for q in "abdlu"]
+            st, lam, xstar = oracle.solve_sort(*host, float(r[k]))
+            assert infos[k].status == api.Status.OK, (what, infos[k])
+            assert_x_close(xs[lo:hi], xstar, dtype, what)
+            assert_feasible(xs[lo:hi], host[1], float(r[k]), dtype, what)
+            assert np.array_equal(bits[lo:hi], (xs[lo:hi] > host[3]) & (xs[lo:hi] < host[4])), what
+            ref = oracle.grad_cqk(xstar, lam, *host, np64(g[lo:hi]))
+            tol = 1e-10 if dtype == torch.float64 else 1e-5
+            for q in "abdlu":
+                err = float(np.max(np.abs(np64(out[q][lo:hi]) - ref[q])))
+                assert err <= tol * (1 + float(np.max(np.abs(ref[q])))), (what, q, err)
+            assert abs(gr[k] - ref["r"]) <= tol * (1 + abs(ref["r"])), what
+
+
+@pytest.mark.parametrize("block_threads,unroll", BUILDS)
+@pytest.mark.parametrize("l1", [False, True])
+def test_batched_projection_builds_match_oracle(block_threads, unroll, l1):
+    # the projection forward has the default and the half-unroll build; its adjoint every build
+    dtype = torch.float32
+    lens = _lengths(41 + l1, 40, 100000)
+    off = torch.from_numpy(_offsets(lens)).to(DEV)
+    n = int(off[-1])
+    y = W.simplex_normal(n, seed=17, dtype=dtype).to(DEV)
+    g = torch.randn(n, generator=torch.Generator().manual_seed(5), dtype=torch.float64).to(dtype).to(DEV)
+    r = torch.ones(len(lens), dtype=torch.float64)
+    fwd_unroll = unroll if block_threads == 256 else 0
+    fn = api.project_l1_batched if l1 else api.project_simplex_batched
+    ws = api.Workspace(n, len(lens), dtype)
+    x, infos, mask = fn(y, off, r, want_mask=True, ws=ws, unroll=fwd_unroll)
+    out = api.backward("l1" if l1 else "simplex", g, x, ws.info, offsets=off, mask=mask, block_threads=block_threads,
+                       unroll=unroll)
+    xs, ys, gs, gy, gr = np64(x), np64(y), np64(g), np64(out["y"]), out["r"].cpu().numpy()
+    for k, m in enumerate(lens):
+        lo, hi = int(off[k]), int(off[k + 1])
+        if m == 0:
+            continue
+        what = f"build {block_threads}/{unroll} l1={l1} instance {k} (m={m})"
+        if l1:
+            lam, xstar, inside = oracle.project_l1(ys[lo:hi], 1.0)
+            ref = oracle.grad_l1(ys[lo:hi], xstar, gs[lo:hi], inside)
+        else:
+            lam, xstar = oracle.project_simplex_sort(ys[lo:hi], 1.0)
+            ref = oracle.grad_simplex(xstar, gs[lo:hi])
+        assert infos[k].status == api.Status.OK, (what, infos[k])
+        assert_x_close(xs[lo:hi], xstar, dtype, what)
+        err = float(np.max(np.abs(gy[lo:hi] - ref["y"])))
+        assert err <= 1e-5 * (1 + float(np.max(np.abs(ref["y"])))), (what, err)
+        assert abs(gr[k] - ref["r"]) <= 1e-5 * (1 + abs(ref["r"])), what
+
+
+def test_unsupported_builds_are_rejected():
+    # the projection forward has no 128/512-thread build; single-instance calls have one build
+    y = W.simplex_normal(1000, seed=1).to(DEV)
+    off = torch.tensor([0, 500, 1000], dtype=torch.int64, device=DEV)
+    r = torch.ones(2, dtype=torch.float64)
+    for bt in (128, 512, 64):
+        with pytest.raises(RuntimeError, match="bad_arg"):
+            api.project_simplex_batched(y, off, r, block_threads=bt)
+    with pytest.raises(RuntimeError, match="bad_arg"):
+        api.project_simplex(y, 1.0, unroll=1)
+    with pytest.raises(RuntimeError, match="bad_arg"):
+        api.project_simplex_batched(y, off, r, block_threads=512, unroll=1)
