@@ -1,6 +1,7 @@
 """Benchmark of the CQK semismooth Newton hot path on B300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--no-extras]
+                    [--no-cpu-baseline] [--no-oracle-check]
 
 Workload (default): projection of y ~ N(0,1), n = 10^8, FP64, onto the unit simplex and onto
 the unit l1 ball, Condat start (Alg. 2 per chunk, then Alg. 4); one step = both projections
@@ -14,8 +15,19 @@ For N > 1 (torchrun, one process per GPU) every rank projects its own vector (se
 independent replicas, weak scaling, no data-path collective; rank 0 prints one JSON line
 with the max over ranks of the timed region.
 
---impl reference times the FP64 CPU oracle (its sequential Alg. 2 + Alg. 4, the paper's CPU
-method) on the host cores on a bounded sample of the same workload, same metric.
+Every result is also compared with the FP64 oracle's exact solution on the host
+(err_vs_oracle: the headline projections, every variant, config 0 and every instance of the
+two batches, forward and adjoint), after the GPU timing it describes.
+
+Extra keys: variants (formula vs Condat start, the 1%-sparse input, the general correlated
+family at n = 1e8 in FP64 and FP32 storage), config0 (the latency-bound n = 10,000 solve, L2
+warm and cold), batched (the two ragged batches forward + adjoint: batched launch, CUDA
+graph, autotuned options, per-instance launches from Python and in one CUDA graph, roofline
+at the algorithmic bytes) and cpu_baseline (the oracle on all host cores and on one core).
+
+--impl reference times the FP64 CPU oracle -- Alg. 2 per thread chunk and Alg. 4 with
+OpenMP map-reduce passes, the paper's CPU Jacobi form -- on all host cores on the same
+workload, same metric.
 """
 from __future__ import annotations
 
@@ -225,6 +237,90 @@ def algorithmic_bytes_projection(n, elem_bytes, info):
     return n * elem_bytes * info.passes + n * elem_bytes
 
 
+def algorithmic_bytes_general(n, elem_bytes, info):
+    """Bytes of one general solve: the eq. (CQKlambda0) pass reads a, b, d; every Newton pass
+    reads a, b, d, l, u; the final pass reads the five arrays and writes x."""
+    return n * elem_bytes * (3 + 5 * (info.passes - 2) + 6)
+
+
+def host_cores():
+    return len(os.sched_getaffinity(0))
+
+
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
+
+
+def pool_map(fn, items):
+    """[fn(i) for i in items] on a thread pool of all host cores: the C oracle's calls release
+    the GIL (ctypes), so independent solves run in parallel."""
+    from concurrent.futures import ThreadPoolExecutor
+    items = list(items)
+    if len(items) <= 1:
+        return [fn(i) for i in items]
+    with ThreadPoolExecutor(max_workers=max(1, min(len(items), host_cores()))) as pool:
+        return list(pool.map(fn, items))
+
+
+# ------------------------------------------------------------------------------ error vs oracle
+TOL_X = {"f64": 1e-10, "f32": 1e-5}
+TOL_FEAS = {"f64": 1e-12, "f32": 1e-5}
+
+
+def _x_rel(x, xstar):
+    import numpy as np
+    return float(np.max(np.abs(x - xstar))) / (1.0 + float(np.max(np.abs(xstar)))) if x.size else 0.0
+
+
+def exact_projection(y64, l1, r=1.0):
+    """(lambda*, x*) of the oracle's sort-based projection (l1 ball: Lemma 3.2)."""
+    import oracle
+    if l1:
+        lam, xstar, _ = oracle.project_l1(y64, r)
+        return lam, xstar
+    return oracle.project_simplex_sort(y64, r)
+
+
+def err_projection(x64, xstar, r, dt):
+    """Error of a projection against the oracle's exact one: max |x - x*| / (1 + max |x*|) and
+    |sum |x_i| - r| / r, with the tolerances of the storage type."""
+    import numpy as np
+    xr = _x_rel(x64, xstar)
+    fr = abs(float(np.sum(np.abs(x64), dtype=np.longdouble)) - r) / r
+    return {"x_rel": xr, "feas_rel": fr, "tol_x": TOL_X[dt], "tol_feas": TOL_FEAS[dt],
+            "within_tol": bool(xr <= TOL_X[dt] and fr <= TOL_FEAS[dt])}
+
+
+def err_general(host, r, x64, exact, dt):
+    """Error of a general solve against the oracle's exact solution: max |x - x*| / (1 + max |x*|)
+    and |b'x - r| / sum |b_i x_i| (the problem statement's feasibility, eq. (CQK))."""
+    import numpy as np
+    st, lam, xstar = exact
+    bx = host[1] * x64
+    fr = abs(float(np.sum(bx, dtype=np.longdouble)) - r) / max(float(np.sum(np.abs(bx))), 1e-300)
+    xr = _x_rel(x64, xstar) if st == "ok" else float("nan")
+    return {"x_rel": xr, "feas_rel": fr, "tol_x": TOL_X[dt], "tol_feas": TOL_FEAS[dt],
+            "within_tol": bool(st == "ok" and xr <= TOL_X[dt] and fr <= TOL_FEAS[dt])}
+
+
+def _max_err(items):
+    """Worst of per-instance error dicts."""
+    keys = [k for k in items[0] if k.endswith("_rel")]
+    out = {k: max(it[k] for it in items) for k in keys}
+    out.update({k: items[0][k] for k in items[0] if k.startswith("tol")})
+    out["within_tol"] = all(it["within_tol"] for it in items)
+    out["instances"] = len(items)
+    return out
+
+
+# ------------------------------------------------------------------------------ our arm
 def run_ours(args, world, rank, local):
     import torch
     import torch.distributed as dist
@@ -290,6 +386,17 @@ def run_ours(args, world, rank, local):
     bytes_l = algorithmic_bytes_projection(n, 8, i2)
     achieved = (bytes_s + bytes_l) / ((t_s + t_l) * 1e-3) / 1e9
     peak, peak_kind = measured_peak_hbm()
+    traffic = measured_traffic(n)
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic, "traffic_unit": "bytes per step (both launches), ncu",
+            "kernel": "simplex_kernel<double> (simplex + l1 launches)",
+            "achieved_basis": "algorithmic bytes / CUDA-event time (effective bandwidth)",
+            "peak_source": peak_kind, "ms_simplex": t_s, "ms_l1": t_l,
+            "algorithmic_bytes": bytes_s + bytes_l, "frac_of_8TBs": achieved / 8000.0}
+    if traffic:
+        # DRAM bytes the ncu capture counted for the same launches, over the same live time
+        dram = traffic / ((t_s + t_l) * 1e-3) / 1e9
+        roof.update({"dram_GBps": dram, "dram_frac": dram / peak})
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -299,14 +406,22 @@ def run_ours(args, world, rank, local):
                    "n": n, "init": "condat", "projections_per_step": 2, "iters_simplex": i1.iters,
                    "iters_l1": i2.iters, "passes_simplex": i1.passes, "passes_l1": i2.passes,
                    "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (800 MB per vector)"},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": measured_traffic(n), "traffic_unit": "bytes per step (both launches), ncu",
-                     "kernel": "simplex_kernel<double> (simplex + l1 launches)",
-                     "peak_source": peak_kind, "ms_simplex": t_s, "ms_l1": t_l,
-                     "algorithmic_bytes": bytes_s + bytes_l, "frac_of_8TBs": achieved / 8000.0},
+        "roofline": roof,
         "gpu_launches": 2 * K,
         "clocks": clk.summary(),
     }
+
+    # error of the step's two projections against the oracle's exact ones (host, all cores)
+    if rank == 0 and args.oracle_check:
+        y64, xs1, xs2 = y.cpu().numpy(), x1.cpu().numpy(), x2.cpu().numpy()
+        ex = pool_map(lambda l1: exact_projection(y64, l1), (False, True))
+        out["err_vs_oracle"] = {"simplex": err_projection(xs1, ex[0][1], 1.0, "f64"),
+                                "l1": err_projection(xs2, ex[1][1], 1.0, "f64"),
+                                "oracle": "sort-based projection (l1: Lemma 3.2), FP64, long double sums"}
+        exact_dense = {False: ex[0][1], True: ex[1][1]}
+        del xs1, xs2
+    else:
+        y64, exact_dense = None, None
 
     # end to end through the public API with host buffers: every step copies its y from pinned
     # host memory to the device, runs both projections and copies both x back to pinned host
@@ -365,13 +480,16 @@ def run_ours(args, world, rank, local):
     out["e2e"] = {"value": world * n * iters * Ke / (ems * 1e-3), "unit": UNIT, "h2d_bytes_per_step": 8 * n,
                   "d2h_bytes_per_step": 16 * n, "ms_per_step": ems / Ke,
                   "overlap": "copy in, compute and copy out on three streams, double-buffered"}
+    del y_host, xh1, xh2, yd, xo1, xo2
+    torch.cuda.empty_cache()
 
     if args.extras and rank == 0:
-        out["variants"] = extras(args, api, W, dev, stream)
-        out["batched"] = batched_extras(api, W, dev, stream)
+        out["variants"] = extras(args, api, W, dev, stream, y64, exact_dense)
+        out["config0"] = config0(api, W, dev, stream, args.oracle_check)
+        out["batched"] = batched_extras(api, W, dev, stream, args.oracle_check)
     if rank == 0 and args.cpu_baseline:
-        yc = y[:CPU_SAMPLE].cpu().numpy()
-        out["cpu_baseline"] = cpu_baseline(yc)
+        ycpu = y64 if y64 is not None else y.cpu().numpy()
+        out["cpu_baseline"] = cpu_baseline(ycpu)
     if world > 1:
         dist.destroy_process_group()
     return out if rank == 0 else None
@@ -390,17 +508,19 @@ def _time(fn, stream, reps=5):
     return a.elapsed_time(b) / reps
 
 
-def extras(args, api, W, dev, stream):
+def extras(args, api, W, dev, stream, y64=None, exact_dense=None):
     """Side measurements (not part of `value`): the plain (formula) start, the 1%-sparse
     variant, and the general CQK solve of the correlated family at n = 1e8 in FP64 and
-    FP32 storage."""
+    FP32 storage; each with its error against the oracle's exact solution."""
     import torch
     n = args.n
+    peak, _ = measured_peak_hbm()
     res = {}
     y = W.simplex_normal(n, seed=0, device=dev)
     ys = W.simplex_normal(n, seed=0, sparse=True, device=dev)
     x = torch.empty_like(y)
     ws = api.Workspace(n, 1, y.dtype, dev)
+    xs_host = {}
     for name, vec in (("dense", y), ("sparse", ys)):
         for init in (api.Init.CONDAT, api.Init.FORMULA):
             for proj in ("simplex", "l1"):
@@ -408,10 +528,27 @@ def extras(args, api, W, dev, stream):
                 ms = _time(lambda: f(vec, 1.0, init=init, out=x, ws=ws, sync=False), stream)
                 inf = ws.read_info()
                 byt = algorithmic_bytes_projection(n, 8, inf)
-                res[f"{proj}_{name}_{init.name.lower()}"] = {
+                key = f"{proj}_{name}_{init.name.lower()}"
+                res[key] = {
                     "ms": ms, "iters": inf.iters, "passes": inf.passes, "status": int(inf.status),
-                    "elem_iter_per_s": n * inf.iters / (ms * 1e-3), "GBps": byt / (ms * 1e-3) / 1e9}
+                    "elem_iter_per_s": n * inf.iters / (ms * 1e-3), "GBps": byt / (ms * 1e-3) / 1e9,
+                    "frac": byt / (ms * 1e-3) / 1e9 / peak}
+                if args.oracle_check:
+                    xs_host[key] = x.cpu().numpy()
+    if args.oracle_check:
+        vecs = {"dense": y64 if y64 is not None else y.cpu().numpy(), "sparse": ys.cpu().numpy()}
+        jobs = [(nm, l1) for nm in ("dense", "sparse") for l1 in (False, True)
+                if not (nm == "dense" and exact_dense is not None)]
+        ex = dict(zip(jobs, pool_map(lambda j: exact_projection(vecs[j[0]], j[1])[1], jobs)))
+        if exact_dense is not None:
+            ex[("dense", False)], ex[("dense", True)] = exact_dense[False], exact_dense[True]
+        for key, xh in xs_host.items():
+            proj, nm, _ = key.split("_")
+            res[key]["err_vs_oracle"] = err_projection(xh, ex[(nm, proj == "l1")], 1.0, "f64")
+        del vecs, ex, xs_host
     del y, ys, x
+    torch.cuda.empty_cache()
+    sols = {}
     for dt, tag in ((torch.float64, "f64"), (torch.float32, "f32")):
         p = W.correlated(n, seed=0, device=dev, dtype=dt)
         xg = torch.empty_like(p["a"])
@@ -420,23 +557,117 @@ def extras(args, api, W, dev, stream):
                    stream, reps=3)
         inf = wsg.read_info()
         es = 8 if dt == torch.float64 else 4
-        # pass 0 reads a, b, d; each Newton pass reads 5 arrays; the final pass reads 5, writes x
-        byt = n * es * (3 + 5 * (inf.passes - 2) + 6)
-        res[f"general_correlated_{tag}"] = {"ms": ms, "iters": inf.iters, "passes": inf.passes,
-                                            "status": int(inf.status), "elem_iter_per_s": n * inf.iters / (ms * 1e-3),
-                                            "GBps": byt / (ms * 1e-3) / 1e9}
+        byt = algorithmic_bytes_general(n, es, inf)
+        res[f"general_correlated_{tag}"] = {
+            "ms": ms, "iters": inf.iters, "passes": inf.passes, "status": int(inf.status),
+            "elem_iter_per_s": n * inf.iters / (ms * 1e-3), "GBps": byt / (ms * 1e-3) / 1e9,
+            "frac": byt / (ms * 1e-3) / 1e9 / peak,
+            "arithmetic": "per element: double-float (hi + lo float pair, ~2^-46 relative) for FP64 data in "
+                          "[2^-60, 2^60], exact FP64 outside; FP32 with a double-float multiplier for FP32 "
+                          "data; lambda and the sums FP64 (double-float partial sums flushed into FP64)"}
+        if args.oracle_check:
+            sols[tag] = ([p[k].double().cpu().numpy() for k in "abdlu"], p["r"], xg.double().cpu().numpy())
         del p, xg
         torch.cuda.empty_cache()
+    if args.oracle_check:
+        import oracle
+        tags = list(sols)
+        exact = pool_map(lambda t: oracle.solve_sort(*sols[t][0], sols[t][1]), tags)
+        for t, e in zip(tags, exact):
+            host, r, xh = sols[t]
+            res[f"general_correlated_{t}"]["err_vs_oracle"] = err_general(host, r, xh, e, t)
+        del sols, exact
     return res
 
 
-def batched_extras(api, W, dev, stream):
+def config0(api, W, dev, stream, oracle_check=True):
+    """The latency-bound single solve: general CQK, box family, n = 10,000, FP64 (400 KB per
+    iteration, L2-resident).  Each solve is timed alone with CUDA events: 50 with the data
+    warm in L2, 20 after a write of 256 MiB (larger than L2) that evicts it; and 20 solves
+    captured in one CUDA graph (launch gaps removed)."""
+    import statistics as st
+
+    import torch
+    n = 10_000
+    p = W.uncorrelated_box(n, seed=0, device=dev)
+    x = torch.empty_like(p["a"])
+    ws = api.Workspace(n, 1, p["a"].dtype, dev)
+
+    def solve(s=None):
+        api.solve(p["a"], p["b"], p["d"], p["l"], p["u"], p["r"], out=x, ws=ws, sync=False, stream=s)
+
+    for _ in range(5):
+        solve()
+    torch.cuda.synchronize()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def timed(reps, cold):
+        out = []
+        for _ in range(reps):
+            if cold:
+                flush.fill_(1)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            solve()
+            b.record(stream)
+            b.synchronize()
+            out.append(a.elapsed_time(b) * 1e3)
+        return out
+
+    warm = timed(50, False)
+    cold = timed(20, True)
+    graph_us = None
+    try:
+        g = torch.cuda.CUDAGraph()
+        cs = torch.cuda.Stream(dev)
+        cs.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(cs):
+            solve(cs)
+            torch.cuda.synchronize()
+            with torch.cuda.graph(g, stream=cs):
+                for _ in range(20):
+                    solve(cs)
+        graph_us = _time(g.replay, torch.cuda.current_stream(), reps=10) * 1e3 / 20
+    except Exception as e:  # noqa: BLE001
+        graph_us = f"capture failed: {type(e).__name__}: {e}"
+    inf = ws.read_info()
+    res = {"workload": "general CQK, box family (d~U[1,100], b~U[10,25], a~U[-10,10], l~U[-5,0], "
+                       "u=l+U[0.5,5], r=b'(l+u)/2), n=10000, FP64, seed 0",
+           "iters": inf.iters, "passes": inf.passes, "status": int(inf.status),
+           "us_warm_min": min(warm), "us_warm_median": st.median(warm),
+           "us_cold_min": min(cold), "us_cold_median": st.median(cold),
+           "us_per_solve_graph": graph_us,
+           "elem_iter_per_s_warm": n * inf.iters / (st.median(warm) * 1e-6),
+           "elem_iter_per_s_cold": n * inf.iters / (st.median(cold) * 1e-6),
+           "l2": "warm: data resident in L2; cold: 256 MiB written before each solve"}
+    if oracle_check:
+        import oracle
+        host = [p[k].cpu().numpy() for k in "abdlu"]
+        res["err_vs_oracle"] = err_general(host, p["r"], x.cpu().numpy(), oracle.solve_sort(*host, p["r"]), "f64")
+        # the sequential oracle (Alg. 1 from eq. (CQKlambda0)) on one core, same instance, for context
+        t = []
+        for _ in range(20):
+            t0 = time.perf_counter()
+            oracle.newton_cqk(*host, p["r"])
+            t.append(time.perf_counter() - t0)
+        res["cpu_oracle_us_min_1core"] = min(t) * 1e6
+    del flush
+    return res
+
+
+def batched_extras(api, W, dev, stream, oracle_check=True):
     """The batched, differentiable workloads: forward + backward of a ragged batch in two
     launches (captured once in a CUDA graph and replayed) against the same solves issued as
-    one forward and one backward launch per instance.
+    one forward and one backward launch per instance, from Python and captured in one CUDA
+    graph; the options the autotuner picks for the batch against the defaults; the achieved
+    bandwidth at the algorithmic bytes; and the error of every instance against the oracle.
       simplex: 4096 instances, lengths log-uniform in [16, 2^20], FP32 y ~ N(0,1), r = 1
       general: 256 instances, lengths log-uniform in [1e3, 1e6], FP64 uncorrelated box"""
+    import numpy as np
     import torch
+
+    from paper_2603_15910_b300 import tune
+    peak, _ = measured_peak_hbm()
     res = {}
     cases = (
         ("simplex_f32_b4096", lambda: W.batched_simplex(batch=4096, lo=16, hi=1 << 20, seed=0, device=dev,
@@ -455,15 +686,17 @@ def batched_extras(api, W, dev, stream):
         x = torch.empty_like(vec)
         mask = torch.zeros((n + 31) // 32, dtype=torch.int32, device=dev)
         ws = api.Workspace(n, B, vec.dtype, dev)
-        grads = {k: torch.empty_like(vec) for k in ("a", "b", "d", "l", "u", "y")}
+        grads = {k: torch.empty_like(vec) for k in (("a", "b", "d", "l", "u") if general else ("y",))}
         gr = torch.empty(B, dtype=torch.float64, device=dev)
         st = torch.empty(B, dtype=torch.int32, device=dev)
         lib = api.library()
-        opt = api.make_options()
         P = api.ptr
         code = api.dtype_code(vec.dtype)
+        es = vec.element_size()
 
-        def fwd_bwd(s=None):
+        def fwd_bwd(s=None, opt=None, opt_b=None):
+            opt = opt or api.make_options()
+            opt_b = opt_b or opt
             sh = api.stream_handle(s or stream)
             if general:
                 rc = lib.cqk_solve_batched(B, P(off), code, P(d["a"]), P(d["b"]), P(d["d"]), P(d["l"]), P(d["u"]),
@@ -472,126 +705,260 @@ def batched_extras(api, W, dev, stream):
                 api.check_rc(rc, "cqk_solve_batched")
                 rc = lib.cqk_backward(B, P(off), n, code, P(g), P(x), P(d["a"]), P(d["b"]), P(d["d"]), P(d["l"]),
                                       P(d["u"]), P(mask), P(ws.info), P(grads["a"]), P(grads["b"]), P(grads["d"]),
-                                      P(grads["l"]), P(grads["u"]), P(gr), P(st), api.ctypes.byref(opt),
+                                      P(grads["l"]), P(grads["u"]), P(gr), P(st), api.ctypes.byref(opt_b),
                                       P(ws.buf), ws.nbytes, sh)
                 api.check_rc(rc, "cqk_backward")
             else:
                 rc = lib.cqk_project_simplex_batched(B, P(off), code, P(d["y"]), P(r), P(x), P(mask), P(ws.info),
-                                                     api.ctypes.byref(opt), P(ws.buf), ws.nbytes,
-                                                     sh)
+                                                     api.ctypes.byref(opt), P(ws.buf), ws.nbytes, sh)
                 api.check_rc(rc, "cqk_project_simplex_batched")
                 rc = lib.cqk_backward_simplex(B, P(off), n, code, P(g), P(x), P(mask), P(ws.info), P(grads["y"]),
-                                              P(gr), P(st), api.ctypes.byref(opt), P(ws.buf), ws.nbytes,
-                                              sh)
+                                              P(gr), P(st), api.ctypes.byref(opt_b), P(ws.buf), ws.nbytes, sh)
                 api.check_rc(rc, "cqk_backward_simplex")
+
+        def graph_of(fn):
+            gph = torch.cuda.CUDAGraph()
+            cs = torch.cuda.Stream(dev)
+            cs.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(cs):
+                fn(cs)
+                torch.cuda.synchronize()
+                with torch.cuda.graph(gph, stream=cs):
+                    fn(cs)
+            torch.cuda.synchronize()
+            return gph
 
         ms_batched = _time(fwd_bwd, stream)
         infos = ws.read_infos(B)
         ok = sum(int(i.status) == 0 for i in infos)
-        graph_ms = None
         try:
-            gph = torch.cuda.CUDAGraph()
-            cs = torch.cuda.Stream()
-            cs.wait_stream(torch.cuda.current_stream())
-            with torch.cuda.stream(cs):
-                fwd_bwd(cs)
-                torch.cuda.synchronize()
-                with torch.cuda.graph(gph, stream=cs):
-                    fwd_bwd(cs)
-            graph_ms = _time(gph.replay, torch.cuda.current_stream())
+            graph_ms = _time(graph_of(fwd_bwd).replay, torch.cuda.current_stream())
         except Exception as e:  # capture unsupported: report, do not fail the bench
             graph_ms = f"capture failed: {type(e).__name__}: {e}"
-        # per-instance launches (one forward + one backward per instance), same arrays
+        best_ms = graph_ms if isinstance(graph_ms, float) else ms_batched
+        # algorithmic bytes of the forward (per instance: its passes) and of the adjoint
         offs = off.cpu().tolist()
+        lens = [offs[k + 1] - offs[k] for k in range(B)]
+        if general:
+            fwd_bytes = sum(es * m * (3 + 5 * (i.passes - 2) + 6) + m / 8 for m, i in zip(lens, infos) if m)
+            bwd_bytes = sum(es * m * (4 + 6 + 5) + m / 4 for m in lens)  # g,x,b,d | g,x,b,d,l,u -> 5 grads
+        else:
+            fwd_bytes = sum(es * m * (i.passes + 1) + m / 8 for m, i in zip(lens, infos) if m)
+            bwd_bytes = sum(es * m * 3 + m / 4 for m in lens)  # g | g -> gy, mask read twice
+        alg = fwd_bytes + bwd_bytes
+        # per-instance launches (one forward + one backward per instance), same arrays
         rl = d["r"].cpu().tolist()
-        ws1 = api.Workspace(max(offs[k + 1] - offs[k] for k in range(B)), 1, vec.dtype, dev)
+        ws1 = api.Workspace(max(lens), 1, vec.dtype, dev)
         info1 = ws1.info
+        opt1 = api.make_options()
 
-        def per_instance():
+        def per_instance(s=None):
+            sh = api.stream_handle(s or stream)
             for k in range(B):
                 lo, hi = offs[k], offs[k + 1]
                 m = hi - lo
                 if m == 0:
                     continue
-                es = vec.element_size()
                 if general:
                     ap = [P(d[q][lo:hi]) for q in ("a", "b", "d", "l", "u")]
-                    lib.cqk_solve(m, code, *ap, float(rl[k]), P(x[lo:hi]), None, P(info1), api.ctypes.byref(opt),
-                                  P(ws1.buf), ws1.nbytes, api.stream_handle(stream))
+                    lib.cqk_solve(m, code, *ap, float(rl[k]), P(x[lo:hi]), None, P(info1), api.ctypes.byref(opt1),
+                                  P(ws1.buf), ws1.nbytes, sh)
                     lib.cqk_backward(1, None, m, code, P(g[lo:hi]), P(x[lo:hi]), *ap, None, P(info1),
                                      P(grads["a"][lo:hi]), P(grads["b"][lo:hi]), P(grads["d"][lo:hi]),
                                      P(grads["l"][lo:hi]), P(grads["u"][lo:hi]), P(gr[k:k + 1]), P(st[k:k + 1]),
-                                     api.ctypes.byref(opt), P(ws1.buf), ws1.nbytes, api.stream_handle(stream))
+                                     api.ctypes.byref(opt1), P(ws1.buf), ws1.nbytes, sh)
                 else:
                     lib.cqk_project_simplex(m, code, P(d["y"][lo:hi]), float(rl[k]), P(x[lo:hi]), None, P(info1),
-                                            api.ctypes.byref(opt), P(ws1.buf), ws1.nbytes, api.stream_handle(stream))
+                                            api.ctypes.byref(opt1), P(ws1.buf), ws1.nbytes, sh)
                     lib.cqk_backward_simplex(1, None, m, code, P(g[lo:hi]), P(x[lo:hi]), None, P(info1),
                                              P(grads["y"][lo:hi]), P(gr[k:k + 1]), P(st[k:k + 1]),
-                                             api.ctypes.byref(opt), P(ws1.buf), ws1.nbytes, api.stream_handle(stream))
+                                             api.ctypes.byref(opt1), P(ws1.buf), ws1.nbytes, sh)
 
         ms_loop = _time(per_instance, stream, reps=2)
-        res[name] = {"instances": B, "n_total": n, "dtype": str(vec.dtype).replace("torch.", ""),
-                     "ms_fwd_bwd_batched": ms_batched, "ms_fwd_bwd_graph": graph_ms,
-                     "ms_fwd_bwd_per_instance_launches": ms_loop,
-                     "speedup_vs_per_instance": ms_loop / (graph_ms if isinstance(graph_ms, float) else ms_batched),
-                     "instances_ok": ok, "mean_iters": sum(i.iters for i in infos) / B,
-                     "elements_per_s_fwd_bwd": n / ((graph_ms if isinstance(graph_ms, float) else ms_batched) * 1e-3)}
+        try:
+            ms_loop_graph = _time(graph_of(per_instance).replay, torch.cuda.current_stream(), reps=3)
+        except Exception as e:  # noqa: BLE001
+            ms_loop_graph = f"capture failed: {type(e).__name__}: {e}"
+        # the autotuner on this batch: forward + backward with the options it picks
+        kind = "general" if general else "simplex"
+        arrays = tuple(d[q] for q in ("a", "b", "d", "l", "u")) if general else (d["y"],)
+        t0 = time.perf_counter()
+        best_f, best_b, t_f, t_b = tune.tune_fwd_bwd(kind, *arrays, offsets=off, r=r, g=g, reps=2)
+        tune_s = time.perf_counter() - t0
+        tune.clear()
+        ms_tuned = _time(lambda s=None: fwd_bwd(s, api.make_options(**best_f), api.make_options(**best_b)), stream)
+        entry = {"instances": B, "n_total": n, "dtype": str(vec.dtype).replace("torch.", ""),
+                 "ms_fwd_bwd_batched": ms_batched, "ms_fwd_bwd_graph": graph_ms,
+                 "ms_fwd_bwd_tuned": ms_tuned, "tuned_options": {"forward": best_f, "adjoint": best_b},
+                 "tuned_ms": {"forward_best": t_f[0][0], "adjoint_best": t_b[0][0],
+                              "forward_worst": t_f[-1][0], "adjoint_worst": t_b[-1][0]},
+                 "speedup_tuned_vs_default": ms_batched / ms_tuned,
+                 "tuning_seconds": tune_s, "tuning_candidates": len(t_f) + len(t_b),
+                 "ms_fwd_bwd_per_instance_launches": ms_loop, "ms_fwd_bwd_per_instance_graph": ms_loop_graph,
+                 "speedup_vs_per_instance_launches": ms_loop / best_ms,
+                 "speedup_vs_per_instance_graph": (ms_loop_graph / best_ms if isinstance(ms_loop_graph, float)
+                                                   else None),
+                 "instances_ok": ok, "mean_iters": sum(i.iters for i in infos) / B,
+                 "elements_per_s_fwd_bwd": n / (best_ms * 1e-3),
+                 "roofline": {"bound": "hbm", "algorithmic_bytes": alg, "fwd_bytes": fwd_bytes,
+                              "bwd_bytes": bwd_bytes, "achieved": alg / (best_ms * 1e-3) / 1e9, "unit": "GB/s",
+                              "peak": peak, "frac": alg / (best_ms * 1e-3) / 1e9 / peak,
+                              "basis": "forward: every pass streams the instance's arrays (info.passes), the final "
+                                       "pass writes x and the mask; adjoint: two passes (DESIGN table)"}}
+        if oracle_check:
+            fwd_bwd()  # default options: the results checked below
+            torch.cuda.synchronize()
+            entry["err_vs_oracle"] = _batch_errors(general, d, x, grads, gr, offs, B, vec.dtype)
+        res[name] = entry
         del d, x, mask, ws, grads, ws1
         torch.cuda.empty_cache()
     return res
 
 
-# ------------------------------------------------------------------------------ oracle timing
-def cpu_baseline(y, max_seconds=30.0):
-    """The FP64 oracle as it stands (sequential C: Alg. 2 start + Alg. 4), on the host, for
-    the same two projections of a bounded sample of the workload."""
+def _batch_errors(general, d, x, grads, gr, offs, B, dtype):
+    """Per-instance error of the forward and of the adjoint against the oracle (exact solution;
+    implicit-function gradient at the oracle's own solution), worst over the batch."""
     import numpy as np
 
     import oracle
+    dt = "f64" if dtype.itemsize == 8 else "f32"
+    xs = x.double().cpu().numpy()
+    grs = gr.cpu().numpy()
+    gs = d["g"].double().cpu().numpy()
+    if general:
+        host = {k: d[k].double().cpu().numpy() for k in "abdlu"}
+        gh = {k: grads[k].double().cpu().numpy() for k in "abdlu"}
+        rs = d["r"].cpu().numpy()
+
+        def one(k):
+            s = slice(offs[k], offs[k + 1])
+            hk = [host[q][s] for q in "abdlu"]
+            ex = oracle.solve_sort(*hk, float(rs[k]))
+            e = err_general(hk, float(rs[k]), xs[s], ex, dt)
+            ref = oracle.grad_cqk(ex[2], ex[1], *hk, gs[s])
+            e["grad_rel"] = max(_x_rel(gh[q][s], ref[q]) for q in "abdlu")
+            e["grad_r_rel"] = abs(grs[k] - ref["r"]) / (1 + abs(ref["r"]))
+            return e
+    else:
+        ys = d["y"].double().cpu().numpy()
+        gy = grads["y"].double().cpu().numpy()
+
+        def one(k):
+            s = slice(offs[k], offs[k + 1])
+            lam, xstar = oracle.project_simplex_sort(ys[s], 1.0)
+            e = err_projection(xs[s], xstar, 1.0, dt)
+            ref = oracle.grad_simplex(xstar, gs[s])
+            e["grad_rel"] = _x_rel(gy[s], ref["y"])
+            e["grad_r_rel"] = abs(grs[k] - ref["r"]) / (1 + abs(ref["r"]))
+            return e
+
+    items = [e for e in pool_map(one, [k for k in range(B) if offs[k + 1] > offs[k]])]
+    out = _max_err(items)
+    out["tol_grad"] = 1e-10 if dt == "f64" else 1e-5
+    out["grad_basis"] = "oracle gradient at the oracle's own solution; an element whose free status is a tie " \
+                        "would show here as a large grad_rel"
+    return out
+
+
+# ------------------------------------------------------------------------------ oracle timing
+def _oracle_step(y, threads):
+    """One step of the CPU method on y: simplex and l1 projection, each by Alg. 2 then Alg. 4
+    (one thread: Alg. 2 over all of y; several: Alg. 2 per contiguous chunk, one chunk per
+    thread, and lambda_0 from the union of the J's, Sec. 4).  Returns phi evaluations."""
+    import oracle
     n = y.shape[0]
-    t = time.perf_counter()
     evals = 0
-    reps = 0
-    while True:
-        lam0, _, _ = oracle.condat_init(y, 1.0)
-        evals += oracle.newton_simplex(y, 1.0, lam0=lam0)["evals"]
-        lam0, _, _ = oracle.condat_init(y, 1.0, l1=True)
-        evals += oracle.newton_simplex(y, 1.0, lam0=lam0, l1=True)["evals"]
-        reps += 1
-        if time.perf_counter() - t > max_seconds / 3 or reps >= 3:
-            break
-    el = time.perf_counter() - t
-    return {"value": n * evals / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"first {n} elements of the n=1e8 vector, {reps} step(s) (simplex + l1, Alg. 2 start + "
-                      f"Alg. 4, sequential C oracle)",
-            "seconds": el, "host_cores_available": len(os.sched_getaffinity(0))}
+    for l1 in (False, True):
+        if threads == 1:
+            lam0, _, _ = oracle.condat_init(y, 1.0, l1=l1)
+        else:
+            lam0, _, _ = oracle.condat_chunks(y, 1.0, (n + threads - 1) // threads, threads, l1=l1)
+        evals += oracle.newton_simplex(y, 1.0, lam0=lam0, l1=l1)["evals"]
+    return evals
+
+
+def _time_oracle(y, threads, max_seconds, min_reps=3):
+    """Min and median seconds per step over repetitions (the paper's protocol: the minimum over
+    repeated runs), and the phi evaluations of a step."""
+    import oracle
+    prev = oracle.reference.set_threads(threads)
+    try:
+        times, evals = [], 0
+        t_start = time.perf_counter()
+        while True:
+            t0 = time.perf_counter()
+            evals = _oracle_step(y, threads)
+            times.append(time.perf_counter() - t0)
+            if len(times) >= min_reps and time.perf_counter() - t_start > max_seconds:
+                break
+            if len(times) >= 50:
+                break
+    finally:
+        oracle.reference.set_threads(prev)
+    return min(times), statistics.median(times), evals, len(times)
+
+
+def cpu_baseline(y):
+    """The FP64 oracle on the host cores for the same two projections: the sequential oracle
+    (Alg. 2 + Alg. 4) on one core on the first 2e7 elements; the same algorithms with
+    OpenMP-parallel passes and per-thread Alg. 2 chunks (the paper's CPU Jacobi form) on all
+    cores on the whole vector; and the sort-based projection on one core."""
+    import oracle
+    oracle.reference.build()
+    n = y.shape[0]
+    cores = host_cores()
+    t_min, t_med, evals, reps = _time_oracle(y, cores, max_seconds=10.0)
+    one = y[:CPU_SAMPLE]
+    o_min, o_med, o_evals, o_reps = _time_oracle(one, 1, max_seconds=8.0, min_reps=2)
+    t0 = time.perf_counter()
+    oracle.project_simplex_sort(one, 1.0)
+    sort_s = time.perf_counter() - t0
+    return {"value": n * evals / t_min, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"the whole n={n} vector, simplex + l1 per step, Alg. 2 per thread chunk ({cores} chunks) "
+                      f"+ Alg. 4 with OpenMP map-reduce passes; min over {reps} steps",
+            "seconds_per_step_min": t_min, "seconds_per_step_median": t_med, "phi_evaluations_per_step": evals,
+            "cpu_model": cpu_model(),
+            "one_core": {"value": one.shape[0] * o_evals / o_min, "unit": UNIT, "cores": 1,
+                         "sample": f"first {one.shape[0]} elements, sequential Alg. 2 + Alg. 4, min over "
+                                   f"{o_reps} steps", "seconds_per_step_min": o_min,
+                         "seconds_per_step_median": o_med},
+            "sort_oracle_one_core": {"seconds_per_projection": sort_s, "elements": one.shape[0],
+                                     "elements_per_s": one.shape[0] / sort_s,
+                                     "what": "textbook sort-based simplex projection (the exact checker)"}}
 
 
 def run_reference(args, world, rank):
     if rank != 0:
         return None
-    import torch
-
     from paper_2603_15910_b300 import workloads as W
-    y = W.simplex_normal(args.n, seed=0, device="cpu")[:CPU_SAMPLE].numpy()
     import oracle
     oracle.reference.build()
-    for _ in range(min(args.warmup, 1)):
-        cpu_baseline(y[:1_000_000])
-    vals = []
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        vals.append(cpu_baseline(y, max_seconds=10.0))
-        if time.perf_counter() - t0 > 150:
-            break
-    v = statistics.median([c["value"] for c in vals])
-    cb = dict(vals[0])
-    cb["value"] = v
-    return {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": len(vals), "warmup": args.warmup,
-            "ms_per_step": 1e3 * statistics.median([c["seconds"] for c in vals]), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+    y = W.simplex_normal(args.n, seed=0, device="cpu").numpy()
+    cores = host_cores()
+    prev = oracle.reference.set_threads(cores)
+    try:
+        for _ in range(min(args.warmup, 1)):
+            _oracle_step(y[:1_000_000], cores)
+        times, evals = [], 0
+        t_start = time.perf_counter()
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            evals = _oracle_step(y, cores)
+            times.append(time.perf_counter() - t0)
+            if time.perf_counter() - t_start > 150:
+                break
+    finally:
+        oracle.reference.set_threads(prev)
+    ms = 1e3 * sum(times) / len(times)
+    v = args.n * evals * len(times) / sum(times)
+    cb = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu_model": cpu_model(),
+          "sample": f"the whole n={args.n} vector (y~N(0,1) from the CPU generator), simplex + l1 per step, "
+                    f"Alg. 2 per thread chunk + Alg. 4 with OpenMP map-reduce passes on {cores} cores"}
+    return {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": len(times), "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
             "config": {"workload": "simplex + l1-ball projection, n=1e8, FP64, y~N(0,1), r=1, Condat start",
-                       "n": args.n, "sample": CPU_SAMPLE},
+                       "n": args.n},
             "cpu_baseline": cb, "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -604,6 +971,7 @@ def main():
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--no-extras", dest="extras", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-oracle-check", dest="oracle_check", action="store_false")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
