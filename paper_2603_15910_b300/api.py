@@ -344,6 +344,13 @@ def project_l1(y, r=1.0, *, init=Init.CONDAT, max_iter=100, lambda0=0.0, validat
 
 def _batch_args(arrays, offsets, r):
     host, dev, arrays = _on_device(list(arrays))
+    if not (torch.is_tensor(offsets) and offsets.device.type == "cuda"):
+        # offsets given on the host: the instances must lie inside the arrays (device offsets
+        # are read by the kernels only; a decreasing pair is reported per instance there)
+        off_h = torch.as_tensor(offsets, dtype=torch.int64)
+        if off_h.numel() and (int(off_h[0]) < 0 or int(off_h[-1]) > arrays[0].numel()):
+            raise ValueError(f"offsets span [{int(off_h[0])}, {int(off_h[-1])}) outside the {arrays[0].numel()} "
+                             "elements of the arrays")
     offsets = torch.as_tensor(offsets, dtype=torch.int64).to(dev).contiguous()
     r = torch.as_tensor(r, dtype=torch.float64).to(dev).contiguous()
     _check_device(*arrays, offsets, r)

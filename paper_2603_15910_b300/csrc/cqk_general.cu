@@ -134,16 +134,14 @@ __device__ __noinline__ double elem_f64_exact(double a, double b, double d, doub
 }
 
 // ---- FP64 data in the df range ----------------------------------------------------------
-// v = a + lambda b (fused df), 1/d by the MUFU reciprocal and one df Newton correction,
+// From v = a + lambda b (df): 1/d by the MUFU reciprocal and one df Newton correction,
 // t = v/d, and the status of x_i(lambda) read off t against l, u (equivalent to v against
-// d l, d u for d > 0) with the tie band of the file header, scaled to x.
+// d l, d u for d > 0).  TIES: elements within the tie band of the file header (scn = |a| +
+// |lambda b| in float, scaled to x) count as lying on their breakpoint; without TIES the
+// classification is the plain sign test (a pass whose lambda is not a breakpoint).
 // Returns x; bx = b x, beta = b^2/d.
-template <bool FIN>
-__device__ __forceinline__ df elem_df(df A, df B, df D, df Lo, df Up, df Lm, Cls& cl, df& bx, df& beta) {
-    const df p = two_prod(Lm.hi, B.hi);
-    const float e = fmaf(Lm.hi, B.lo, fmaf(Lm.lo, B.hi, p.lo));
-    const df s = two_sum(A.hi, p.hi);
-    const df v = fast_two_sum(s.hi, __fadd_rn(__fadd_rn(s.lo, e), A.lo));
+template <bool FIN, bool TIES>
+__device__ __forceinline__ df elem_df_tail(df v, float scn, df B, df D, df Lo, df Up, Cls& cl, df& bx, df& beta) {
     const float r0 = rcp_approx(D.hi);
     const float res = fmaf(-D.lo, r0, fmaf(-D.hi, r0, 1.0f));
     const df invd = fast_two_sum(r0, __fmul_rn(r0, res));
@@ -151,9 +149,12 @@ __device__ __forceinline__ df elem_df(df A, df B, df D, df Lo, df Up, df Lm, Cls
     const bool linf = !FIN && isinf(Lo.hi), uinf = !FIN && isinf(Up.hi);  // FIN: finite bounds
     const float dL = __fadd_rn(__fsub_rn(t.hi, Lo.hi), __fsub_rn(t.lo, Lo.lo));
     const float dU = __fadd_rn(__fsub_rn(t.hi, Up.hi), __fsub_rn(t.lo, Up.lo));
-    const float sc = __fmul_rn(__fadd_rn(fabsf(A.hi), fabsf(p.hi)), r0);  // (|a| + |lambda b|)/d
-    const bool tieL = !linf && fabsf(dL) <= kTieRel * (sc + fabsf(Lo.hi));
-    const bool tieU = !uinf && fabsf(dU) <= kTieRel * (sc + fabsf(Up.hi));
+    bool tieL = false, tieU = false;
+    if constexpr (TIES) {
+        const float sc = __fmul_rn(scn, r0);  // (|a| + |lambda b|)/d
+        tieL = !linf && fabsf(dL) <= kTieRel * (sc + fabsf(Lo.hi));
+        tieU = !uinf && fabsf(dU) <= kTieRel * (sc + fabsf(Up.hi));
+    }
     const bool below = tieL || dL < 0.0f;
     const bool above = !below && (tieU || dU > 0.0f);
     cl.c = below ? 1 : (above ? 2 : 0);
@@ -163,8 +164,18 @@ __device__ __forceinline__ df elem_df(df A, df B, df D, df Lo, df Up, df Lm, Cls
     if (below) x = Lo;
     if (above) x = Up;
     bx = df_mul_lazy(B, x);
-    beta = df_mul_lazy(df_mul(B, B), invd);
+    beta = df_mul_lazy(df_mul_lazy(B, B), invd);  // unnormalised chain: ~2^-46 relative
     return x;
+}
+
+// v = a + lambda b in df from the split a, b and lambda (TwoProd + TwoSum)
+template <bool FIN, bool TIES>
+__device__ __forceinline__ df elem_df(df A, df B, df D, df Lo, df Up, df Lm, Cls& cl, df& bx, df& beta) {
+    const df p = two_prod(Lm.hi, B.hi);
+    const float e = fmaf(Lm.hi, B.lo, fmaf(Lm.lo, B.hi, p.lo));
+    const df s = two_sum(A.hi, p.hi);
+    const df v = fast_two_sum(s.hi, __fadd_rn(__fadd_rn(s.lo, e), A.lo));
+    return elem_df_tail<FIN, TIES>(v, __fadd_rn(fabsf(A.hi), fabsf(p.hi)), B, D, Lo, Up, cl, bx, beta);
 }
 
 // sanity checks of Sec. 5.1.1 on the bit patterns: d > 0, b > 0 finite; a finite; l <= u;
@@ -190,7 +201,7 @@ __device__ __forceinline__ bool bad_elem_f(float a, float b, float d, float l, f
 // MUFU reciprocal and one correction (~1 ulp); the status is read off t against l, u with a
 // tie band of 2^-20 relative (the float rounding of t); b x by TwoProd; b^2/d in float.
 constexpr float kTieRel32 = 9.5367431640625e-07f;  // 2^-20
-template <bool FIN>
+template <bool FIN, bool TIES>
 __device__ __forceinline__ float elem_f32(float a, float b, float d, float l, float u, df Lm, Cls& cl, df& bx,
                                           float& beta) {
     const df p = two_prod(Lm.hi, b);
@@ -202,9 +213,12 @@ __device__ __forceinline__ float elem_f32(float a, float b, float d, float l, fl
     t = fmaf(fmaf(-t, d, vh), r0, t);
     const bool linf = !FIN && isinf(l), uinf = !FIN && isinf(u);
     const float dL = __fsub_rn(t, l), dU = __fsub_rn(t, u);
-    const float sc = __fmul_rn(__fadd_rn(fabsf(a), fabsf(p.hi)), r0);
-    const bool tieL = !linf && fabsf(dL) <= kTieRel32 * (sc + fabsf(l));
-    const bool tieU = !uinf && fabsf(dU) <= kTieRel32 * (sc + fabsf(u));
+    bool tieL = false, tieU = false;
+    if constexpr (TIES) {
+        const float sc = __fmul_rn(__fadd_rn(fabsf(a), fabsf(p.hi)), r0);
+        tieL = !linf && fabsf(dL) <= kTieRel32 * (sc + fabsf(l));
+        tieU = !uinf && fabsf(dU) <= kTieRel32 * (sc + fabsf(u));
+    }
     const bool below = tieL || dL < 0.0f;
     const bool above = !below && (tieU || dU > 0.0f);
     cl.c = below ? 1 : (above ? 2 : 0);
@@ -225,7 +239,9 @@ __device__ __forceinline__ float elem_f32(float a, float b, float d, float l, fl
 // warp's first vector (a multiple of 32).
 // FAST: every FP64 value is known to be valid and inside the df operating range (checked in
 // the first pass), so the per-element checks are skipped.
-template <typename T, bool FAST, bool FIN>
+// TIES: the tie band of the file header is tested (passes whose lambda may sit on a breakpoint:
+// the first, the final pass and those after a breakpoint step); otherwise the plain sign test.
+template <typename T, bool FAST, bool FIN, bool TIES = true>
 __device__ __forceinline__ void eval_vec(const GeneralArgs& A, const T (&va)[VecOf<T>::V], const T (&vb)[VecOf<T>::V],
                                          const T (&vd)[VecOf<T>::V], const T (&vl)[VecOf<T>::V],
                                          const T (&vu)[VecOf<T>::V], const bool (&ok)[VecOf<T>::V], int64_t q,
@@ -249,13 +265,14 @@ __device__ __forceinline__ void eval_vec(const GeneralArgs& A, const T (&va)[Vec
             Cls cl;
             df bx;
             if constexpr (sizeof(T) == 8) {
-                df Ad, Bd, Dd, Ld, Ud;
+                df Ad, Bd, Dd, Ld, Ud, xv;
                 if constexpr (FAST) {
                     Ad = split_f64_finite(a);
                     Bd = split_f64_pos(b);  // b, d > 0 inside the range (checked in the first pass)
                     Dd = split_f64_pos(d);
                     Ld = FIN ? split_f64_finite(l) : split_f64(l);  // FIN: no infinite bound (first pass)
                     Ud = FIN ? split_f64_finite(u) : split_f64(u);
+                    xv = elem_df<FIN, TIES>(Ad, Bd, Dd, Ld, Ud, Lm, cl, bx, beta[j]);
                 } else {
                     // operating range by exponent-field tests: b, d positive in [2^-60, 2^60];
                     // a 0 or in range; l, u 0, +-inf or in range.  In-range values are finite and
@@ -283,8 +300,8 @@ __device__ __forceinline__ void eval_vec(const GeneralArgs& A, const T (&va)[Vec
                     Ld = split_f64(l);
                     Ud = split_f64(u);
                     if (check) acc.bad |= df_lt(Ud, Ld);
+                    xv = elem_df<FIN, TIES>(Ad, Bd, Dd, Ld, Ud, Lm, cl, bx, beta[j]);
                 }
-                const df xv = elem_df<FIN>(Ad, Bd, Dd, Ld, Ud, Lm, cl, bx, beta[j]);
                 if (write_x) {
                     xo[j] = cl.c == 1 ? l : (cl.c == 2 ? u : 0.0);
                     freem |= (cl.c == 0 ? 1u : 0u) << j;
@@ -297,7 +314,7 @@ __device__ __forceinline__ void eval_vec(const GeneralArgs& A, const T (&va)[Vec
                 if (!FAST && check) acc.bad |= bad_elem_f(a, b, d, l, u);
                 if (!FAST) acc.luinf |= isinf(l) || isinf(u);
                 float bt;
-                xo[j] = elem_f32<FIN>(a, b, d, l, u, Lm, cl, bx, bt);
+                xo[j] = elem_f32<FIN, TIES>(a, b, d, l, u, Lm, cl, bx, bt);
                 beta[j] = df_make(bt);
             }
             fr[j] = cl.c == 0;
@@ -307,13 +324,15 @@ __device__ __forceinline__ void eval_vec(const GeneralArgs& A, const T (&va)[Vec
                 else lazy_add(acc.absbx, bx.hi < 0.0f ? df_neg(bx) : bx);
                 lazy_add(acc.sfree, fr[j] ? beta[j] : df_make(0.0f));
             }
-            tiem |= ((cl.tieL && !cl.tieU) ? 1u : 0u) << (2 * j);
-            tiem |= ((cl.tieU && !cl.tieL) ? 2u : 0u) << (2 * j);
+            if constexpr (TIES) {
+                tiem |= ((cl.tieL && !cl.tieU) ? 1u : 0u) << (2 * j);
+                tiem |= ((cl.tieU && !cl.tieL) ? 2u : 0u) << (2 * j);
+            }
         }
         // rare cases, one loop trip per element concerned (a data-dependent loop keeps FP64
         // instructions off the common path): elements on a breakpoint (lateral-slope ties)
         // and FP64 values outside the df operating range (exact FP64)
-        if (!write_x) {
+        if (TIES && !write_x) {
             for (unsigned m = tiem; m; m &= m - 1) {
                 const int bit = __ffs(m) - 1;
                 const double bj = df_to_f64(pick(beta, bit >> 1));
@@ -362,7 +381,7 @@ __device__ __forceinline__ void eval_vec(const GeneralArgs& A, const T (&va)[Vec
 }
 
 // ---- one pass over all elements with plain loads (arrays not 16-byte aligned)
-template <typename T, bool FAST, bool FIN>
+template <typename T, bool FAST, bool FIN, bool TIES>
 __device__ __forceinline__ void eval_pass_plain(const GeneralArgs& A, const Grp& gp, double lam, bool write_x,
                                                 bool check, bool rev, EvalAcc& acc) {
     constexpr int V = VecOf<T>::V;
@@ -398,8 +417,8 @@ __device__ __forceinline__ void eval_pass_plain(const GeneralArgs& A, const Grp&
         }
 #pragma unroll
         for (int w = 0; w < U; w++)
-            eval_vec<T, FAST, FIN>(A, va[w], vb[w], vd[w], vl[w], vu[w], ok[w], base + w * 32 + lane, base + w * 32, lam, Lm,
-                              lam_ok, write_x, check, acc, sp);
+            eval_vec<T, FAST, FIN, TIES>(A, va[w], vb[w], vd[w], vl[w], vu[w], ok[w], base + w * 32 + lane, base + w * 32,
+                                         lam, Lm, lam_ok, write_x, check, acc, sp);
     }
 }
 
@@ -407,7 +426,7 @@ __device__ __forceinline__ void eval_pass_plain(const GeneralArgs& A, const Grp&
 template <typename T>
 __host__ __device__ constexpr int stage_tile() { return kGenTileBytes / (int)sizeof(T); }  // elements per array per stage
 
-template <typename T, bool FAST, bool FIN>
+template <typename T, bool FAST, bool FIN, bool TIES>
 __device__ __forceinline__ bool eval_pass_staged(const GeneralArgs& A, const Grp& gp, double lam, bool write_x,
                                                  bool check, bool rev, EvalAcc& acc, T* smem, uint64_t* bars,
                                                  unsigned& parity, int* err) {
@@ -465,7 +484,7 @@ __device__ __forceinline__ bool eval_pass_staged(const GeneralArgs& A, const Grp
                 load_vec<T>(src[3], sp, q, false, vl, ok);
                 load_vec<T>(src[4], sp, q, false, vu, ok);
             }
-            eval_vec<T, FAST, FIN>(A, va, vb, vd, vl, vu, ok, q, qw, lam, Lm, lam_ok, write_x, check, acc, sp);
+            eval_vec<T, FAST, FIN, TIES>(A, va, vb, vd, vl, vu, ok, q, qw, lam, Lm, lam_ok, write_x, check, acc, sp);
         }
         __syncthreads();  // the stage is refilled only after every thread has read it
     }
@@ -474,12 +493,13 @@ __device__ __forceinline__ bool eval_pass_staged(const GeneralArgs& A, const Grp
 }
 
 // one pass over all elements, staged or plain
-template <typename T, bool FAST, bool FIN = false>
+template <typename T, bool FAST, bool FIN = false, bool TIES = true>
 __device__ __forceinline__ bool eval_pass(const GeneralArgs& A, const Grp& gp, double lam, bool write_x, bool check,
                                           bool rev, EvalAcc& acc, T* smem, uint64_t* bars, unsigned& parity,
                                           int* err) {
-    if (A.staged) return eval_pass_staged<T, FAST, FIN>(A, gp, lam, write_x, check, rev, acc, smem, bars, parity, err);
-    eval_pass_plain<T, FAST, FIN>(A, gp, lam, write_x, check, rev, acc);
+    if (A.staged)
+        return eval_pass_staged<T, FAST, FIN, TIES>(A, gp, lam, write_x, check, rev, acc, smem, bars, parity, err);
+    eval_pass_plain<T, FAST, FIN, TIES>(A, gp, lam, write_x, check, rev, acc);
     return true;
 }
 
@@ -806,6 +826,7 @@ __device__ __forceinline__ void general_solve(const GeneralArgs& A, const Grp& g
     bool bad_input = false;
     bool wide_data = true;  // until the first pass has checked every value
     bool fin_data = false;  // every bound finite (known after the first pass)
+    bool lam_on_bp = false; // lambda is a breakpoint (set by a breakpoint step): ties possible
     for (k = 0;; k++) {
         if (k >= A.max_iter) {
             status = CQK_MAXITER;
@@ -813,11 +834,20 @@ __device__ __forceinline__ void general_solve(const GeneralArgs& A, const Grp& g
         }
         EvalAcc acc;
         acc.init();
-        if (k > 0 && !wide_data && fin_data)
-            eval_pass<T, true, true>(A, gp, lam, false, false, (k & 1) == 1, acc, smem, ring_bars, ring_parity, err);
+        // a lambda from a Newton or secant step lies on an element's breakpoint only by chance, and
+        // then the plain sign test classifies the element as exact arithmetic would; the tie band
+        // of the file header is needed after a breakpoint step (and in the first pass, whose
+        // range checks come with it)
+        const bool rev = (k & 1) == 1;
+        if (k > 0 && !wide_data && fin_data && !lam_on_bp)
+            eval_pass<T, true, true, false>(A, gp, lam, false, false, rev, acc, smem, ring_bars, ring_parity, err);
+        else if (k > 0 && !wide_data && fin_data)
+            eval_pass<T, true, true, true>(A, gp, lam, false, false, rev, acc, smem, ring_bars, ring_parity, err);
+        else if (k > 0 && !wide_data && !lam_on_bp)
+            eval_pass<T, true, false, false>(A, gp, lam, false, false, rev, acc, smem, ring_bars, ring_parity, err);
         else if (k > 0 && !wide_data)
-            eval_pass<T, true>(A, gp, lam, false, false, (k & 1) == 1, acc, smem, ring_bars, ring_parity, err);
-        else eval_pass<T, false>(A, gp, lam, false, k == 0 && A.validate, (k & 1) == 1, acc, smem, ring_bars, ring_parity, err);
+            eval_pass<T, true, false, true>(A, gp, lam, false, false, rev, acc, smem, ring_bars, ring_parity, err);
+        else eval_pass<T, false>(A, gp, lam, false, k == 0 && A.validate, rev, acc, smem, ring_bars, ring_parity, err);
         acc.flush();
         passes++;
         if (__any_sync(0xffffffffu, acc.bad) && (threadIdx.x & 31) == 0) atomicOr(&gp.hdr->flags, kFlagBadInput);
@@ -933,6 +963,7 @@ __device__ __forceinline__ void general_solve(const GeneralArgs& A, const Grp& g
             }
             next = m;
         }
+        lam_on_bp = need_bp != 0;
         if (upper - lower < A.eps34 * fmax(fabs(upper), fabs(lower))) {
             stop = CQK_STOP_BRACKET;
             k++;

@@ -268,7 +268,7 @@ def test_projection_backward_unaligned_and_batched_staging(dtype):
     out_u = api.backward("simplex", gbig[1:], x, ws.info, mask=mask)  # g only 4/8-byte aligned
     _close(np64(out_u["y"]), ref["y"], dtype, "unaligned")
     assert abs(float(out_u["r"][0]) - ref["r"]) <= TOL[dtype] * (1 + abs(ref["r"]))
-    lens = [5000, 0, 3, 40000, 1, 25000]
+    lens = [5000, 0, 3, 40000, 1, 24997]  # the whole array of n = 70001
     off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
     offd = torch.from_numpy(off).to(DEV)
     yb = y[: int(off[-1])].contiguous()
