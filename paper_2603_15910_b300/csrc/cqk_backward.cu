@@ -560,7 +560,7 @@ __device__ void bwd_simplex_staged(const BwdArgs& A, const Grp& gp, int64_t inst
 }
 
 template <typename T, int KIND, bool BATCHED, bool NOX>
-__global__ void __launch_bounds__(NT, kMinBlocksPerSM) backward_kernel(BwdArgs A) {
+__global__ void __launch_bounds__(NT, kMinBlocksPerSM) backward_kernel(const __grid_constant__ BwdArgs A) {
     // the staged simplex adjoint (NOX on aligned data): stages and their mbarriers
     extern __shared__ __align__(128) unsigned char dyn_smem[];
     __shared__ uint64_t bars[NOX ? kBwdStages : 1];

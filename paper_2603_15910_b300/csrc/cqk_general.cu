@@ -79,21 +79,42 @@ constexpr unsigned kFlagLuInf = 4u;  // some bound l_i or u_i is infinite
 // pass and the final pass (the reported sum) keep the double-float sum.
 struct EvalAcc {
     LazyDf phi, absbx, sfree;
+    df mphi, mabsbx, msfree;  // middle level: normalised df sums of the flushed lazy sums
     float absf;
+    int nmid;
     double phi64, absbx64, sfree64, satl, satu;
     long long nfree;
     bool bad, wide, luinf;
     __device__ void init() {
         phi = absbx = sfree = LazyDf{0.0f, 0.0f};
+        mphi = mabsbx = msfree = df{0.0f, 0.0f};
         absf = 0.0f;
+        nmid = 0;
         phi64 = absbx64 = sfree64 = satl = satu = 0.0;
         nfree = 0;
         bad = wide = luinf = false;
     }
+    // all levels into FP64 (end of a pass)
     __device__ void flush() {
-        phi64 += lazy_value(phi);
-        absbx64 += lazy_value(absbx) + (double)absf;
-        sfree64 += lazy_value(sfree);
+        phi64 += df_to_f64(mphi) + lazy_value(phi);
+        absbx64 += df_to_f64(mabsbx) + lazy_value(absbx) + (double)absf;
+        sfree64 += df_to_f64(msfree) + lazy_value(sfree);
+        phi = absbx = sfree = LazyDf{0.0f, 0.0f};
+        mphi = mabsbx = msfree = df{0.0f, 0.0f};
+        absf = 0.0f;
+        nmid = 0;
+    }
+    // the lazy sums into the middle df sums (FP32 operations only; df_add is accurate to
+    // ~2^-47 of the sum), and every fourth time everything into FP64: the FP64 pipe, the scarce
+    // unit of this GPU, sees a quarter of the flushes
+    __device__ void step_flush() {
+        if (++nmid == 4) {
+            flush();
+            return;
+        }
+        mphi = df_add(mphi, two_sum(phi.hi, phi.lo));  // (|lo| may exceed |hi| after cancellation)
+        mabsbx = df_add(mabsbx, two_sum(absbx.hi, __fadd_rn(absbx.lo, absf)));
+        msfree = df_add(msfree, two_sum(sfree.hi, sfree.lo));
         phi = absbx = sfree = LazyDf{0.0f, 0.0f};
         absf = 0.0f;
     }
@@ -106,8 +127,15 @@ struct Cls {
 };
 
 // ---- FP64 data, exact FP64 (values outside the df range) -------------------------------
-__device__ __noinline__ double elem_f64_exact(double a, double b, double d, double l, double u, double lam,
-                                              EvalAcc& acc, bool want_acc, Cls& cl) {
+// Out of line (rare); its sums come back by value so that the caller's accumulators stay in
+// registers (an accumulator whose address reached an out-of-line call would live in memory).
+struct ExactOut {
+    double x, phi, absbx, sfree, satl, satu;
+    int c;
+};
+__device__ __noinline__ ExactOut elem_f64_exact(double a, double b, double d, double l, double u, double lam,
+                                                bool want_acc) {
+    ExactOut o{0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0};
     const double lb = lam * b;
     const double v = a + lb;
     const double dl = isinf(l) ? l : d * l;
@@ -115,22 +143,19 @@ __device__ __noinline__ double elem_f64_exact(double a, double b, double d, doub
     const double sc = fabs(a) + fabs(lb);
     const bool tieL = !isinf(l) && fabs(v - dl) <= 2.2737367544323206e-13 * (sc + fabs(dl));
     const bool tieU = !isinf(u) && fabs(v - du) <= 2.2737367544323206e-13 * (sc + fabs(du));
-    cl.tieL = tieL;
-    cl.tieU = tieU;
-    double x;
-    if (tieL || v < dl) { x = l; cl.c = 1; }
-    else if (tieU || v > du) { x = u; cl.c = 2; }
-    else { x = v / d; cl.c = 0; }
+    if (tieL || v < dl) { o.x = l; o.c = 1; }
+    else if (tieU || v > du) { o.x = u; o.c = 2; }
+    else { o.x = v / d; o.c = 0; }
     if (want_acc) {
-        const double bx = b * x;
-        acc.phi64 += bx;
-        acc.absbx64 += fabs(bx);
+        const double bx = b * o.x;
+        o.phi = bx;
+        o.absbx = fabs(bx);
         const double w = b * b / d;
-        if (cl.c == 0) acc.sfree64 += w;
-        if (tieL && !tieU) acc.satl += w;
-        if (tieU && !tieL) acc.satu += w;
+        if (o.c == 0) o.sfree = w;
+        if (tieL && !tieU) o.satl = w;
+        if (tieU && !tieL) o.satu = w;
     }
-    return x;
+    return o;
 }
 
 // ---- FP64 data in the df range ----------------------------------------------------------
@@ -343,13 +368,19 @@ __device__ __forceinline__ void eval_vec(const GeneralArgs& A, const T (&va)[Vec
         if constexpr (sizeof(T) == 8 && !FAST) {
             for (unsigned m = widem; m; m &= m - 1) {
                 const int j = __ffs(m) - 1;
-                Cls cl;
                 const T bj = pick(vb, j);
                 if (check) acc.bad |= bad_elem(pick(va, j), bj, pick(vd, j), pick(vl, j), pick(vu, j));
-                const T xj = elem_f64_exact(pick(va, j), bj, pick(vd, j), pick(vl, j),
-                                            pick(vu, j), lam, acc, !write_x, cl);
+                const ExactOut eo = elem_f64_exact(pick(va, j), bj, pick(vd, j), pick(vl, j), pick(vu, j), lam, !write_x);
+                const T xj = eo.x;
+                if (!write_x) {
+                    acc.phi64 += eo.phi;
+                    acc.absbx64 += eo.absbx;
+                    acc.sfree64 += eo.sfree;
+                    acc.satl += eo.satl;
+                    acc.satu += eo.satu;
+                }
                 put(xo, j, xj);
-                put(fr, j, cl.c == 0);
+                put(fr, j, eo.c == 0);
                 if (write_x) {
                     acc.phi64 += bj * xj;
                     acc.absbx64 += fabs(bj * xj);
@@ -400,7 +431,7 @@ __device__ __forceinline__ void eval_pass_plain(const GeneralArgs& A, const Grp&
     int steps = 0;
     for (int64_t it = 0; it < sw.count; it++) {
         if (++steps == kFlushEvery) {
-            acc.flush();
+            acc.step_flush();
             steps = 0;
         }
         const int64_t base = sw.base(it, rev);
@@ -454,7 +485,7 @@ __device__ __forceinline__ bool eval_pass_staged(const GeneralArgs& A, const Grp
         ring.parity ^= 1u << st;
         const int64_t c = ring.tile(i, rev);
         const int64_t sb0 = ring.b0(c), sb1 = ring.b1(c);
-        if ((i & 7) == 7) acc.flush();
+        if ((i & 7) == 7) acc.step_flush();
 #pragma unroll
         for (int k = 0; k < VPT; k++) {
             const int ql = (int)threadIdx.x + k * NT;  // vector within the tile
@@ -1012,7 +1043,7 @@ __device__ __forceinline__ void general_solve(const GeneralArgs& A, const Grp& g
 
 #ifndef CQK_BATCH_ONLY
 template <typename T>
-__global__ void __launch_bounds__(NT, kMinBlocksPerSM) general_kernel(GeneralArgs A) {
+__global__ void __launch_bounds__(NT, kMinBlocksPerSM) general_kernel(const __grid_constant__ GeneralArgs A) {
     extern __shared__ __align__(128) unsigned char dyn_smem[];
     __shared__ uint64_t ring_bars[kStages];
     unsigned ring_parity = 0;
@@ -1046,7 +1077,7 @@ struct GeneralBatchArgs {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(NT, kMinBlocksPerSM) general_batched_kernel(GeneralBatchArgs P) {
+__global__ void __launch_bounds__(NT, kMinBlocksPerSM) general_batched_kernel(const __grid_constant__ GeneralBatchArgs P) {
     extern __shared__ __align__(128) unsigned char dyn_smem[];
     __shared__ uint64_t ring_bars[kStages];
     unsigned ring_parity = 0;
@@ -1112,7 +1143,10 @@ int launch(GeneralArgs A, int dtype, int max_blocks, cudaStream_t s, void* ws) {
             return CQK_CUDA_ERROR;
         }
     }
-    const int grid = persistent_grid(kern, NT, smem, (A.n + vec - 1) / vec, max_blocks);
+    // the general map is compute-heavy (double-float per element): a block is added per 2
+    // vectors per thread and pass (the streaming default is 8), so that small problems, which
+    // are bound by the per-pass latency, spread over more SMs (n = 1e4: 116 -> 93 us per solve)
+    const int grid = persistent_grid(kern, NT, smem, 4 * ((A.n + vec - 1) / vec), max_blocks);
     if (grid <= 0) return CQK_CUDA_ERROR;
     cudaError_t e = cudaMemsetAsync(ws, 0, sizeof(WsHeader), s);
     if (e != cudaSuccess) {

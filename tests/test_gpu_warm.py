@@ -55,7 +55,9 @@ def test_general_warm_start_empty_free_set_is_the_cold_start():
     dev = [p[k].to(DEV) for k in "abdlu"]
     _, warm, _ = api.solve(*dev, p["r"], init=api.Init.WARM, xbar=xbar)
     _, cold, _ = api.solve(*dev, p["r"])
-    assert warm.lambda0 == cold.lambda0 and warm.iters == cold.iters
+    # the same formula over all variables; the two passes sum in different orders (plain loads
+    # vs the staged tiles of the cold start), so lambda_0 agrees to rounding
+    assert math.isclose(warm.lambda0, cold.lambda0, rel_tol=1e-13) and warm.iters == cold.iters
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
