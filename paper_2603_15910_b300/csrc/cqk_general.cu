@@ -259,6 +259,32 @@ __device__ __forceinline__ float elem_f32(float a, float b, float d, float l, fl
     return x;
 }
 
+// l < x strictly, as doubles, on order keys (-0 taken as +0; a NaN x is never inside)
+__device__ __forceinline__ long long cmp_key(double v) {
+    const unsigned long long b = opaque_bits(v);
+    return (b << 1) == 0ull ? 0ll : order_key(v);
+}
+template <typename T>
+__device__ __forceinline__ bool strictly_inside(T l, T x, T u) {
+    if constexpr (sizeof(T) == 8) {
+        const long long kx = cmp_key(x);
+        return cmp_key(l) < kx && kx < cmp_key(u) && !f64_is_nan(x);
+    } else {
+        return l < x && x < u;
+    }
+}
+
+// x clamped to [l, u] exactly (l <= u, no NaN: checked data); order keys for doubles
+template <typename T>
+__device__ __forceinline__ T clamp_exact(T l, T x, T u) {
+    if constexpr (sizeof(T) == 8) {
+        const long long kx = cmp_key(x);
+        return kx < cmp_key(l) ? l : (kx > cmp_key(u) ? u : x);
+    } else {
+        return x < l ? l : (x > u ? u : x);
+    }
+}
+
 // ---- the map of one 16-byte vector of elements (V of them): accumulate (write_x = false)
 // or write x / mask and the sums of the stored x.  q = global vector index, qw = index of the
 // warp's first vector (a multiple of 32).
@@ -388,13 +414,24 @@ __device__ __forceinline__ void eval_vec(const GeneralArgs& A, const T (&va)[Vec
             }
         }
         if (write_x) {
-            // free x of FP64 data: df -> double, one FP64 add per free element
+            // free x of FP64 data: df -> double, one FP64 add per free element (measured faster here
+            // than the integer-pipe conversion)
             if constexpr (sizeof(T) == 8) {
-                for (unsigned m = freem; m; m &= m - 1) {
-                    const int j = __ffs(m) - 1;
-                    put(xo, j, df_to_f64_int(pick(xdf, j)));
-                }
-            } else {
+#pragma unroll
+                for (int j = 0; j < V; j++)
+                    if ((freem >> j) & 1u) xo[j] = df_to_f64_int(xdf[j]);
+            }
+            // without the tie band a rounded t may land on a bound (or a hair past it): the stored x
+            // of a free element is kept inside [l, u] exactly and its mask bit is read off it
+            if constexpr (!TIES) {
+#pragma unroll
+                for (int j = 0; j < V; j++)
+                    if (ok[j] && fr[j]) {
+                        xo[j] = clamp_exact<T>(vl[j], xo[j], vu[j]);
+                        fr[j] = strictly_inside<T>(vl[j], xo[j], vu[j]);
+                    }
+            }
+            if constexpr (sizeof(T) != 8) {
                 // FP32 data: sums of the stored (float) x, b x exact by TwoProd
 #pragma unroll
                 for (int j = 0; j < V; j++) {
@@ -691,21 +728,6 @@ __device__ __forceinline__ bool lambda0_pass(const GeneralArgs& A, const Grp& gp
     return okw;
 }
 
-// l < x strictly, as doubles, on order keys (-0 taken as +0; a NaN x is never inside)
-__device__ __forceinline__ long long cmp_key(double v) {
-    const unsigned long long b = opaque_bits(v);
-    return (b << 1) == 0ull ? 0ll : order_key(v);
-}
-template <typename T>
-__device__ __forceinline__ bool strictly_inside(T l, T x, T u) {
-    if constexpr (sizeof(T) == 8) {
-        const long long kx = cmp_key(x);
-        return cmp_key(l) < kx && kx < cmp_key(u) && !f64_is_nan(x);
-    } else {
-        return l < x && x < u;
-    }
-}
-
 // Warm start (Sec. 2): the sums of eq. (CQKlambda0) over J = {l < xbar < u} and over all
 // variables, and |J|, in one pass with plain loads.  out = {s_J, q_J, |J|, s_all, q_all}.
 template <typename T>
@@ -857,7 +879,9 @@ __device__ __forceinline__ void general_solve(const GeneralArgs& A, const Grp& g
     bool bad_input = false;
     bool wide_data = true;  // until the first pass has checked every value
     bool fin_data = false;  // every bound finite (known after the first pass)
-    bool lam_on_bp = false; // lambda is a breakpoint (set by a breakpoint step): ties possible
+    // lambda may sit exactly on a breakpoint (it came from a breakpoint step, or is the caller's
+    // start): only then is the tie band tested
+    bool lam_on_bp = A.init == CQK_INIT_GIVEN;
     for (k = 0;; k++) {
         if (k >= A.max_iter) {
             status = CQK_MAXITER;
@@ -865,11 +889,12 @@ __device__ __forceinline__ void general_solve(const GeneralArgs& A, const Grp& g
         }
         EvalAcc acc;
         acc.init();
-        // a lambda from a Newton or secant step lies on an element's breakpoint only by chance, and
-        // then the plain sign test classifies the element as exact arithmetic would; the tie band
-        // of the file header is needed after a breakpoint step (and in the first pass, whose
-        // range checks come with it)
+        // a lambda from eq. (CQKlambda0) or a Newton or secant step lies on an element's breakpoint
+        // only by chance, and then the plain sign test classifies the element as exact arithmetic
+        // would; the tie band of the file header is needed after a breakpoint step (or at a start
+        // the caller gave)
         const bool rev = (k & 1) == 1;
+        const bool chk = k == 0 && A.validate;
         if (k > 0 && !wide_data && fin_data && !lam_on_bp)
             eval_pass<T, true, true, false>(A, gp, lam, false, false, rev, acc, smem, ring_bars, ring_parity, err);
         else if (k > 0 && !wide_data && fin_data)
@@ -878,7 +903,9 @@ __device__ __forceinline__ void general_solve(const GeneralArgs& A, const Grp& g
             eval_pass<T, true, false, false>(A, gp, lam, false, false, rev, acc, smem, ring_bars, ring_parity, err);
         else if (k > 0 && !wide_data)
             eval_pass<T, true, false, true>(A, gp, lam, false, false, rev, acc, smem, ring_bars, ring_parity, err);
-        else eval_pass<T, false>(A, gp, lam, false, k == 0 && A.validate, rev, acc, smem, ring_bars, ring_parity, err);
+        else if (!lam_on_bp)
+            eval_pass<T, false, false, false>(A, gp, lam, false, chk, rev, acc, smem, ring_bars, ring_parity, err);
+        else eval_pass<T, false, false, true>(A, gp, lam, false, chk, rev, acc, smem, ring_bars, ring_parity, err);
         acc.flush();
         passes++;
         if (__any_sync(0xffffffffu, acc.bad) && (threadIdx.x & 31) == 0) atomicOr(&gp.hdr->flags, kFlagBadInput);
@@ -994,7 +1021,6 @@ __device__ __forceinline__ void general_solve(const GeneralArgs& A, const Grp& g
             }
             next = m;
         }
-        lam_on_bp = need_bp != 0;
         if (upper - lower < A.eps34 * fmax(fabs(upper), fabs(lower))) {
             stop = CQK_STOP_BRACKET;
             k++;
@@ -1005,6 +1031,7 @@ __device__ __forceinline__ void general_solve(const GeneralArgs& A, const Grp& g
             k++;
             break;
         }
+        lam_on_bp = need_bp != 0;  // (describes lam from here on)
         lam = next;
         final_lam = lam;
     }
@@ -1013,11 +1040,20 @@ __device__ __forceinline__ void general_solve(const GeneralArgs& A, const Grp& g
     EvalAcc acc;
     acc.init();
     if (!bad_input && status != CQK_INFEASIBLE) {
-        if (!wide_data && fin_data)
-            eval_pass<T, true, true>(A, gp, final_lam, true, false, (k & 1) == 1, acc, smem, ring_bars, ring_parity, err);
+        // FP64 data keep the tie band in the final pass (it also keeps every stored x inside
+        // [l, u]: measured cheaper than clamping afterwards); FP32 data test ties only when x is
+        // formed at a breakpoint lambda and clamp the stored float x instead
+        const bool ties = sizeof(T) == 8 || (lam_on_bp && final_lam == lam);
+        const bool rev = (k & 1) == 1;
+        if (!wide_data && fin_data && !ties)
+            eval_pass<T, true, true, false>(A, gp, final_lam, true, false, rev, acc, smem, ring_bars, ring_parity, err);
+        else if (!wide_data && fin_data)
+            eval_pass<T, true, true, true>(A, gp, final_lam, true, false, rev, acc, smem, ring_bars, ring_parity, err);
+        else if (!wide_data && !ties)
+            eval_pass<T, true, false, false>(A, gp, final_lam, true, false, rev, acc, smem, ring_bars, ring_parity, err);
         else if (!wide_data)
-            eval_pass<T, true>(A, gp, final_lam, true, false, (k & 1) == 1, acc, smem, ring_bars, ring_parity, err);
-        else eval_pass<T, false>(A, gp, final_lam, true, false, (k & 1) == 1, acc, smem, ring_bars, ring_parity, err);
+            eval_pass<T, true, false, true>(A, gp, final_lam, true, false, rev, acc, smem, ring_bars, ring_parity, err);
+        else eval_pass<T, false>(A, gp, final_lam, true, false, rev, acc, smem, ring_bars, ring_parity, err);
         passes++;
     }
     acc.flush();
