@@ -149,31 +149,6 @@ __device__ __forceinline__ double f32_to_f64_bits(float f) {
 // df -> double with one FP64 add and no conversion instruction.
 __device__ __forceinline__ double df_to_f64_int(df a) { return f32_to_f64_bits(a.hi) + f32_to_f64_bits(a.lo); }
 
-// df -> double with no FP64 instruction: lo is added to hi's bit pattern as an integer
-// number of hi's ulps, rounded to the nearest ulp.  The integer sum is the FP64 sum only while
-// it stays in hi's binade: a normalised pair (|lo| at most half a float ulp of hi, i.e. 2^28
-// ulps of hi as a double) cannot carry into the binade above, but an lo of the opposite sign
-// borrows into the binade below when hi is an exact power of two, and there one ulp is half
-// as large.  That case, unnormalised pairs and non-finite or subnormal parts take one FP64 add.
-__device__ __forceinline__ double df_to_f64_bits(df a) {
-    if (a.lo == 0.0f) return f32_to_f64_bits(a.hi);
-    const unsigned hu = __float_as_uint(a.hi), lu = __float_as_uint(a.lo);
-    const int ehf = (int)((hu >> 23) & 0xFFu), el = (int)((lu >> 23) & 0xFFu);
-    if (ehf == 0 || ehf == 0xFF || el == 0xFF) return df_to_f64_int(a);
-    const unsigned long long hb = opaque_bits(f32_to_f64_bits(a.hi));
-    const int eh = ehf + 896;  // biased double exponent of hi
-    const unsigned long long ml = el ? (unsigned long long)((lu & 0x7FFFFFu) | 0x800000u) : (unsigned long long)(lu & 0x7FFFFFu);
-    const int sh = (el ? el : 1) - 150 - (eh - 1075);  // lo = ml * 2^sh ulps of h
-    if (sh > 4) return df_to_f64_int(a);  // |lo| above 2^28 ulps of hi: not normalised
-    const unsigned long long units =
-        sh >= 0 ? (ml << sh) : (sh > -40 ? ((ml + (1ull << (-sh - 1))) >> (-sh)) : 0ull);
-    const unsigned long long mag = hb & 0x7FFFFFFFFFFFFFFFull;
-    const bool same = (hu >> 31) == (lu >> 31);
-    if (units > (1ull << 28) || (!same && (mag & 0xFFFFFFFFFFFFFull) < units)) return df_to_f64_int(a);
-    const unsigned long long m = same ? mag + units : mag - units;
-    return __longlong_as_double((long long)((hb & 0x8000000000000000ull) | m));
-}
-
 // double -> df with FP64 arithmetic (per-call scalars only): the pair rounds x to ~48 bits.
 __device__ __forceinline__ df df_from_f64(double x) {
     float h = __double2float_rn(x);
