@@ -2,6 +2,7 @@
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--no-extras]
                     [--no-cpu-baseline] [--no-oracle-check]
+    python bench.py --case general|batched_simplex|batched_general [--n N] [--batch B]
 
 Workload (default): projection of y ~ N(0,1), n = 10^8, FP64, onto the unit simplex and onto
 the unit l1 ball, Condat start (Alg. 2 per chunk, then Alg. 4); one step = both projections
@@ -24,6 +25,11 @@ family at n = 1e8 in FP64 and FP32 storage), config0 (the latency-bound n = 10,0
 warm and cold), batched (the two ragged batches forward + adjoint: batched launch, CUDA
 graph, autotuned options, per-instance launches from Python and in one CUDA graph, roofline
 at the algorithmic bytes) and cpu_baseline (the oracle on all host cores and on one core).
+
+--case runs one side workload alone and prints its CUDA-event timings (a profiling aid: the
+commands of the ncu summaries): the general solve of the correlated family at --n in FP64 and
+FP32 storage (one warm-up and 7 timed solves each), or a ragged batch of --batch instances
+(the simplex recipe in FP32, the general recipe in FP64) forward + adjoint, twice.
 
 --impl reference times the FP64 CPU oracle -- Alg. 2 per thread chunk and Alg. 4 with
 OpenMP map-reduce passes, the paper's CPU Jacobi form -- on all host cores on the same
@@ -962,6 +968,65 @@ def run_reference(args, world, rank):
             "cpu_baseline": cb, "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_case(args):
+    """One side workload alone (see the module docstring), for profiling."""
+    import torch
+
+    from paper_2603_15910_b300 import api, workloads as W
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    out = {"case": args.case}
+
+    def timed(f, reps):
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            f()
+            b.record()
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+    if args.case == "general":
+        n = args.n
+        for dt, tag in ((torch.float64, "f64"), (torch.float32, "f32")):
+            p = W.correlated(n, seed=0, device=dev, dtype=dt)
+            x = torch.empty_like(p["a"])
+            ws = api.Workspace(n, 1, dt, dev)
+
+            def f():
+                api.solve(p["a"], p["b"], p["d"], p["l"], p["u"], p["r"], out=x, ws=ws, sync=False)
+            f()
+            ms = timed(f, 7)
+            inf = ws.read_info()
+            out[tag] = {"ms": ms, "passes": inf.passes, "iters": inf.iters, "status": int(inf.status)}
+            del p, x
+            torch.cuda.empty_cache()
+    else:
+        B = args.batch
+        if args.case == "batched_simplex":
+            d = W.batched_simplex(batch=B, lo=16, hi=1 << 20, seed=0, device=dev, dtype=torch.float32)
+            ws = api.Workspace(d["y"].numel(), B, torch.float32, dev)
+
+            def f():
+                x, _, m = api.project_simplex_batched(d["y"], d["offsets"], d["r"], want_mask=True, ws=ws,
+                                                      sync=False, use_tuning=False)
+                api.backward("simplex", d["g"], x, ws.info, offsets=d["offsets"], mask=m, ws=ws, use_tuning=False)
+        else:
+            d = W.batched_general(batch=B, lo=1000, hi=1000000, seed=0, device=dev)
+            ws = api.Workspace(d["a"].numel(), B, torch.float64, dev)
+            arr = [d[k] for k in "abdlu"]
+
+            def f():
+                x, _, m = api.solve_batched(*arr, d["offsets"], d["r"], want_mask=True, ws=ws, sync=False,
+                                            use_tuning=False)
+                api.backward("general", d["g"], x, ws.info, offsets=d["offsets"], mask=m, ws=ws, use_tuning=False,
+                             **dict(zip("abdlu", arr)))
+        out["ms_fwd_bwd"] = [timed(f, 1), timed(f, 1)]
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -972,7 +1037,12 @@ def main():
     ap.add_argument("--no-extras", dest="extras", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-oracle-check", dest="oracle_check", action="store_false")
+    ap.add_argument("--case", default=None, choices=["general", "batched_simplex", "batched_general"])
+    ap.add_argument("--batch", type=int, default=1024)
     args = ap.parse_args()
+    if args.case:
+        print(json.dumps(run_case(args)), flush=True)
+        return
     if args.warmup < 3:
         args.warmup = 3
     world, rank, local = dist_env()

@@ -792,7 +792,7 @@ __device__ __forceinline__ void lambda0_warm_pass(const GeneralArgs& A, const Gr
 #define CQK_BARRIER_OR_LEAVE()                                                  \
     do {                                                                        \
         if (!group_barrier(gp, bar_target, A.limit_ns, A.fault_inject == 1)) {     \
-            if (threadIdx.x == 0) A.info->status = CQK_TIMEOUT;                 \
+            if (threadIdx.x == 0) info->status = CQK_TIMEOUT;                   \
             return;                                                             \
         }                                                                       \
         bar_target += (unsigned)G;                                              \
@@ -801,15 +801,16 @@ __device__ __forceinline__ void lambda0_warm_pass(const GeneralArgs& A, const Gr
 // ---- one solve (or one phi evaluation) by one group of blocks ------------------------------
 // smem / ring_bars: the block's bulk-copy stages and their mbarriers (initialised by the
 // caller when A.staged); ring_parity: their phase bits, carried across calls.
+// r and info are the instance's (a batch passes its kernel argument A unchanged, so that A is
+// read from the parameter space instead of a per-instance copy in local memory).
 template <typename T>
-__device__ __forceinline__ void general_solve(const GeneralArgs& A, const Grp& gp, T* smem, uint64_t* ring_bars,
-                                              unsigned& ring_parity) {
+__device__ __forceinline__ void general_solve(const GeneralArgs& A, const Grp& gp, const double r, cqk_info* info,
+                                              T* smem, uint64_t* ring_bars, unsigned& ring_parity) {
     __shared__ double sh[kPartialQ][NWARP];
     __shared__ double bc[kPartialQ];
     const int G = gp.g;
     unsigned bar_target = (unsigned)G + (A.fault_inject == 1 ? 1u : 0u);
     int* err = &gp.hdr->error;
-    const double r = A.r;
     int passes = 0, par = 0;
 
     if (A.phi_only) {  // cqk_phi: one evaluation at A.lambda0 (and x when requested)
@@ -1073,7 +1074,7 @@ __device__ __forceinline__ void general_solve(const GeneralArgs& A, const Grp& g
         inf.stop = stop;
         inf.nchunks = 0;
         inf.tile = 0;
-        *A.info = inf;
+        *info = inf;
     }
 }
 
@@ -1096,7 +1097,7 @@ __global__ void __launch_bounds__(NT, kMinBlocksPerSM) general_kernel(const __gr
     gp.sp = Span{0, A.n};
     gp.hdr = A.hdr;
     gp.part = A.part;
-    general_solve<T>(A, gp, reinterpret_cast<T*>(dyn_smem), ring_bars, ring_parity);
+    general_solve<T>(A, gp, A.r, A.info, reinterpret_cast<T*>(dyn_smem), ring_bars, ring_parity);
 }
 
 #endif  // CQK_BATCH_ONLY
@@ -1128,19 +1129,18 @@ __global__ void __launch_bounds__(NT, kMinBlocksPerSM) general_batched_kernel(co
         const Slot sl = next_slot(P.R, P.B);
         if (sl.inst < 0) break;
         const Grp gp = slot_group(P.R, P.offsets, sl);
-        GeneralArgs A = P.base;
-        A.r = P.r[sl.inst];
-        A.info = P.info + sl.inst;
+        const double r = P.r[sl.inst];
+        cqk_info* info = P.info + sl.inst;
         const int64_t len = gp.sp.hi - gp.sp.lo;
-        if (len <= 0 || A.r != A.r) {
+        if (len <= 0 || r != r) {
             // no variable: feasible iff r == 0 (as for a single solve with n = 0)
             if (sl.member == 0 && threadIdx.x == 0) {
-                if (len < 0 || A.r != A.r) write_plain_info(A.info, CQK_BAD_ARG, CQK_STOP_NONE, A.r);
-                else write_plain_info(A.info, A.r == 0.0 ? CQK_OK : CQK_INFEASIBLE, CQK_STOP_NONE, A.r);
+                if (len < 0 || r != r) write_plain_info(info, CQK_BAD_ARG, CQK_STOP_NONE, r);
+                else write_plain_info(info, r == 0.0 ? CQK_OK : CQK_INFEASIBLE, CQK_STOP_NONE, r);
             }
             continue;
         }
-        general_solve<T>(A, gp, reinterpret_cast<T*>(dyn_smem), ring_bars, ring_parity);
+        general_solve<T>(P.base, gp, r, info, reinterpret_cast<T*>(dyn_smem), ring_bars, ring_parity);
     }
 }
 
