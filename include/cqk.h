@@ -120,8 +120,7 @@ typedef struct cqk_options {
                             /* deals its tiles to scan_warps chunks (1, 2 or 4; other positive   */
                             /* values round down to one of these), scanned by as                */
                             /* many warps side by side (the partition then has nchunks =         */
-                            /* blocks * scan_warps, a looser union start); 0 (default): 4 for a  */
-                            /* one-block instance of 4 to 15 tiles of 16 KB, else 1             */
+                            /* blocks * scan_warps, a looser union start); 0 (default): 1        */
     int32_t block_threads;  /* batched calls: threads per block of the persistent kernel.  0       */
                             /* (default) = 256; 128 or 512 for cqk_solve_batched (general) and   */
                             /* the batched adjoints; the batched projections and every single-   */

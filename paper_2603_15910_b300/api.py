@@ -211,7 +211,7 @@ def make_options(init=None, max_iter=100, lambda0=0.0, validate=True, final_step
     return o
 
 
-_TUNABLE = ("group_elems", "warp_elems", "condat_chunk", "block_threads", "unroll", "max_blocks")
+_TUNABLE = ("group_elems", "warp_elems", "condat_chunk", "scan_warps", "block_threads", "unroll", "max_blocks")
 
 
 def _with_tuning(kind, dtype, offsets, kw, use_tuning):

@@ -1527,17 +1527,14 @@ __device__ __forceinline__ void simplex_solve(const SimplexArgs& A, const Grp& g
         // a partition into many small chunks multiplies, and larger chunks give a better
         // lambda_0), at most one per block
         const int nchunk = (int)min((int64_t)G, max((int64_t)1, (n + A.condat_chunk - 1) / A.condat_chunk));
-        // chunks per block: the scan of a chunk is one warp's dependency chain, so a block that
-        // alone holds a short instance splits it over four scan warps.  Each doubling of the
-        // chunks loosens the union's lambda_0 by about one Newton step (measured on ragged FP32
-        // batches: 3.4 -> 4.5 -> 5.3 steps), which only instances of 4 to 15 tiles recover
-        // (0.37 -> 0.32 ms on 531 instances of 16K-64K elements; 1.8 -> 2.9 ms on 553 of
-        // 256K-1M)
+        // chunks per block (option scan_warps, default 1): the scan of a chunk is one warp's
+        // dependency chain, and a block that alone holds a short instance may split it over
+        // several scan warps, but each doubling of the chunks loosens the union's lambda_0 by
+        // about one Newton step (ragged FP32 batches: 3.4 -> 4.5 -> 5.3 steps); on the 4096-
+        // instance batch one scan warp per block is the fastest (2.30 ms; 2.35 ms with four for
+        // one-block instances of 4 to 15 tiles, 2.56 / 2.80 ms with two / four everywhere)
         int nscan = 1;
-        if (condat && aligned) {
-            const int64_t tiles = (n + condat_tile<T>() - 1) / condat_tile<T>();
-            nscan = A.scan_warps > 0 ? A.scan_warps : (G == 1 && tiles >= 4 && tiles < 16 ? 4 : 1);
-        }
+        if (condat && aligned) nscan = A.scan_warps > 0 ? A.scan_warps : 1;
         if (condat) {
             double Sw = 0.0;
             long long nJw = 0;

@@ -8,6 +8,7 @@ work split and the kernel build change):
   warp_elems     instances shorter than this are solved by one warp each (projections; the
                  split between segment-per-warp and segment-per-block)
   condat_chunk   minimum elements per chunk of the parallel Alg. 2 start (projections)
+  scan_warps     chunks (scan warps) per block of the Alg. 2 start (projections)
   block_threads  threads per block of the persistent kernel: 128, 256 or 512 (general batches
                  and the adjoints; the projection forward runs 256)
   unroll         elements per thread: 0 = the full per-lane unroll of the streaming loops, 1 =
@@ -56,13 +57,13 @@ def _grid(**axes):
 
 
 SIMPLEX_CANDIDATES = _grid(group_elems=(1 << 16, 1 << 18, 1 << 20, (1 << 31) - 1), condat_chunk=(512, 1 << 14),
-                           warp_elems=(4096, 16384, 1 << 17), build=BUILDS_PROJECTION_FORWARD)
+                           warp_elems=(4096, 16384, 1 << 17), scan_warps=(1, 4), build=BUILDS_PROJECTION_FORWARD)
 GENERAL_CANDIDATES = _grid(group_elems=(1 << 14, 1 << 15, 1 << 16, 1 << 17, 1 << 18), build=BUILDS_ALL)
 SIMPLEX_BWD_CANDIDATES = _grid(group_elems=(1 << 16, 1 << 18, 1 << 20), warp_elems=(4096, 16384, 1 << 17),
                                build=BUILDS_ALL)
 GENERAL_BWD_CANDIDATES = _grid(group_elems=(1 << 13, 1 << 14, 1 << 15, 1 << 16, 1 << 17), build=BUILDS_ALL)
 
-TUNABLE_KEYS = ("group_elems", "warp_elems", "condat_chunk", "block_threads", "unroll", "max_blocks")
+TUNABLE_KEYS = ("group_elems", "warp_elems", "condat_chunk", "scan_warps", "block_threads", "unroll", "max_blocks")
 
 
 def signature(kind: str, dtype, offsets) -> tuple:
