@@ -40,7 +40,11 @@ def _u(g, n, lo, hi, device):
 
 
 def _bdot(b, v):
-    return float(torch.dot(b.double(), v.double()).item())
+    # in pieces of 2^30 (the library dot product takes at most 2^31 - 1 elements); one piece,
+    # the same value as a single dot, for every smaller array
+    step = 1 << 30
+    return float(sum(torch.dot(b[i:i + step].double(), v[i:i + step].double()).item()
+                     for i in range(0, max(b.numel(), 1), step)))
 
 
 def uncorrelated_box(n, seed=0, device="cpu", dtype=torch.float64):
