@@ -229,6 +229,30 @@ __device__ __forceinline__ void block_sum(double (&v)[NQ], double (*sh)[NWARP]) 
     __syncthreads();
 }
 
+// Sum NQ doubles over the block (fixed order); result valid in thread 0.  Every thread stores
+// its values in scr (NQ x NT doubles of shared memory); warp 0 alone adds them, lane l the
+// threads l, l + 32, ... in turn, then one butterfly.  The FP64 pipe, the scarce unit of this
+// GPU, sees NWARP + 5 adds per value in one warp instead of a 5-level butterfly in every warp
+// (at n = 1e4, ~4.5 -> ~1.5 us per Newton pass of the general solve).
+template <int NQ>
+__device__ __forceinline__ void block_sum_smem(double (&v)[NQ], double* scr) {
+#pragma unroll
+    for (int q = 0; q < NQ; q++) scr[q * NT + threadIdx.x] = v[q];
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double t[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; q++) {
+            t[q] = scr[q * NT + threadIdx.x];
+#pragma unroll
+            for (int k = 1; k < NWARP; k++) t[q] += scr[q * NT + k * 32 + threadIdx.x];
+        }
+#pragma unroll
+        for (int q = 0; q < NQ; q++) v[q] = warp_sum(t[q]);
+    }
+    __syncthreads();
+}
+
 // Totals of the group's g partials of pass parity `par` (sums, and a max for q == qmax), in
 // a fixed order; valid in every lane of warp 0, computed by warp 0 alone (the other threads
 // return at once): lane l takes blocks l, l + 32, ... in turn, then a butterfly.  Every block

@@ -94,11 +94,13 @@ struct EvalAcc {
         nfree = 0;
         bad = wide = luinf = false;
     }
-    // all levels into FP64 (end of a pass)
+    // all levels into FP64 (end of a pass).  The float parts are widened on the integer pipe
+    // and added in FP64: float -> double conversion instructions run on the FP64 pipe, which
+    // every warp of the SM shares at the end of a pass.
     __device__ void flush() {
-        phi64 += df_to_f64(mphi) + lazy_value(phi);
-        absbx64 += df_to_f64(mabsbx) + lazy_value(absbx) + (double)absf;
-        sfree64 += df_to_f64(msfree) + lazy_value(sfree);
+        phi64 += df_to_f64_int(df_add(mphi, two_sum(phi.hi, phi.lo)));
+        absbx64 += df_to_f64_int(df_add(mabsbx, two_sum(absbx.hi, __fadd_rn(absbx.lo, absf))));
+        sfree64 += df_to_f64_int(df_add(msfree, two_sum(sfree.hi, sfree.lo)));
         phi = absbx = sfree = LazyDf{0.0f, 0.0f};
         mphi = mabsbx = msfree = df{0.0f, 0.0f};
         absf = 0.0f;
@@ -807,6 +809,7 @@ template <typename T>
 __device__ __forceinline__ void general_solve(const GeneralArgs& A, const Grp& gp, const double r, cqk_info* info,
                                               T* smem, uint64_t* ring_bars, unsigned& ring_parity) {
     __shared__ double sh[kPartialQ][NWARP];
+    __shared__ double bscr[5 * NT];  // per-thread sums of a pass (block_sum_smem)
     __shared__ double bc[kPartialQ];
     const int G = gp.g;
     unsigned bar_target = (unsigned)G + (A.fault_inject == 1 ? 1u : 0u);
@@ -820,8 +823,8 @@ __device__ __forceinline__ void general_solve(const GeneralArgs& A, const Grp& g
         acc.flush();
         double pv[3] = {acc.phi64, acc.sfree64, acc.absbx64};
         double pt[2] = {acc.satl, acc.satu};
-        block_sum<3>(pv, sh);
-        block_sum<2>(pt, sh);
+        block_sum_smem<3>(pv, bscr);
+        block_sum_smem<2>(pt, bscr);
         if (threadIdx.x == 0) {
             const double w5[5] = {pv[0], pv[1], pv[2], pt[0], pt[1]};
             write_partials<5>(gp.part, gp.member, G, 0, w5);
@@ -851,7 +854,7 @@ __device__ __forceinline__ void general_solve(const GeneralArgs& A, const Grp& g
         double s, q;
         lambda0_pass<T>(A, gp, s, q, smem, ring_bars, ring_parity, err);
         double pv[2] = {s, q};
-        block_sum<2>(pv, sh);
+        block_sum_smem<2>(pv, bscr);
         write_partials<2>(gp.part, gp.member, G, par, pv);
         CQK_BARRIER_OR_LEAVE();
         double red[2];
@@ -862,7 +865,7 @@ __device__ __forceinline__ void general_solve(const GeneralArgs& A, const Grp& g
     } else if (A.init == CQK_INIT_WARM) {
         double w[5];
         lambda0_warm_pass<T>(A, gp, w);
-        block_sum<5>(w, sh);
+        block_sum_smem<5>(w, bscr);
         write_partials<5>(gp.part, gp.member, G, par, w);
         CQK_BARRIER_OR_LEAVE();
         double red[5];
@@ -873,7 +876,10 @@ __device__ __forceinline__ void general_solve(const GeneralArgs& A, const Grp& g
         passes++;
     }
 
-    // ---- Alg. 1
+    // ---- Alg. 1.  Thread 0 keeps the bracket and runs the update (FP64 divisions: the FP64 pipe
+    // is the scarce unit, so one thread does it instead of every thread of every block); its
+    // decisions reach the block through shared memory.  Every block's thread 0 computes the same
+    // bits from the same totals.
     double lam = lam0, lower = -INFINITY, upper = INFINITY, phi_lower = NAN, phi_upper = NAN, slope = 0.0;
     double final_lam = lam;
     int status = CQK_OK, stop = CQK_STOP_NONE, k = 0;
@@ -883,6 +889,8 @@ __device__ __forceinline__ void general_solve(const GeneralArgs& A, const Grp& g
     // lambda may sit exactly on a breakpoint (it came from a breakpoint step, or is the caller's
     // start): only then is the tie band tested
     bool lam_on_bp = A.init == CQK_INIT_GIVEN;
+    __shared__ double s_val[2];  // the next (or the final) lambda; the breakpoint search origin
+    __shared__ int s_ctl[2];     // 1 = stop; breakpoint search direction (0: none)
     for (k = 0;; k++) {
         if (k >= A.max_iter) {
             status = CQK_MAXITER;
@@ -913,7 +921,7 @@ __device__ __forceinline__ void general_solve(const GeneralArgs& A, const Grp& g
         if (k == 0 && __any_sync(0xffffffffu, acc.wide) && (threadIdx.x & 31) == 0) atomicOr(&gp.hdr->flags, kFlagWide);
         if (k == 0 && __any_sync(0xffffffffu, acc.luinf) && (threadIdx.x & 31) == 0) atomicOr(&gp.hdr->flags, kFlagLuInf);
         double pv[5] = {acc.phi64, acc.sfree64, acc.satl, acc.satu, acc.absbx64};
-        block_sum<5>(pv, sh);
+        block_sum_smem<5>(pv, bscr);
         write_partials<5>(gp.part, gp.member, G, par, pv);
         CQK_BARRIER_OR_LEAVE();
         double red[5];
@@ -929,76 +937,93 @@ __device__ __forceinline__ void general_solve(const GeneralArgs& A, const Grp& g
             k++;
             break;
         }
-        const double phi = red[0], dplus = red[1] + red[2], dminus = red[1] + red[3], absbx = red[4];
-        const double g = phi - r;
-        final_lam = lam;
-        if (g == 0.0) {
-            stop = CQK_STOP_EXACT;
-            k++;
-            break;
-        }
-        if (fabs(g) < A.eps34_stop1 * (absbx + fabs(r))) {
-            stop = CQK_STOP_RESIDUAL;
-            if (A.final_step) {
-                double s = g < 0 ? (dplus > 0 ? -g / dplus : 0.0) : (dminus > 0 ? -g / dminus : 0.0);
-                const double t = lam + s;
-                if (g < 0 && !(t < upper)) s = 0.0;
-                if (g > 0 && !(t > lower)) s = 0.0;
-                final_lam = lam + s;
-            }
-            k++;
-            break;
-        }
-        double next = lam;
-        int need_bp = 0;
-        bool done = false;
-        if (g < 0) {
-            lower = lam;
-            phi_lower = phi;
-            if (dplus > 0) {
-                slope = dplus;
-                const double step = -g / dplus;
-                const double t = lam + step;
-                if (fabs(step) < A.eps34) {
-                    stop = CQK_STOP_STEP;
-                    if (A.final_step && t < upper) final_lam = t;
-                    done = true;
-                } else if (t < upper) {
-                    next = t;
+        if (threadIdx.x == 0) {
+            const double phi = red[0], dplus = red[1] + red[2], dminus = red[1] + red[3], absbx = red[4];
+            const double g = phi - r;
+            double next = lam, fin = lam, from = 0.0;
+            int done = 0, need_bp = 0;
+            if (g == 0.0) {
+                stop = CQK_STOP_EXACT;
+                done = 1;
+            } else if (fabs(g) < A.eps34_stop1 * (absbx + fabs(r))) {
+                stop = CQK_STOP_RESIDUAL;
+                if (A.final_step) {
+                    double st = g < 0 ? (dplus > 0 ? -g / dplus : 0.0) : (dminus > 0 ? -g / dminus : 0.0);
+                    const double t = lam + st;
+                    if (g < 0 && !(t < upper)) st = 0.0;
+                    if (g > 0 && !(t > lower)) st = 0.0;
+                    fin = lam + st;
+                }
+                done = 1;
+            } else if (g < 0) {
+                lower = lam;
+                phi_lower = phi;
+                if (dplus > 0) {
+                    slope = dplus;
+                    const double step = -g / dplus;
+                    const double t = lam + step;
+                    if (fabs(step) < A.eps34) {
+                        stop = CQK_STOP_STEP;
+                        if (A.final_step && t < upper) fin = t;
+                        done = 1;
+                    } else if (t < upper) {
+                        next = t;
+                    } else {
+                        next = lower - (phi_lower - r) * (upper - lower) / (phi_upper - phi_lower);
+                    }
                 } else {
-                    next = lower - (phi_lower - r) * (upper - lower) / (phi_upper - phi_lower);
+                    need_bp = +1;  // closest breakpoint right of the lower end (Alg. 1)
+                    from = lower;
                 }
             } else {
-                need_bp = +1;
-            }
-        } else {
-            upper = lam;
-            phi_upper = phi;
-            if (dminus > 0) {
-                slope = dminus;
-                const double step = -g / dminus;
-                const double t = lam + step;
-                if (fabs(step) < A.eps34) {
-                    stop = CQK_STOP_STEP;
-                    if (A.final_step && t > lower) final_lam = t;
-                    done = true;
-                } else if (t > lower) {
-                    next = t;
+                upper = lam;
+                phi_upper = phi;
+                if (dminus > 0) {
+                    slope = dminus;
+                    const double step = -g / dminus;
+                    const double t = lam + step;
+                    if (fabs(step) < A.eps34) {
+                        stop = CQK_STOP_STEP;
+                        if (A.final_step && t > lower) fin = t;
+                        done = 1;
+                    } else if (t > lower) {
+                        next = t;
+                    } else {
+                        next = lower - (phi_lower - r) * (upper - lower) / (phi_upper - phi_lower);
+                    }
                 } else {
-                    next = lower - (phi_lower - r) * (upper - lower) / (phi_upper - phi_lower);
+                    need_bp = -1;  // closest breakpoint left of the upper end
+                    from = upper;
                 }
-            } else {
-                need_bp = -1;
             }
+            if (!done && !need_bp) {
+                if (upper - lower < A.eps34 * fmax(fabs(upper), fabs(lower))) {
+                    stop = CQK_STOP_BRACKET;
+                    done = 1;
+                } else if (next == lam) {
+                    stop = CQK_STOP_SAME;
+                    done = 1;
+                }
+            }
+            s_ctl[0] = done;
+            s_ctl[1] = need_bp;
+            s_val[0] = done ? fin : next;
+            s_val[1] = from;
         }
+        __syncthreads();
+        const int done = s_ctl[0], need_bp = s_ctl[1];
+        double next = s_val[0];
+        const double from = s_val[1];
+        __syncthreads();  // s_val / s_ctl are rewritten only after every thread has read them
         if (done) {
+            final_lam = next;
             k++;
             break;
         }
         if (need_bp) {
             // closest breakpoint right of the lower end / left of the upper end (Alg. 1); the
             // block maximum of (-bp) or (bp) keeps one reduction code path
-            double bp = breakpoint_pass<T>(A, gp, need_bp > 0 ? lower : upper, need_bp);
+            double bp = breakpoint_pass<T>(A, gp, from, need_bp);
             bp = need_bp > 0 ? -bp : bp;
             bp = warp_max(bp);
             if ((threadIdx.x & 31) == 0) sh[0][threadIdx.x >> 5] = bp;
@@ -1015,22 +1040,32 @@ __device__ __forceinline__ void general_solve(const GeneralArgs& A, const Grp& g
             grid_reduce<1>(gp.part, G, par, 0, redb, sh, bc);
             par ^= 1;
             const double m = need_bp > 0 ? -redb[0] : redb[0];
-            if (!isfinite(m)) {
+            if (!isfinite(m)) {  // no breakpoint in the needed direction: r is out of reach
                 status = CQK_INFEASIBLE;
+                final_lam = lam;
                 k++;
                 break;
             }
             next = m;
-        }
-        if (upper - lower < A.eps34 * fmax(fabs(upper), fabs(lower))) {
-            stop = CQK_STOP_BRACKET;
-            k++;
-            break;
-        }
-        if (next == lam) {
-            stop = CQK_STOP_SAME;
-            k++;
-            break;
+            if (threadIdx.x == 0) {
+                int stop_now = 0;
+                if (upper - lower < A.eps34 * fmax(fabs(upper), fabs(lower))) {
+                    stop = CQK_STOP_BRACKET;
+                    stop_now = 1;
+                } else if (next == lam) {
+                    stop = CQK_STOP_SAME;
+                    stop_now = 1;
+                }
+                s_ctl[0] = stop_now;
+            }
+            __syncthreads();
+            const int stop_now = s_ctl[0];
+            __syncthreads();
+            if (stop_now) {
+                final_lam = lam;
+                k++;
+                break;
+            }
         }
         lam_on_bp = need_bp != 0;  // (describes lam from here on)
         lam = next;
