@@ -294,13 +294,14 @@ __device__ __forceinline__ T clamp_exact(T l, T x, T u) {
 // the first pass), so the per-element checks are skipped.
 // TIES: the tie band of the file header is tested (passes whose lambda may sit on a breakpoint:
 // the first, the final pass and those after a breakpoint step); otherwise the plain sign test.
-template <typename T, bool FAST, bool FIN, bool TIES = true>
+template <typename T, bool FAST, bool FIN, bool TIES, bool WX>
 __device__ __forceinline__ void eval_vec(const GeneralArgs& A, const T (&va)[VecOf<T>::V], const T (&vb)[VecOf<T>::V],
                                          const T (&vd)[VecOf<T>::V], const T (&vl)[VecOf<T>::V],
                                          const T (&vu)[VecOf<T>::V], const bool (&ok)[VecOf<T>::V], int64_t q,
-                                         int64_t qw, double lam, df Lm, bool lam_ok, bool write_x, bool check,
-                                         EvalAcc& acc, const Span& sp) {
+                                         int64_t qw, double lam, df Lm, bool lam_ok, bool check, EvalAcc& acc,
+                                         const Span& sp) {
     constexpr int V = VecOf<T>::V;
+    constexpr bool write_x = WX;
     const bool aligned = A.aligned != 0;
     T* __restrict__ px = static_cast<T*>(A.x);
         T xo[V];
@@ -451,9 +452,9 @@ __device__ __forceinline__ void eval_vec(const GeneralArgs& A, const T (&va)[Vec
 }
 
 // ---- one pass over all elements with plain loads (arrays not 16-byte aligned)
-template <typename T, bool FAST, bool FIN, bool TIES>
-__device__ __forceinline__ void eval_pass_plain(const GeneralArgs& A, const Grp& gp, double lam, bool write_x,
-                                                bool check, bool rev, EvalAcc& acc) {
+template <typename T, bool FAST, bool FIN, bool TIES, bool WX>
+__device__ __forceinline__ void eval_pass_plain(const GeneralArgs& A, const Grp& gp, double lam, bool check, bool rev,
+                                                EvalAcc& acc) {
     constexpr int V = VecOf<T>::V;
     constexpr int U = kGenU;
     const T* __restrict__ pa = static_cast<const T*>(A.a);
@@ -487,8 +488,8 @@ __device__ __forceinline__ void eval_pass_plain(const GeneralArgs& A, const Grp&
         }
 #pragma unroll
         for (int w = 0; w < U; w++)
-            eval_vec<T, FAST, FIN, TIES>(A, va[w], vb[w], vd[w], vl[w], vu[w], ok[w], base + w * 32 + lane, base + w * 32,
-                                         lam, Lm, lam_ok, write_x, check, acc, sp);
+            eval_vec<T, FAST, FIN, TIES, WX>(A, va[w], vb[w], vd[w], vl[w], vu[w], ok[w], base + w * 32 + lane,
+                                             base + w * 32, lam, Lm, lam_ok, check, acc, sp);
     }
 }
 
@@ -496,10 +497,10 @@ __device__ __forceinline__ void eval_pass_plain(const GeneralArgs& A, const Grp&
 template <typename T>
 __host__ __device__ constexpr int stage_tile() { return kGenTileBytes / (int)sizeof(T); }  // elements per array per stage
 
-template <typename T, bool FAST, bool FIN, bool TIES>
-__device__ __forceinline__ bool eval_pass_staged(const GeneralArgs& A, const Grp& gp, double lam, bool write_x,
-                                                 bool check, bool rev, EvalAcc& acc, T* smem, uint64_t* bars,
-                                                 unsigned& parity, int* err) {
+template <typename T, bool FAST, bool FIN, bool TIES, bool WX>
+__device__ __forceinline__ bool eval_pass_staged(const GeneralArgs& A, const Grp& gp, double lam, bool check,
+                                                 bool rev, EvalAcc& acc, T* smem, uint64_t* bars, unsigned& parity,
+                                                 int* err) {
     constexpr int V = VecOf<T>::V;
     constexpr int TT = stage_tile<T>();
     constexpr int VPT = TT / V / NT;  // vectors per thread per tile
@@ -554,7 +555,7 @@ __device__ __forceinline__ bool eval_pass_staged(const GeneralArgs& A, const Grp
                 load_vec<T>(src[3], sp, q, false, vl, ok);
                 load_vec<T>(src[4], sp, q, false, vu, ok);
             }
-            eval_vec<T, FAST, FIN, TIES>(A, va, vb, vd, vl, vu, ok, q, qw, lam, Lm, lam_ok, write_x, check, acc, sp);
+            eval_vec<T, FAST, FIN, TIES, WX>(A, va, vb, vd, vl, vu, ok, q, qw, lam, Lm, lam_ok, check, acc, sp);
         }
         __syncthreads();  // the stage is refilled only after every thread has read it
     }
@@ -562,14 +563,13 @@ __device__ __forceinline__ bool eval_pass_staged(const GeneralArgs& A, const Grp
     return okw;
 }
 
-// one pass over all elements, staged or plain
-template <typename T, bool FAST, bool FIN = false, bool TIES = true>
-__device__ __forceinline__ bool eval_pass(const GeneralArgs& A, const Grp& gp, double lam, bool write_x, bool check,
-                                          bool rev, EvalAcc& acc, T* smem, uint64_t* bars, unsigned& parity,
-                                          int* err) {
-    if (A.staged)
-        return eval_pass_staged<T, FAST, FIN, TIES>(A, gp, lam, write_x, check, rev, acc, smem, bars, parity, err);
-    eval_pass_plain<T, FAST, FIN, TIES>(A, gp, lam, write_x, check, rev, acc);
+// one pass over all elements, staged or plain; WX: the final pass (write x, the mask and the
+// sums of the stored x) instead of the accumulation of phi and its slopes
+template <typename T, bool WX, bool FAST, bool FIN = false, bool TIES = true>
+__device__ __forceinline__ bool eval_pass(const GeneralArgs& A, const Grp& gp, double lam, bool check, bool rev,
+                                          EvalAcc& acc, T* smem, uint64_t* bars, unsigned& parity, int* err) {
+    if (A.staged) return eval_pass_staged<T, FAST, FIN, TIES, WX>(A, gp, lam, check, rev, acc, smem, bars, parity, err);
+    eval_pass_plain<T, FAST, FIN, TIES, WX>(A, gp, lam, check, rev, acc);
     return true;
 }
 
@@ -819,7 +819,7 @@ __device__ __forceinline__ void general_solve(const GeneralArgs& A, const Grp& g
     if (A.phi_only) {  // cqk_phi: one evaluation at A.lambda0 (and x when requested)
         EvalAcc acc;
         acc.init();
-        eval_pass<T, false>(A, gp, A.lambda0, false, false, false, acc, smem, ring_bars, ring_parity, err);
+        eval_pass<T, false, false>(A, gp, A.lambda0, false, false, acc, smem, ring_bars, ring_parity, err);
         acc.flush();
         double pv[3] = {acc.phi64, acc.sfree64, acc.absbx64};
         double pt[2] = {acc.satl, acc.satu};
@@ -832,7 +832,7 @@ __device__ __forceinline__ void general_solve(const GeneralArgs& A, const Grp& g
         if (A.x) {
             EvalAcc acc2;
             acc2.init();
-            eval_pass<T, false>(A, gp, A.lambda0, true, false, true, acc2, smem, ring_bars, ring_parity, err);
+            eval_pass<T, true, false>(A, gp, A.lambda0, false, true, acc2, smem, ring_bars, ring_parity, err);
         }
         double dummy[1] = {0.0}, tot[1];
         if (last_block_sums<1>(gp.part, gp.member, G, &gp.hdr->ticket, dummy, tot, sh)) {
@@ -905,16 +905,16 @@ __device__ __forceinline__ void general_solve(const GeneralArgs& A, const Grp& g
         const bool rev = (k & 1) == 1;
         const bool chk = k == 0 && A.validate;
         if (k > 0 && !wide_data && fin_data && !lam_on_bp)
-            eval_pass<T, true, true, false>(A, gp, lam, false, false, rev, acc, smem, ring_bars, ring_parity, err);
+            eval_pass<T, false, true, true, false>(A, gp, lam, false, rev, acc, smem, ring_bars, ring_parity, err);
         else if (k > 0 && !wide_data && fin_data)
-            eval_pass<T, true, true, true>(A, gp, lam, false, false, rev, acc, smem, ring_bars, ring_parity, err);
+            eval_pass<T, false, true, true, true>(A, gp, lam, false, rev, acc, smem, ring_bars, ring_parity, err);
         else if (k > 0 && !wide_data && !lam_on_bp)
-            eval_pass<T, true, false, false>(A, gp, lam, false, false, rev, acc, smem, ring_bars, ring_parity, err);
+            eval_pass<T, false, true, false, false>(A, gp, lam, false, rev, acc, smem, ring_bars, ring_parity, err);
         else if (k > 0 && !wide_data)
-            eval_pass<T, true, false, true>(A, gp, lam, false, false, rev, acc, smem, ring_bars, ring_parity, err);
+            eval_pass<T, false, true, false, true>(A, gp, lam, false, rev, acc, smem, ring_bars, ring_parity, err);
         else if (!lam_on_bp)
-            eval_pass<T, false, false, false>(A, gp, lam, false, chk, rev, acc, smem, ring_bars, ring_parity, err);
-        else eval_pass<T, false, false, true>(A, gp, lam, false, chk, rev, acc, smem, ring_bars, ring_parity, err);
+            eval_pass<T, false, false, false, false>(A, gp, lam, chk, rev, acc, smem, ring_bars, ring_parity, err);
+        else eval_pass<T, false, false, false, true>(A, gp, lam, chk, rev, acc, smem, ring_bars, ring_parity, err);
         acc.flush();
         passes++;
         if (__any_sync(0xffffffffu, acc.bad) && (threadIdx.x & 31) == 0) atomicOr(&gp.hdr->flags, kFlagBadInput);
@@ -1079,17 +1079,17 @@ __device__ __forceinline__ void general_solve(const GeneralArgs& A, const Grp& g
         // FP64 data keep the tie band in the final pass (it also keeps every stored x inside
         // [l, u]: measured cheaper than clamping afterwards); FP32 data test ties only when x is
         // formed at a breakpoint lambda and clamp the stored float x instead
-        const bool ties = sizeof(T) == 8 || (lam_on_bp && final_lam == lam);
+        const bool ties = lam_on_bp && final_lam == lam;
         const bool rev = (k & 1) == 1;
         if (!wide_data && fin_data && !ties)
-            eval_pass<T, true, true, false>(A, gp, final_lam, true, false, rev, acc, smem, ring_bars, ring_parity, err);
+            eval_pass<T, true, true, true, false>(A, gp, final_lam, false, rev, acc, smem, ring_bars, ring_parity, err);
         else if (!wide_data && fin_data)
-            eval_pass<T, true, true, true>(A, gp, final_lam, true, false, rev, acc, smem, ring_bars, ring_parity, err);
+            eval_pass<T, true, true, true, true>(A, gp, final_lam, false, rev, acc, smem, ring_bars, ring_parity, err);
         else if (!wide_data && !ties)
-            eval_pass<T, true, false, false>(A, gp, final_lam, true, false, rev, acc, smem, ring_bars, ring_parity, err);
+            eval_pass<T, true, true, false, false>(A, gp, final_lam, false, rev, acc, smem, ring_bars, ring_parity, err);
         else if (!wide_data)
-            eval_pass<T, true, false, true>(A, gp, final_lam, true, false, rev, acc, smem, ring_bars, ring_parity, err);
-        else eval_pass<T, false>(A, gp, final_lam, true, false, rev, acc, smem, ring_bars, ring_parity, err);
+            eval_pass<T, true, true, false, true>(A, gp, final_lam, false, rev, acc, smem, ring_bars, ring_parity, err);
+        else eval_pass<T, true, false>(A, gp, final_lam, false, rev, acc, smem, ring_bars, ring_parity, err);
         passes++;
     }
     acc.flush();
