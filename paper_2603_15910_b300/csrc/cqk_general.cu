@@ -1079,7 +1079,7 @@ __device__ __forceinline__ void general_solve(const GeneralArgs& A, const Grp& g
         // FP64 data keep the tie band in the final pass (it also keeps every stored x inside
         // [l, u]: measured cheaper than clamping afterwards); FP32 data test ties only when x is
         // formed at a breakpoint lambda and clamp the stored float x instead
-        const bool ties = lam_on_bp && final_lam == lam;
+        const bool ties = sizeof(T) == 8 || (lam_on_bp && final_lam == lam);
         const bool rev = (k & 1) == 1;
         if (!wide_data && fin_data && !ties)
             eval_pass<T, true, true, true, false>(A, gp, final_lam, false, rev, acc, smem, ring_bars, ring_parity, err);
