@@ -597,22 +597,42 @@ __device__ __forceinline__ double breakpoint_pass(const GeneralArgs& A, const Gr
     return best;
 }
 
-// eq. (CQKlambda0) terms of V elements: s += b a/d, q += b^2/d (df, FP64 outside the range)
+// What a pass learnt about the data: a sanity check of Sec. 5.1.1 failed, an FP64 value lies
+// outside the df operating range, a bound is infinite.
+struct DataFlags {
+    bool bad, wide, luinf;
+};
+
+// eq. (CQKlambda0) terms of V elements: s += b a/d, q += b^2/d (df, FP64 outside the range),
+// and the checks of the data that the Newton passes rely on (the lambda_0 pass reads l and u
+// for them): the sanity checks of Sec. 5.1.1 (when check), infinite bounds and FP64 values
+// outside the df operating range
 template <typename T>
 __device__ __forceinline__ void lambda0_vec(const T (&va)[VecOf<T>::V], const T (&vb)[VecOf<T>::V],
-                                            const T (&vd)[VecOf<T>::V], const bool (&ok)[VecOf<T>::V], LazyDf& s,
-                                            LazyDf& q, double& s64, double& q64) {
+                                            const T (&vd)[VecOf<T>::V], const T (&vl)[VecOf<T>::V],
+                                            const T (&vu)[VecOf<T>::V], const bool (&ok)[VecOf<T>::V], LazyDf& s,
+                                            LazyDf& q, double& s64, double& q64, bool check, DataFlags& fl) {
     constexpr int V = VecOf<T>::V;
-    unsigned wide = 0;
+    unsigned exact = 0, wide = 0;
 #pragma unroll
     for (int j = 0; j < V; j++) {
         if (!ok[j]) continue;
-        const T a = va[j], b = vb[j], d = vd[j];
+        const T a = va[j], b = vb[j], d = vd[j], l = vl[j], u = vu[j];
         if constexpr (sizeof(T) == 8) {
-            // b, d positive in [2^-60, 2^60], a zero or in that range (exponent-field tests)
+            // operating range by exponent-field tests: b, d positive in [2^-60, 2^60]; a 0 or in
+            // that range; l, u 0, +-inf or in that range.  Values in range are not NaN, so of the
+            // sanity checks only l <= u remains for them; the others take the exact checks below.
             const unsigned ha = hi_word(a), la = lo_word(a);
+            const unsigned hl = hi_word(l), ll = lo_word(l), hu = hi_word(u), lu = lo_word(u);
+            auto rng = [](unsigned h) { return (((h >> 20) & 0x7FFu) - 963u) <= 120u; };
+            auto zero = [](unsigned h, unsigned lo) { return ((h & 0x7FFFFFFFu) | lo) == 0u; };
+            auto inf = [](unsigned h, unsigned lo) { return (h & 0x7FFFFFFFu) == 0x7FF00000u && lo == 0u; };
             const bool inr = ((hi_word(b) >> 20) - 963u) <= 120u && ((hi_word(d) >> 20) - 963u) <= 120u &&
-                             ((((ha >> 20) & 0x7FFu) - 963u) <= 120u || ((ha & 0x7FFFFFFFu) | la) == 0u);
+                             (rng(ha) || zero(ha, la));
+            const bool linf = inf(hl, ll), uinf = inf(hu, lu);
+            const bool lur = (rng(hl) || zero(hl, ll) || linf) && (rng(hu) || zero(hu, lu) || uinf);
+            fl.luinf |= linf || uinf;
+            if (check && inr && lur) fl.bad |= order_key(l) > order_key(u);
             const df B = split_f64_finite(b), D = split_f64_finite(d);
             const float r0 = rcp_approx(D.hi);
             const float res = fmaf(-D.lo, r0, fmaf(-D.hi, r0, 1.0f));
@@ -621,8 +641,11 @@ __device__ __forceinline__ void lambda0_vec(const T (&va)[VecOf<T>::V], const T 
             const df ps = df_mul_lazy(wgt, split_f64_finite(a)), pq = df_mul_lazy(wgt, B);
             lazy_add(s, df{inr ? ps.hi : 0.0f, inr ? ps.lo : 0.0f});
             lazy_add(q, df{inr ? pq.hi : 0.0f, inr ? pq.lo : 0.0f});
-            wide |= (inr ? 0u : 1u) << j;
+            exact |= (inr ? 0u : 1u) << j;
+            wide |= (inr && lur ? 0u : 1u) << j;
         } else {
+            if (check) fl.bad |= bad_elem_f(a, b, d, l, u);
+            fl.luinf |= isinf(l) || isinf(u);
             const float rd = rcp_approx(d);
             float wgt = __fmul_rn(b, rd);
             wgt = fmaf(fmaf(-wgt, d, b), rd, wgt);
@@ -630,21 +653,32 @@ __device__ __forceinline__ void lambda0_vec(const T (&va)[VecOf<T>::V], const T 
             lazy_add(q, two_prod(wgt, b));
         }
     }
-    for (unsigned m = wide; m; m &= m - 1) {  // exact FP64 outside the df range (rare)
+    for (unsigned m = exact; m; m &= m - 1) {  // exact FP64 outside the df range (rare)
         const int j = __ffs(m) - 1;
         const double a = pick(va, j), b = pick(vb, j), d = pick(vd, j);
         s64 += b * a / d;
         q64 += b * b / d;
     }
+    if constexpr (sizeof(T) == 8) {
+        fl.wide |= wide != 0u;
+        if (check)
+            for (unsigned m = wide; m; m &= m - 1) {
+                const int j = __ffs(m) - 1;
+                fl.bad |= bad_elem(pick(va, j), pick(vb, j), pick(vd, j), pick(vl, j), pick(vu, j));
+            }
+    }
 }
 
 template <typename T>
 __device__ __forceinline__ bool lambda0_pass(const GeneralArgs& A, const Grp& gp, double& s_out, double& q_out,
-                                             T* smem, uint64_t* bars, unsigned& parity, int* err) {
+                                             bool check, DataFlags& fl, T* smem, uint64_t* bars, unsigned& parity,
+                                             int* err) {
     constexpr int V = VecOf<T>::V;
     const T* __restrict__ pa = static_cast<const T*>(A.a);
     const T* __restrict__ pb = static_cast<const T*>(A.b);
     const T* __restrict__ pd = static_cast<const T*>(A.d);
+    const T* __restrict__ pl = static_cast<const T*>(A.l);
+    const T* __restrict__ pu = static_cast<const T*>(A.u);
     const Span sp = gp.sp;
     LazyDf s{0.0f, 0.0f}, q{0.0f, 0.0f};
     double s64 = 0.0, q64 = 0.0;
@@ -653,8 +687,8 @@ __device__ __forceinline__ bool lambda0_pass(const GeneralArgs& A, const Grp& gp
         constexpr int TT = stage_tile<T>();
         constexpr int VPT = TT / V / NT;
         using VT = typename VecOf<T>::type;
-        const T* src[3] = {pa, pb, pd};
-        TileRing<T, 3, TT> ring;
+        const T* src[5] = {pa, pb, pd, pl, pu};
+        TileRing<T, 5, TT> ring;
         ring.setup(sp.lo, sp.hi, smem, bars, gp.member, gp.g);
         ring.parity = parity;
         if (threadIdx.x == 0)
@@ -677,25 +711,31 @@ __device__ __forceinline__ bool lambda0_pass(const GeneralArgs& A, const Grp& gp
             for (int k = 0; k < VPT; k++) {
                 const int ql = (int)threadIdx.x + k * NT;
                 const int64_t qg = c * (TT / V) + ql;
-                T va[V], vb[V], vd[V];
+                T va[V], vb[V], vd[V], vl[V], vu[V];
                 bool ok[V];
                 if (qg * V >= sb0 && (qg + 1) * V <= sb1) {
                     const VT wa = reinterpret_cast<const VT*>(ring.stage(st, 0))[ql];
                     const VT wb = reinterpret_cast<const VT*>(ring.stage(st, 1))[ql];
                     const VT wd = reinterpret_cast<const VT*>(ring.stage(st, 2))[ql];
+                    const VT wl = reinterpret_cast<const VT*>(ring.stage(st, 3))[ql];
+                    const VT wu = reinterpret_cast<const VT*>(ring.stage(st, 4))[ql];
 #pragma unroll
                     for (int j = 0; j < V; j++) {
                         va[j] = reinterpret_cast<const T*>(&wa)[j];
                         vb[j] = reinterpret_cast<const T*>(&wb)[j];
                         vd[j] = reinterpret_cast<const T*>(&wd)[j];
+                        vl[j] = reinterpret_cast<const T*>(&wl)[j];
+                        vu[j] = reinterpret_cast<const T*>(&wu)[j];
                         ok[j] = true;
                     }
                 } else {
                     load_vec<T>(pa, sp, qg, false, va, ok);
                     load_vec<T>(pb, sp, qg, false, vb, ok);
                     load_vec<T>(pd, sp, qg, false, vd, ok);
+                    load_vec<T>(pl, sp, qg, false, vl, ok);
+                    load_vec<T>(pu, sp, qg, false, vu, ok);
                 }
-                lambda0_vec<T>(va, vb, vd, ok, s, q, s64, q64);
+                lambda0_vec<T>(va, vb, vd, vl, vu, ok, s, q, s64, q64, check, fl);
             }
             __syncthreads();
         }
@@ -713,16 +753,19 @@ __device__ __forceinline__ bool lambda0_pass(const GeneralArgs& A, const Grp& gp
                 steps = 0;
             }
             const int64_t base = sw.base(it, false);
-            T va[U][V], vb[U][V], vd[U][V];
+            T va[U][V], vb[U][V], vd[U][V], vl[U][V], vu[U][V];
             bool ok[U][V];
 #pragma unroll
             for (int w = 0; w < U; w++) {
                 load_vec<T>(pa, sp, base + w * 32 + lane, A.aligned != 0, va[w], ok[w]);
                 load_vec<T>(pb, sp, base + w * 32 + lane, A.aligned != 0, vb[w], ok[w]);
                 load_vec<T>(pd, sp, base + w * 32 + lane, A.aligned != 0, vd[w], ok[w]);
+                load_vec<T>(pl, sp, base + w * 32 + lane, A.aligned != 0, vl[w], ok[w]);
+                load_vec<T>(pu, sp, base + w * 32 + lane, A.aligned != 0, vu[w], ok[w]);
             }
 #pragma unroll
-            for (int w = 0; w < U; w++) lambda0_vec<T>(va[w], vb[w], vd[w], ok[w], s, q, s64, q64);
+            for (int w = 0; w < U; w++)
+                lambda0_vec<T>(va[w], vb[w], vd[w], vl[w], vu[w], ok[w], s, q, s64, q64, check, fl);
         }
     }
     s_out = lazy_value(s) + s64;
@@ -780,8 +823,9 @@ __device__ __forceinline__ void lambda0_warm_pass(const GeneralArgs& A, const Gr
                 inJ[j] = ok[w][j] && strictly_inside<T>(vl[w][j], vx[w][j], vu[w][j]);
                 m += inJ[j] ? 1 : 0;
             }
-            lambda0_vec<T>(va[w], vb[w], vd[w], inJ, sJ, qJ, sJ64, qJ64);
-            lambda0_vec<T>(va[w], vb[w], vd[w], ok[w], sA, qA, sA64, qA64);
+            DataFlags unused{false, false, false};  // (the first Newton pass checks the data)
+            lambda0_vec<T>(va[w], vb[w], vd[w], vl[w], vu[w], inJ, sJ, qJ, sJ64, qJ64, false, unused);
+            lambda0_vec<T>(va[w], vb[w], vd[w], vl[w], vu[w], ok[w], sA, qA, sA64, qA64, false, unused);
         }
     }
     out[0] = lazy_value(sJ) + sJ64;
@@ -850,9 +894,18 @@ __device__ __forceinline__ void general_solve(const GeneralArgs& A, const Grp& g
 
     // ---- pass 0: lambda_0
     double lam0 = A.lambda0;
+    int status = CQK_OK;
+    bool bad_input = false;
+    bool checked = false;   // the lambda_0 pass has checked the data
+    bool wide_data = true;  // until a pass has checked every value
+    bool fin_data = false;  // every bound finite (known once the data are checked)
     if (A.init == CQK_INIT_FORMULA) {
         double s, q;
-        lambda0_pass<T>(A, gp, s, q, smem, ring_bars, ring_parity, err);
+        DataFlags fl{false, false, false};
+        lambda0_pass<T>(A, gp, s, q, A.validate != 0, fl, smem, ring_bars, ring_parity, err);
+        if (__any_sync(0xffffffffu, fl.bad) && (threadIdx.x & 31) == 0) atomicOr(&gp.hdr->flags, kFlagBadInput);
+        if (__any_sync(0xffffffffu, fl.wide) && (threadIdx.x & 31) == 0) atomicOr(&gp.hdr->flags, kFlagWide);
+        if (__any_sync(0xffffffffu, fl.luinf) && (threadIdx.x & 31) == 0) atomicOr(&gp.hdr->flags, kFlagLuInf);
         double pv[2] = {s, q};
         block_sum_smem<2>(pv, bscr);
         write_partials<2>(gp.part, gp.member, G, par, pv);
@@ -862,6 +915,14 @@ __device__ __forceinline__ void general_solve(const GeneralArgs& A, const Grp& g
         par ^= 1;
         lam0 = (r - red[0]) / red[1];  // eq. (CQKlambda0), J = all variables
         passes++;
+        const unsigned fls = __ldcg(&gp.hdr->flags);
+        checked = true;
+        wide_data = (fls & kFlagWide) != 0;
+        fin_data = (fls & kFlagLuInf) == 0;
+        if (A.validate && (fls & kFlagBadInput)) {
+            bad_input = true;
+            status = CQK_BAD_INPUT;
+        }
     } else if (A.init == CQK_INIT_WARM) {
         double w[5];
         lambda0_warm_pass<T>(A, gp, w);
@@ -882,16 +943,13 @@ __device__ __forceinline__ void general_solve(const GeneralArgs& A, const Grp& g
     // bits from the same totals.
     double lam = lam0, lower = -INFINITY, upper = INFINITY, phi_lower = NAN, phi_upper = NAN, slope = 0.0;
     double final_lam = lam;
-    int status = CQK_OK, stop = CQK_STOP_NONE, k = 0;
-    bool bad_input = false;
-    bool wide_data = true;  // until the first pass has checked every value
-    bool fin_data = false;  // every bound finite (known after the first pass)
+    int stop = CQK_STOP_NONE, k = 0;
     // lambda may sit exactly on a breakpoint (it came from a breakpoint step, or is the caller's
     // start): only then is the tie band tested
     bool lam_on_bp = A.init == CQK_INIT_GIVEN;
     __shared__ double s_val[2];  // the next (or the final) lambda; the breakpoint search origin
     __shared__ int s_ctl[2];     // 1 = stop; breakpoint search direction (0: none)
-    for (k = 0;; k++) {
+    for (k = 0; !bad_input; k++) {
         if (k >= A.max_iter) {
             status = CQK_MAXITER;
             break;
@@ -903,14 +961,17 @@ __device__ __forceinline__ void general_solve(const GeneralArgs& A, const Grp& g
         // would; the tie band of the file header is needed after a breakpoint step (or at a start
         // the caller gave)
         const bool rev = (k & 1) == 1;
-        const bool chk = k == 0 && A.validate;
-        if (k > 0 && !wide_data && fin_data && !lam_on_bp)
+        const bool first = k == 0 && !checked;  // this pass checks the data
+        const bool chk = first && A.validate;
+        // the checked fast path: every value valid and in the df range, and |lambda| <= 2^60
+        const bool fast = !first && !wide_data && fabs(lam) <= 1.152921504606847e18;
+        if (fast && fin_data && !lam_on_bp)
             eval_pass<T, false, true, true, false>(A, gp, lam, false, rev, acc, smem, ring_bars, ring_parity, err);
-        else if (k > 0 && !wide_data && fin_data)
+        else if (fast && fin_data)
             eval_pass<T, false, true, true, true>(A, gp, lam, false, rev, acc, smem, ring_bars, ring_parity, err);
-        else if (k > 0 && !wide_data && !lam_on_bp)
+        else if (fast && !lam_on_bp)
             eval_pass<T, false, true, false, false>(A, gp, lam, false, rev, acc, smem, ring_bars, ring_parity, err);
-        else if (k > 0 && !wide_data)
+        else if (fast)
             eval_pass<T, false, true, false, true>(A, gp, lam, false, rev, acc, smem, ring_bars, ring_parity, err);
         else if (!lam_on_bp)
             eval_pass<T, false, false, false, false>(A, gp, lam, chk, rev, acc, smem, ring_bars, ring_parity, err);
@@ -918,8 +979,8 @@ __device__ __forceinline__ void general_solve(const GeneralArgs& A, const Grp& g
         acc.flush();
         passes++;
         if (__any_sync(0xffffffffu, acc.bad) && (threadIdx.x & 31) == 0) atomicOr(&gp.hdr->flags, kFlagBadInput);
-        if (k == 0 && __any_sync(0xffffffffu, acc.wide) && (threadIdx.x & 31) == 0) atomicOr(&gp.hdr->flags, kFlagWide);
-        if (k == 0 && __any_sync(0xffffffffu, acc.luinf) && (threadIdx.x & 31) == 0) atomicOr(&gp.hdr->flags, kFlagLuInf);
+        if (first && __any_sync(0xffffffffu, acc.wide) && (threadIdx.x & 31) == 0) atomicOr(&gp.hdr->flags, kFlagWide);
+        if (first && __any_sync(0xffffffffu, acc.luinf) && (threadIdx.x & 31) == 0) atomicOr(&gp.hdr->flags, kFlagLuInf);
         double pv[5] = {acc.phi64, acc.sfree64, acc.satl, acc.satu, acc.absbx64};
         block_sum_smem<5>(pv, bscr);
         write_partials<5>(gp.part, gp.member, G, par, pv);
@@ -927,11 +988,11 @@ __device__ __forceinline__ void general_solve(const GeneralArgs& A, const Grp& g
         double red[5];
         grid_reduce<5>(gp.part, G, par, -1, red, sh, bc);
         par ^= 1;
-        if (k == 0) {
+        if (first) {
             wide_data = (__ldcg(&gp.hdr->flags) & kFlagWide) != 0;
             fin_data = (__ldcg(&gp.hdr->flags) & kFlagLuInf) == 0;
         }
-        if (k == 0 && A.validate && (__ldcg(&gp.hdr->flags) & kFlagBadInput)) {
+        if (first && A.validate && (__ldcg(&gp.hdr->flags) & kFlagBadInput)) {
             bad_input = true;
             status = CQK_BAD_INPUT;
             k++;
@@ -1081,13 +1142,14 @@ __device__ __forceinline__ void general_solve(const GeneralArgs& A, const Grp& g
         // formed at a breakpoint lambda and clamp the stored float x instead
         const bool ties = sizeof(T) == 8 || (lam_on_bp && final_lam == lam);
         const bool rev = (k & 1) == 1;
-        if (!wide_data && fin_data && !ties)
+        const bool fast = !wide_data && fabs(final_lam) <= 1.152921504606847e18;  // (as in the Newton passes)
+        if (fast && fin_data && !ties)
             eval_pass<T, true, true, true, false>(A, gp, final_lam, false, rev, acc, smem, ring_bars, ring_parity, err);
-        else if (!wide_data && fin_data)
+        else if (fast && fin_data)
             eval_pass<T, true, true, true, true>(A, gp, final_lam, false, rev, acc, smem, ring_bars, ring_parity, err);
-        else if (!wide_data && !ties)
+        else if (fast && !ties)
             eval_pass<T, true, true, false, false>(A, gp, final_lam, false, rev, acc, smem, ring_bars, ring_parity, err);
-        else if (!wide_data)
+        else if (fast)
             eval_pass<T, true, true, false, true>(A, gp, final_lam, false, rev, acc, smem, ring_bars, ring_parity, err);
         else eval_pass<T, true, false>(A, gp, final_lam, false, rev, acc, smem, ring_bars, ring_parity, err);
         passes++;
