@@ -205,8 +205,8 @@ __device__ __forceinline__ void bwd_instance(const BwdArgs& A, const Grp& gp, in
     if (!inside) {
         for (int64_t it = 0; it < sw.count; it++) {
             if ((it & 7) == 7) {
-                S64 += lazy_value(Sl);
-                Q64 += lazy_value(Ql);
+                S64 += lazy_value_int(Sl);
+                Q64 += lazy_value_int(Ql);
                 Sl = Ql = LazyDf{0.0f, 0.0f};
             }
             const int64_t base = sw.base(it, false);
@@ -265,7 +265,7 @@ __device__ __forceinline__ void bwd_instance(const BwdArgs& A, const Grp& gp, in
             }
         }
     }
-    double pv[2] = {lazy_value(Sl) + S64, KIND == kBwdGeneral ? lazy_value(Ql) + Q64 : (double)nF + Q64};
+    double pv[2] = {lazy_value_int(Sl) + S64, KIND == kBwdGeneral ? lazy_value_int(Ql) + Q64 : (double)nF + Q64};
     double red[2];
     if constexpr (WARP) {
         red[0] = warp_sum(pv[0]);
@@ -477,7 +477,7 @@ __device__ void bwd_simplex_staged(const BwdArgs& A, const Grp& gp, int64_t inst
     long long nF = 0;
     sweep(false, [&](const T* stage, int64_t c, int64_t sb0, int64_t sb1, int64_t i, const uint32_t (&mw)[VPT]) {
         if ((i & 7) == 7) {
-            S64 += lazy_value(Sl);
+            S64 += lazy_value_int(Sl);
             Sl = LazyDf{0.0f, 0.0f};
         }
 #pragma unroll
@@ -500,7 +500,7 @@ __device__ void bwd_simplex_staged(const BwdArgs& A, const Grp& gp, int64_t inst
             }
         }
     });
-    double pv[2] = {lazy_value(Sl) + S64, (double)nF + Q64};
+    double pv[2] = {lazy_value_int(Sl) + S64, (double)nF + Q64};
     double red[2];
     block_sum<2>(pv, sh);
     write_partials<2>(gp.part, gp.member, gp.g, 0, pv);

@@ -211,6 +211,23 @@ __device__ __forceinline__ void lazy_add(LazyDf& a, df x) {
     a.lo = __fadd_rn(a.lo, __fadd_rn(s.lo, x.lo));
 }
 __device__ __forceinline__ double lazy_value(LazyDf a) { return (double)a.hi + (double)a.lo; }
+// float -> double on the integer pipe for every finite float, subnormals included (normalised
+// by the position of their leading one)
+__device__ __forceinline__ double f32_to_f64_bits_all(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned m = u & 0x7FFFFFu;
+    if ((u & 0x7F800000u) != 0u || m == 0u) return f32_to_f64_bits(f);
+    const int p = 31 - __clz((int)m);  // f = m 2^-149, leading one at bit p
+    const unsigned long long bits = ((unsigned long long)(u & 0x80000000u) << 32) |
+                                    ((unsigned long long)(p + 874) << 52) |
+                                    ((unsigned long long)(m ^ (1u << p)) << (52 - p));
+    return __longlong_as_double((long long)bits);
+}
+// the same sum as lazy_value with the parts widened on the integer pipe (one FP64 add, no
+// conversion instruction: F2F runs on the FP64 pipe, this GPU's scarce unit)
+__device__ __forceinline__ double lazy_value_int(LazyDf a) {
+    return f32_to_f64_bits_all(a.hi) + f32_to_f64_bits_all(a.lo);
+}
 
 // true iff x is 0, +-inf (when allow_inf) or a finite value with 2^-60 <= |x| <= 2^60
 __device__ __forceinline__ bool df_in_range(double x, bool allow_inf) {

@@ -703,8 +703,8 @@ __device__ __forceinline__ bool lambda0_pass(const GeneralArgs& A, const Grp& gp
             const int64_t c = ring.tile(i, false);
             const int64_t sb0 = ring.b0(c), sb1 = ring.b1(c);
             if ((i & 7) == 7) {
-                s64 += lazy_value(s);
-                q64 += lazy_value(q);
+                s64 += lazy_value_int(s);
+                q64 += lazy_value_int(q);
                 s = q = LazyDf{0.0f, 0.0f};
             }
 #pragma unroll
@@ -747,8 +747,8 @@ __device__ __forceinline__ bool lambda0_pass(const GeneralArgs& A, const Grp& gp
         int steps = 0;
         for (int64_t it = 0; it < sw.count; it++) {
             if (++steps == kFlushEvery) {
-                s64 += lazy_value(s);
-                q64 += lazy_value(q);
+                s64 += lazy_value_int(s);
+                q64 += lazy_value_int(q);
                 s = q = LazyDf{0.0f, 0.0f};
                 steps = 0;
             }
@@ -768,8 +768,8 @@ __device__ __forceinline__ bool lambda0_pass(const GeneralArgs& A, const Grp& gp
                 lambda0_vec<T>(va[w], vb[w], vd[w], vl[w], vu[w], ok[w], s, q, s64, q64, check, fl);
         }
     }
-    s_out = lazy_value(s) + s64;
-    q_out = lazy_value(q) + q64;
+    s_out = lazy_value_int(s) + s64;
+    q_out = lazy_value_int(q) + q64;
     return okw;
 }
 
