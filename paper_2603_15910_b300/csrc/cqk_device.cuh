@@ -223,6 +223,9 @@ __device__ __forceinline__ double f32_to_f64_bits_all(float f) {
                                     ((unsigned long long)(m ^ (1u << p)) << (52 - p));
     return __longlong_as_double((long long)bits);
 }
+// df -> double as df_to_f64 (one FP64 add) with the parts widened on the integer pipe, exact for
+// every finite part (pass-end sums; the per-element conversion is df_to_f64_int)
+__device__ __forceinline__ double df_to_f64_int_all(df a) { return f32_to_f64_bits_all(a.hi) + f32_to_f64_bits_all(a.lo); }
 // the same sum as lazy_value with the parts widened on the integer pipe (one FP64 add, no
 // conversion instruction: F2F runs on the FP64 pipe, this GPU's scarce unit)
 __device__ __forceinline__ double lazy_value_int(LazyDf a) {

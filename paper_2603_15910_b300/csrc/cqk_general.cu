@@ -389,7 +389,7 @@ __device__ __forceinline__ void eval_vec(const GeneralArgs& A, const T (&va)[Vec
         if (TIES && !write_x) {
             for (unsigned m = tiem; m; m &= m - 1) {
                 const int bit = __ffs(m) - 1;
-                const double bj = df_to_f64(pick(beta, bit >> 1));
+                const double bj = df_to_f64_int_all(pick(beta, bit >> 1));
                 if (bit & 1) acc.satu += bj;
                 else acc.satl += bj;
             }
@@ -795,10 +795,10 @@ __device__ __forceinline__ void lambda0_warm_pass(const GeneralArgs& A, const Gr
     int steps = 0;
     for (int64_t it = 0; it < sw.count; it++) {
         if (++steps == kFlushEvery) {
-            sJ64 += lazy_value(sJ);
-            qJ64 += lazy_value(qJ);
-            sA64 += lazy_value(sA);
-            qA64 += lazy_value(qA);
+            sJ64 += lazy_value_int(sJ);
+            qJ64 += lazy_value_int(qJ);
+            sA64 += lazy_value_int(sA);
+            qA64 += lazy_value_int(qA);
             sJ = qJ = sA = qA = LazyDf{0.0f, 0.0f};
             steps = 0;
         }
@@ -828,11 +828,11 @@ __device__ __forceinline__ void lambda0_warm_pass(const GeneralArgs& A, const Gr
             lambda0_vec<T>(va[w], vb[w], vd[w], vl[w], vu[w], ok[w], sA, qA, sA64, qA64, false, unused);
         }
     }
-    out[0] = lazy_value(sJ) + sJ64;
-    out[1] = lazy_value(qJ) + qJ64;
+    out[0] = lazy_value_int(sJ) + sJ64;
+    out[1] = lazy_value_int(qJ) + qJ64;
     out[2] = (double)m;
-    out[3] = lazy_value(sA) + sA64;
-    out[4] = lazy_value(qA) + qA64;
+    out[3] = lazy_value_int(sA) + sA64;
+    out[4] = lazy_value_int(qA) + qA64;
 }
 
 #define CQK_BARRIER_OR_LEAVE()                                                  \

@@ -84,7 +84,7 @@ struct SumAcc {
         acc64 += df_to_f64_int(df{lz.hi, lz.lo});
         lz = LazyDf{0.0f, 0.0f};
     }
-    __device__ double sum() const { return df_to_f64(acc) + acc64 + df_to_f64_int(df{lz.hi, lz.lo}) + acc_wide; }
+    __device__ double sum() const { return df_to_f64_int_all(acc) + acc64 + df_to_f64_int(df{lz.hi, lz.lo}) + acc_wide; }
 };
 
 // one element; returns true when an FP64 value lies outside the df range (the caller adds it
@@ -1233,7 +1233,7 @@ __device__ __forceinline__ void newton_pass(const T* __restrict__ y, const Span&
         const df Lm = df_from_f64(lam);
         if (first) newton_sweep<T, L1, false, true>(y, sp, sw, aligned, rev, 0ull, rd, ru, lam, Lm, pa);
         else newton_sweep<T, L1, false, false>(y, sp, sw, aligned, rev, 0ull, rd, ru, lam, Lm, pa);
-        pa.acc64 = df_to_f64(pa.acc32);
+        pa.acc64 = df_to_f64_int_all(pa.acc32);
     }
 }
 
@@ -1725,7 +1725,7 @@ __device__ __forceinline__ void simplex_solve(const SimplexArgs& A, const Grp& g
     if (!bad_input)
         final_sweep<T, L1>(y, x, A.mask, sp, WarpSweep(qlo, qhi, kStreamU, gp.member, gp.g), aligned, (k & 1) == 0,
                            copy, final_lam, sx, sx32, nz);
-    if constexpr (sizeof(T) == 4) sx = df_to_f64(sx32);
+    if constexpr (sizeof(T) == 4) sx = df_to_f64_int_all(sx32);
     double pv[2] = {sx, (double)nz}, tot[2];
     if (last_block_sums<2>(gp.part, gp.member, G, &gp.hdr->ticket, pv, tot, sh) && threadIdx.x == 0) {
         cqk_info inf;
@@ -1893,7 +1893,7 @@ __device__ void simplex_warp_solve(const SimplexArgs& A, const Span& sp, double*
     if (status != CQK_BAD_INPUT)
         final_sweep<T, L1>(y, static_cast<T*>(A.x), A.mask, sp, WarpSweep::solo(qlo, qhi, kStreamU), aligned,
                            (k & 1) == 0, copy, final_lam, sx, sx32, nz);
-    if constexpr (sizeof(T) == 4) sx = df_to_f64(sx32);
+    if constexpr (sizeof(T) == 4) sx = df_to_f64_int_all(sx32);
     sx = warp_sum(sx);
     const long long nzt = (long long)__reduce_add_sync(0xffffffffu, (unsigned)nz);
     if (lane == 0) {
