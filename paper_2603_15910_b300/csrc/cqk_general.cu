@@ -513,14 +513,13 @@ __device__ __forceinline__ bool eval_pass_staged(const GeneralArgs& A, const Grp
     ring.parity = parity;
     const df Lm = df_from_f64(lam);
     const bool lam_ok = fabs(lam) <= 1.152921504606847e18;  // 2^60
-    if (threadIdx.x == 0)
-        for (int s = 0; s < kStages - 1; s++)
-            if (s < ring.count) ring.issue(ring.tile(s, rev), s, src);
+    for (int s = 0; s < kStages - 1; s++)
+        if (s < ring.count) ring.issue_by_warps(ring.tile(s, rev), s, src);
     bool okw = true;
     for (int64_t i = 0; i < ring.count; i++) {
         const int st = (int)(i % kStages);
-        if (threadIdx.x == 0 && i + kStages - 1 < ring.count)
-            ring.issue(ring.tile(i + kStages - 1, rev), (int)((i + kStages - 1) % kStages), src);
+        if (i + kStages - 1 < ring.count)
+            ring.issue_by_warps(ring.tile(i + kStages - 1, rev), (int)((i + kStages - 1) % kStages), src);
         if (!mbar_wait(&ring.bar[st], (ring.parity >> st) & 1u, err, A.limit_ns, CQK_TIMEOUT)) okw = false;
         ring.parity ^= 1u << st;
         const int64_t c = ring.tile(i, rev);
@@ -691,13 +690,12 @@ __device__ __forceinline__ bool lambda0_pass(const GeneralArgs& A, const Grp& gp
         TileRing<T, 5, TT> ring;
         ring.setup(sp.lo, sp.hi, smem, bars, gp.member, gp.g);
         ring.parity = parity;
-        if (threadIdx.x == 0)
-            for (int st = 0; st < kStages - 1; st++)
-                if (st < ring.count) ring.issue(ring.tile(st, false), st, src);
+        for (int st = 0; st < kStages - 1; st++)
+            if (st < ring.count) ring.issue_by_warps(ring.tile(st, false), st, src);
         for (int64_t i = 0; i < ring.count; i++) {
             const int st = (int)(i % kStages);
-            if (threadIdx.x == 0 && i + kStages - 1 < ring.count)
-                ring.issue(ring.tile(i + kStages - 1, false), (int)((i + kStages - 1) % kStages), src);
+            if (i + kStages - 1 < ring.count)
+                ring.issue_by_warps(ring.tile(i + kStages - 1, false), (int)((i + kStages - 1) % kStages), src);
             if (!mbar_wait(&ring.bar[st], (ring.parity >> st) & 1u, err, A.limit_ns, CQK_TIMEOUT)) okw = false;
             ring.parity ^= 1u << st;
             const int64_t c = ring.tile(i, false);

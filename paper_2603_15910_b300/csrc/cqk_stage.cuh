@@ -104,6 +104,19 @@ struct TileRing {
     __device__ __forceinline__ T* stage(int s, int a) const { return buf + ((size_t)s * NA + a) * TT; }
     __device__ __forceinline__ int64_t b0(int64_t c) const { return c * TT > slo ? c * TT : slo; }
     __device__ __forceinline__ int64_t b1(int64_t c) const { return (c + 1) * TT < shi ? (c + 1) * TT : shi; }
+    // called by every thread: lane 0 of warp w starts the copies of arrays w, w + NWARP, ... of
+    // tile c into stage s (warp 0 also registers the stage's bytes), so that the issue cost is
+    // spread over the warps instead of delaying one
+    __device__ __forceinline__ void issue_by_warps(int64_t c, int s, const T* const* src) const {
+        const int w = threadIdx.x >> 5;
+        if ((threadIdx.x & 31) != 0 || w >= NA) return;
+        const int64_t lo = b0(c), hi = b1(c);
+        const uint32_t bytes = hi > lo ? (uint32_t)((hi - lo) * (int64_t)sizeof(T)) : 0u;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        if (w == 0) mbar_arrive_expect_tx(&bar[s], bytes * NA);
+        if (bytes)
+            for (int a = w; a < NA; a += NWARP) bulk_g2s(stage(s, a) + (lo - c * TT), src[a] + lo, bytes, &bar[s]);
+    }
     // thread 0: start the copies of tile c into stage s
     __device__ __forceinline__ void issue(int64_t c, int s, const T* const* src) const {
         const int64_t lo = b0(c), hi = b1(c);
