@@ -626,13 +626,21 @@ __device__ __forceinline__ void lambda0_vec(const T (&va)[VecOf<T>::V], const T 
             auto rng = [](unsigned h) { return (((h >> 20) & 0x7FFu) - 963u) <= 120u; };
             auto zero = [](unsigned h, unsigned lo) { return ((h & 0x7FFFFFFFu) | lo) == 0u; };
             auto inf = [](unsigned h, unsigned lo) { return (h & 0x7FFFFFFFu) == 0x7FF00000u && lo == 0u; };
-            const bool inr = ((hi_word(b) >> 20) - 963u) <= 120u && ((hi_word(d) >> 20) - 963u) <= 120u &&
+            // (b, d: the pattern itself in [2^-60, 2^61) as an unsigned range, a set sign bit fails)
+            const bool inr = hi_word(b) - 0x3C300000u < 0x07900000u && hi_word(d) - 0x3C300000u < 0x07900000u &&
                              (rng(ha) || zero(ha, la));
             const bool linf = inf(hl, ll), uinf = inf(hu, lu);
             const bool lur = (rng(hl) || zero(hl, ll) || linf) && (rng(hu) || zero(hu, lu) || uinf);
             fl.luinf |= linf || uinf;
-            if (check && inr && lur) fl.bad |= order_key(l) > order_key(u);
-            const df B = split_f64_finite(b), D = split_f64_finite(d);
+            if (check && inr && lur) {
+                // l > u on order keys of the high words (signed magnitude -> two's complement),
+                // the low words deciding between equal high words; +0 and -0 compare equal
+                const int kl = (int)(hl ^ ((unsigned)((int)hl >> 31) >> 1));
+                const int ku = (int)(hu ^ ((unsigned)((int)hu >> 31) >> 1));
+                const bool lo_gt = (int)hl < 0 ? ll < lu : ll > lu;
+                fl.bad |= (kl > ku || (kl == ku && lo_gt)) && !(zero(hl, ll) && zero(hu, lu));
+            }
+            const df B = split_f64_pos(b), D = split_f64_pos(d);  // (discarded unless in range)
             const float r0 = rcp_approx(D.hi);
             const float res = fmaf(-D.lo, r0, fmaf(-D.hi, r0, 1.0f));
             const df invd = fast_two_sum(r0, __fmul_rn(r0, res));
