@@ -205,11 +205,12 @@ __device__ __forceinline__ df elem_df(df A, df B, df D, df Lo, df Up, df Lm, Cls
     return elem_df_tail<FIN, TIES>(v, __fadd_rn(fabsf(A.hi), fabsf(p.hi)), B, D, Lo, Up, cl, bx, beta);
 }
 
-// sanity checks of Sec. 5.1.1 on the bit patterns: d > 0, b > 0 finite; a finite; l <= u;
-// no NaN (integer pipe only)
+// sanity checks of Sec. 5.1.1 on the bit patterns: d > 0, b > 0 finite; a finite; l <= u
+// (as IEEE compares: +0 <= -0); no NaN (integer pipe only)
 __device__ __forceinline__ bool bad_elem(double a, double b, double d, double l, double u) {
+    const bool zeros = ((opaque_bits(l) | opaque_bits(u)) << 1) == 0ull;
     return !f64_pos_finite(d) || !f64_pos_finite(b) || !f64_is_finite(a) || f64_is_nan(l) || f64_is_nan(u) ||
-           order_key(l) > order_key(u);
+           (order_key(l) > order_key(u) && !zeros);
 }
 
 // the same checks on float bit patterns
@@ -220,7 +221,7 @@ __device__ __forceinline__ bool bad_elem_f(float a, float b, float d, float l, f
     auto is_nan = [](int v) { return (v & 0x7FFFFFFF) > 0x7F800000; };
     auto key = [](int v) { return v >= 0 ? v : (int)(0x80000000u - (unsigned)v) - 1; };
     return !pos_finite(id) || !pos_finite(ib) || (ia & 0x7F800000) == 0x7F800000 || is_nan(il) || is_nan(iu) ||
-           key(il) > key(iu);
+           (key(il) > key(iu) && ((il | iu) & 0x7FFFFFFF) != 0);
 }
 
 // ---- FP32 data -----------------------------------------------------------------------------

@@ -155,6 +155,31 @@ def test_infeasible_and_bad_input():
     assert info.status == api.Status.BAD_INPUT
 
 
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("init", ["formula", "given"])
+def test_signed_zero_bounds_are_valid(dtype, init):
+    # l = +0, u = -0 satisfies l <= u (IEEE: the two zeros are equal), so the sanity check of
+    # Sec. 5.1.1 passes and x_i = 0; also with an element outside the double-float range,
+    # which takes the exact checks
+    h = W.uncorrelated_box(3000, seed=21)
+    h["l"][::97] = 0.0
+    h["u"][::97] = -0.0
+    if dtype == torch.float64:
+        h["a"][5] *= 1e-25
+    h["r"] = float((h["b"] * (h["l"] + h["u"]) / 2).sum())
+    p = _dev(h, dtype)
+    a, b, d, l, u = _np(p)
+    assert np.all(l <= u)
+    st, lam_star, xstar = oracle.solve_sort(a, b, d, l, u, p["r"])
+    assert st == "ok"
+    kw = {} if init == "formula" else dict(init=api.Init.GIVEN, lambda0=lam_star * 0.9)
+    x, info, _ = api.solve(p["a"], p["b"], p["d"], p["l"], p["u"], p["r"], **kw)
+    assert info.status == api.Status.OK, info
+    xs = np64(x)
+    assert np.all(xs[::97] == 0.0)
+    assert_x_close(xs, xstar, dtype, init)
+
+
 def test_values_outside_the_double_float_range_are_exact():
     p = W.uncorrelated_box(5000, seed=12)
     p["a"][::7] *= 1e-25
