@@ -141,6 +141,47 @@ __device__ __forceinline__ void store_mask(uint32_t* mask, const Span& sp, int64
     }
 }
 
+// The free-mask bits of U consecutive rows of 32 vectors (row u holds the vectors
+// base + 32u ... base + 32u + 31, lane L the vector base + 32u + L; base a multiple of 32),
+// written as whole words: the U*V words of the rows, word w by lane w, one store per lane
+// instead of one shuffle chain and one 4-byte store per row.  Each lane packs its U*V bits
+// (bit u*V + j = element j of its vector of row u); the lane of word w gathers its V-bit
+// pieces from the 32/V lanes that hold the word's elements.  Words shared with another span
+// are merged with atomics on this span's bits.
+template <int V, int U>
+__device__ __forceinline__ void store_mask_rows(uint32_t* mask, const Span& sp, int64_t base,
+                                                const bool (&sel)[U][V]) {
+    static_assert(U * V <= 32 && 32 % V == 0, "the rows' words fit one per lane");
+    constexpr int LPW = 32 / V;  // lanes per mask word
+    constexpr int NW = U * V;    // words of the U rows
+    const int lane = threadIdx.x & 31;
+    unsigned p = 0;
+#pragma unroll
+    for (int u = 0; u < U; u++)
+#pragma unroll
+        for (int j = 0; j < V; j++) p |= (sel[u][j] ? 1u : 0u) << (u * V + j);
+    const int ru = lane / V, rk = lane % V;  // this lane's word: row ru, word rk of the row
+    const unsigned piece = (1u << V) - 1u;
+    unsigned word = 0;
+#pragma unroll
+    for (int i = 0; i < LPW; i++) {
+        const unsigned q = __shfl_sync(0xffffffffu, p, (rk * LPW + i) & 31);
+        word |= ((q >> ((ru * V) & 31)) & piece) << (i * V);
+    }
+    if (lane >= NW) return;
+    const int64_t wi = base * V / 32 + lane;  // global word index
+    const int64_t w0 = wi * 32;
+    if (w0 >= sp.hi || w0 + 32 <= sp.lo) return;
+    if (w0 >= sp.lo && w0 + 32 <= sp.hi) {
+        mask[wi] = word;
+    } else {
+        const int64_t a = sp.lo > w0 ? sp.lo - w0 : 0, b = sp.hi < w0 + 32 ? sp.hi - w0 : 32;
+        const unsigned in = (b >= 32 ? 0xFFFFFFFFu : ((1u << b) - 1u)) & ~((1u << a) - 1u);
+        atomicAnd(&mask[wi], ~in | word);
+        atomicOr(&mask[wi], word & in);
+    }
+}
+
 // Warp-contiguous traversal of the vectors [qlo, qhi) by the warps of a group: iteration i of
 // warp w (of W = g * NWARP) covers the vectors [base, base + 32*U) with
 // base = floor(qlo/32)*32 + (w + i*W)*32*U, lane L taking base + k*32 + L (k < U), so every

@@ -1374,6 +1374,7 @@ __device__ __forceinline__ void final_sweep(const T* __restrict__ y, T* __restri
             const int64_t base = sw.base(it, rev);
             T vv[kStreamU][V];
             bool okk[kStreamU][V];
+            bool sela[kStreamU][V];  // the iteration's mask bits, stored together after the rows
 #pragma unroll
             for (int u = 0; u < kStreamU; u++) load_vec<T>(y, sp, base + u * 32 + lane, aligned, vv[u], okk[u]);
 #pragma unroll
@@ -1383,7 +1384,7 @@ __device__ __forceinline__ void final_sweep(const T* __restrict__ y, T* __restri
                 const T(&v)[V] = vv[u];
                 const bool(&ok)[V] = okk[u];
                 T o[V];
-                bool sel[V];
+                bool(&sel)[V] = sela[u];
                 unsigned selv = 0;
 #pragma unroll
                 for (int j = 0; j < V; j++) {
@@ -1422,8 +1423,8 @@ __device__ __forceinline__ void final_sweep(const T* __restrict__ y, T* __restri
                     }
                 }
                 store_vec<T>(x, sp, q, aligned, o);
-                if (mask) store_mask<V>(mask, sp, qw, sel);
             }
+            if (mask) store_mask_rows<V, kStreamU>(mask, sp, base, sela);
         }
     }
 }
