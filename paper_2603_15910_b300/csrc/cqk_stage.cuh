@@ -56,6 +56,19 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
     return ok != 0;
 }
 
+// try_wait with a suspend-time hint: the thread may be suspended until the phase completes or
+// about `hint_ns` pass, instead of polling (a polling warp takes issue slots from the warps of
+// its SM sub-partition)
+__device__ __forceinline__ bool mbar_try_wait_suspend(uint64_t* bar, unsigned parity, unsigned hint_ns) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return ok != 0;
+}
+
 // Bounded wait for the completion of phase `parity` of `bar`.  On expiry the error flag is
 // set and the wait goes on for up to another `limit_ns` (the copies of this block must land
 // before it can leave); returns false if the barrier never completed.
@@ -64,7 +77,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, int* e
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = globaltimer_ns();
     bool flagged = false;
-    while (!mbar_try_wait(bar, parity)) {
+    while (!mbar_try_wait_suspend(bar, parity, 1000u)) {
         const unsigned long long dt = globaltimer_ns() - t0;
         if (!flagged && dt > limit_ns) {
             atomicExch(error, timeout_code);
