@@ -747,7 +747,7 @@ def batched_extras(api, W, dev, stream, oracle_check=True):
         lens = [offs[k + 1] - offs[k] for k in range(B)]
         if general:
             fwd_bytes = sum(es * m * (3 + 5 * (i.passes - 2) + 6) + m / 8 for m, i in zip(lens, infos) if m)
-            bwd_bytes = sum(es * m * (4 + 6 + 5) + m / 4 for m in lens)  # g,x,b,d | g,x,b,d,l,u -> 5 grads
+            bwd_bytes = sum(es * m * (3 + 6 + 5) + m / 4 for m in lens)  # g,b,d | g,x,b,d,l,u -> 5 grads
         else:
             fwd_bytes = sum(es * m * (i.passes + 1) + m / 8 for m, i in zip(lens, infos) if m)
             bwd_bytes = sum(es * m * 3 + m / 4 for m in lens)  # g | g -> gy, mask read twice

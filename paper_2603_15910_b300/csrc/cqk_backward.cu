@@ -198,7 +198,9 @@ __device__ __forceinline__ void bwd_instance(const BwdArgs& A, const Grp& gp, in
     const WarpSweep sw = WARP ? WarpSweep::solo(span_qlo<V>(sp), span_qhi<V>(sp), U)
                               : WarpSweep(span_qlo<V>(sp), span_qhi<V>(sp), U, gp.member, gp.g);
 
-    // ---- pass 1: sum_F b g/d and Q = sum_F b^2/d (simplex / l1: sum_F (s) g and |F|)
+    // ---- pass 1: sum_F b g/d and Q = sum_F b^2/d (simplex / l1: sum_F (s) g and |F|); the
+    // general kind with the forward mask needs neither x nor l, u here
+    const void* xp1 = (KIND == kBwdGeneral && A.mask) ? nullptr : xp;
     LazyDf Sl{0.0f, 0.0f}, Ql{0.0f, 0.0f};
     double S64 = 0.0, Q64 = 0.0;
     long long nF = 0;
@@ -218,7 +220,7 @@ __device__ __forceinline__ void bwd_instance(const BwdArgs& A, const Grp& gp, in
                 const int64_t q = base + w * 32 + lane;
                 load_vec<T>(static_cast<const T*>(A.g), sp, q, aligned, vg[w], ok[w]);
                 mw[w] = mask_word<T>(A, sp, q);
-                load_or<T>(xp, sp, q, aligned, vx[w], ok[w], T(0));
+                load_or<T>(xp1, sp, q, aligned, vx[w], ok[w], T(0));
                 if (KIND == kBwdGeneral) {
                     load_or<T>(A.b, sp, q, aligned, vb[w], ok[w], T(1));
                     load_or<T>(A.d, sp, q, aligned, vd[w], ok[w], T(1));
