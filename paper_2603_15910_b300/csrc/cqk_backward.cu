@@ -34,7 +34,11 @@ constexpr int kBwdUNoX = 3;
 constexpr int kBwdU = 4;
 constexpr int kBwdUNoX = 6;
 #endif
-constexpr int kBwdUGen = 1;  // general: 6 arrays, and the register budget of the double-float map
+// general: a single instance keeps two vectors per array in flight (n = 2e7 FP64: 0.62 ->
+// 0.58 ms); the batched kernel, whose per-slot state takes registers too, keeps one (two
+// spilled and measured slower on the 256-instance batch)
+constexpr int kBwdUGen = 2;
+constexpr int kBwdUGenBatched = 1;
 
 enum BwdKind { kBwdGeneral = 0, kBwdSimplex = 1, kBwdL1 = 2 };
 
@@ -181,10 +185,10 @@ __device__ __noinline__ void bwd_map_exact(double g, double x, double b, double 
 
 // one instance by one group (WARP: by one warp alone; gp.sp is the only field used).  NOX: the
 // simplex with the forward mask, where F comes from the mask and x is not read.
-template <typename T, int KIND, bool NOX, bool WARP = false>
+template <typename T, int KIND, bool NOX, bool WARP = false, int UG = kBwdUGen>
 __device__ __forceinline__ void bwd_instance(const BwdArgs& A, const Grp& gp, int64_t inst) {
     constexpr int V = VecOf<T>::V;
-    constexpr int U = KIND == kBwdGeneral ? kBwdUGen : (NOX ? kBwdUNoX : kBwdU);
+    constexpr int U = KIND == kBwdGeneral ? UG : (NOX ? kBwdUNoX : kBwdU);
     __shared__ double sh[kPartialQ][NWARP];
     __shared__ double bc[kPartialQ];
     const Span sp = gp.sp;
@@ -599,7 +603,7 @@ __global__ void __launch_bounds__(NT, kMinBlocksPerSM) backward_kernel(const __g
                             if (A.status) A.status[inst] = CQK_BAD_ARG;
                         }
                     } else {
-                        bwd_instance<T, KIND, NOX, true>(A, gw, inst);
+                        bwd_instance<T, KIND, NOX, true, kBwdUGenBatched>(A, gw, inst);
                     }
                 }
                 continue;
@@ -614,7 +618,7 @@ __global__ void __launch_bounds__(NT, kMinBlocksPerSM) backward_kernel(const __g
                 continue;
             }
             if (staged) bwd_simplex_staged<T>(A, gp, sl.inst, reinterpret_cast<T*>(dyn_smem), bars, parity);
-            else bwd_instance<T, KIND, NOX>(A, gp, sl.inst);
+            else bwd_instance<T, KIND, NOX, false, kBwdUGenBatched>(A, gp, sl.inst);
         }
     }
 }
