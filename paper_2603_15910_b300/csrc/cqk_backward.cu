@@ -183,6 +183,104 @@ __device__ __noinline__ void bwd_map_exact(double g, double x, double b, double 
     }
 }
 
+// ---- the general adjoint per vector, shared by the register and the staged sweeps ---------
+
+// x_i at its lower bound (else at its upper one): x = l, and for a fixed variable (l = u) the
+// side of the bound on which (a + lambda b)/d lies
+template <typename T>
+__device__ __forceinline__ bool at_lower(const BwdArgs& A, int64_t e, T x, T l, T u, T b, T d, double lam) {
+    bool lower = eq_val<T>(x, l);
+    if (lower && eq_val<T>(l, u) && A.a) {
+        const double aj = (double)static_cast<const T*>(A.a)[e];
+        lower = (aj + lam * (double)b) / (double)d <= (double)l;
+    }
+    return lower;
+}
+
+// pass 1: sum_F b g/d and sum_F b^2/d over the free elements (fb) of one vector (double-float,
+// FP64 outside the df range)
+template <typename T>
+__device__ __forceinline__ void bwd_general_sums(unsigned fb, const T (&vg)[VecOf<T>::V], const T (&vb)[VecOf<T>::V],
+                                                 const T (&vd)[VecOf<T>::V], const bool (&ok)[VecOf<T>::V], LazyDf& Sl,
+                                                 LazyDf& Ql, double& S64, double& Q64) {
+    constexpr int V = VecOf<T>::V;
+    unsigned widem = 0;
+#pragma unroll
+    for (int j = 0; j < V; j++) {
+        if (!ok[j] || !((fb >> j) & 1u)) continue;
+        if (!(in_df_range<T>(vg[j]) && in_df_range<T>(vb[j]) && in_df_range<T>(vd[j]))) {
+            widem |= 1u << j;
+            continue;
+        }
+        const df G = to_df<T>(vg[j]), B = to_df<T>(vb[j]);
+        const df W = df_mul(B, inv_df(to_df<T>(vd[j])));
+        lazy_add(Sl, df_mul_lazy(W, G));
+        lazy_add(Ql, df_mul_lazy(W, B));
+    }
+    for (unsigned m = widem; m; m &= m - 1) {
+        const int j = __ffs(m) - 1;
+        bwd_sum_exact((double)pick(vg, j), 0.0, (double)pick(vb, j), (double)pick(vd, j), kBwdGeneral, S64, Q64);
+    }
+}
+
+// pass 2: the gradients of one vector (q: its global index), stored to every requested output
+template <typename T>
+__device__ __forceinline__ void bwd_general_grads(const BwdArgs& A, const Span& sp, int64_t q, bool aligned, unsigned fb,
+                                                  const T (&vg)[VecOf<T>::V], const T (&vx)[VecOf<T>::V],
+                                                  const T (&vb)[VecOf<T>::V], const T (&vd)[VecOf<T>::V],
+                                                  const T (&vl)[VecOf<T>::V], const T (&vu)[VecOf<T>::V],
+                                                  const bool (&ok)[VecOf<T>::V], bool need_lu, bool par_ok, df M, df Lm,
+                                                  double mu, double lam) {
+    constexpr int V = VecOf<T>::V;
+    T oa[V], ob[V], od[V], ol[V], ou[V];
+    unsigned widem = 0;
+#pragma unroll
+    for (int j = 0; j < V; j++) {
+        const bool fr = (fb >> j) & 1u;
+        oa[j] = ob[j] = od[j] = ol[j] = ou[j] = T(0);
+        if (!ok[j]) continue;
+        if (!(par_ok && in_df_range<T>(vg[j]) && in_df_range<T>(vx[j]) && in_df_range<T>(vb[j]) &&
+              in_df_range<T>(vd[j]))) {
+            widem |= 1u << j;
+            continue;
+        }
+        const df G = to_df<T>(vg[j]), B = to_df<T>(vb[j]), X = to_df<T>(vx[j]);
+        const df res = df_add(G, df_neg(df_mul(M, B)));
+        const df mx = df_mul(M, X);
+        if (fr) {
+            const df ga = df_mul(res, inv_df(to_df<T>(vd[j])));
+            oa[j] = from_df<T>(ga);
+            od[j] = from_df<T>(df_neg(df_mul(X, ga)));
+            ob[j] = from_df<T>(df_add(df_mul(Lm, ga), df_neg(mx)));
+        } else {
+            ob[j] = from_df<T>(df_neg(mx));
+            const bool lower = need_lu && at_lower<T>(A, q * V + j, vx[j], vl[j], vu[j], vb[j], vd[j], lam);
+            const T rv = from_df<T>(res);
+            ol[j] = lower ? rv : T(0);
+            ou[j] = lower ? T(0) : rv;
+        }
+    }
+    for (unsigned m = widem; m; m &= m - 1) {
+        const int j = __ffs(m) - 1;
+        const bool fr = (fb >> j) & 1u;
+        const bool lower = !fr && need_lu &&
+                           at_lower<T>(A, q * V + j, pick(vx, j), pick(vl, j), pick(vu, j), pick(vb, j), pick(vd, j), lam);
+        double o5[5];
+        bwd_map_exact((double)pick(vg, j), (double)pick(vx, j), (double)pick(vb, j), (double)pick(vd, j), fr, lower, mu,
+                      lam, kBwdGeneral, o5);
+        put(oa, j, (T)o5[0]);
+        put(ob, j, (T)o5[1]);
+        put(od, j, (T)o5[2]);
+        put(ol, j, (T)o5[3]);
+        put(ou, j, (T)o5[4]);
+    }
+    store_or<T>(A.ga, sp, q, aligned, oa);
+    store_or<T>(A.gb, sp, q, aligned, ob);
+    store_or<T>(A.gd, sp, q, aligned, od);
+    store_or<T>(A.gl, sp, q, aligned, ol);
+    store_or<T>(A.gu, sp, q, aligned, ou);
+}
+
 // one instance by one group (WARP: by one warp alone; gp.sp is the only field used).  NOX: the
 // simplex with the forward mask, where F comes from the mask and x is not read.
 template <typename T, int KIND, bool NOX, bool WARP = false, int UG = kBwdUGen>
@@ -238,35 +336,26 @@ __device__ __forceinline__ void bwd_instance(const BwdArgs& A, const Grp& gp, in
             for (int w = 0; w < U; w++) {
                 const int64_t q = base + w * 32 + lane;
                 const unsigned fb = free_bits<T, KIND>(A, q, mw[w], vx[w], vl[w], vu[w]);
+                if constexpr (KIND == kBwdGeneral) {
+                    bwd_general_sums<T>(fb, vg[w], vb[w], vd[w], ok[w], Sl, Ql, S64, Q64);
+                    continue;
+                }
                 unsigned widem = 0;
 #pragma unroll
                 for (int j = 0; j < V; j++) {
                     if (!ok[w][j] || !((fb >> j) & 1u)) continue;
-                    bool inr = in_df_range<T>(vg[w][j]);
-                    if (KIND == kBwdGeneral) inr = inr && in_df_range<T>(vb[w][j]) && in_df_range<T>(vd[w][j]);
-                    if (!inr) {
+                    if (!in_df_range<T>(vg[w][j])) {
                         widem |= 1u << j;
                         continue;
                     }
                     const df G = to_df<T>(vg[w][j]);
-                    if (KIND == kBwdGeneral) {
-                        const df B = to_df<T>(vb[w][j]);
-                        const df W = df_mul(B, inv_df(to_df<T>(vd[w][j])));
-                        lazy_add(Sl, df_mul_lazy(W, G));
-                        lazy_add(Ql, df_mul_lazy(W, B));
-                    } else if (KIND == kBwdSimplex) {
-                        lazy_add(Sl, G);
-                        nF++;
-                    } else {
-                        lazy_add(Sl, vx[w][j] > T(0) ? G : df_neg(G));
-                        nF++;
-                    }
+                    if (KIND == kBwdSimplex) lazy_add(Sl, G);
+                    else lazy_add(Sl, vx[w][j] > T(0) ? G : df_neg(G));
+                    nF++;
                 }
                 for (unsigned m = widem; m; m &= m - 1) {
                     const int j = __ffs(m) - 1;
-                    bwd_sum_exact((double)pick(vg[w], j), (double)pick(vx[w], j),
-                                  KIND == kBwdGeneral ? (double)pick(vb[w], j) : 1.0,
-                                  KIND == kBwdGeneral ? (double)pick(vd[w], j) : 1.0, KIND, S64, Q64);
+                    bwd_sum_exact((double)pick(vg[w], j), (double)pick(vx[w], j), 1.0, 1.0, KIND, S64, Q64);
                 }
             }
         }
@@ -316,84 +405,40 @@ __device__ __forceinline__ void bwd_instance(const BwdArgs& A, const Grp& gp, in
         for (int w = 0; w < U; w++) {
             const int64_t q = base + w * 32 + lane;
             const unsigned fb = inside ? ((1u << V) - 1u) : free_bits<T, KIND>(A, q, mw[w], vx[w], vl[w], vu[w]);
-            T oa[V], ob[V], od[V], ol[V], ou[V];
+            if constexpr (KIND == kBwdGeneral) {
+                bwd_general_grads<T>(A, sp, q, aligned, fb, vg[w], vx[w], vb[w], vd[w], vl[w], vu[w], ok[w], need_lu,
+                                     par_ok, M, Lm, mu, lam);
+                continue;
+            }
+            T oa[V];
             unsigned widem = 0;
 #pragma unroll
             for (int j = 0; j < V; j++) {
                 const bool fr = (fb >> j) & 1u;
-                oa[j] = ob[j] = od[j] = ol[j] = ou[j] = T(0);
+                oa[j] = T(0);
                 if (!ok[w][j]) continue;
                 if (KIND == kBwdL1 && inside) {
                     oa[j] = vg[w][j];
                     continue;
                 }
-                bool inr = par_ok && in_df_range<T>(vg[w][j]) && in_df_range<T>(vx[w][j]);
-                if (KIND == kBwdGeneral) inr = inr && in_df_range<T>(vb[w][j]) && in_df_range<T>(vd[w][j]);
-                if (!inr) {
+                if (!(par_ok && in_df_range<T>(vg[w][j]) && in_df_range<T>(vx[w][j]))) {
                     widem |= 1u << j;
                     continue;
                 }
-                const df G = to_df<T>(vg[w][j]);
-                if (KIND == kBwdGeneral) {
-                    const df B = to_df<T>(vb[w][j]), X = to_df<T>(vx[w][j]);
-                    const df res = df_add(G, df_neg(df_mul(M, B)));
-                    const df mx = df_mul(M, X);
-                    if (fr) {
-                        const df ga = df_mul(res, inv_df(to_df<T>(vd[w][j])));
-                        oa[j] = from_df<T>(ga);
-                        od[j] = from_df<T>(df_neg(df_mul(X, ga)));
-                        ob[j] = from_df<T>(df_add(df_mul(Lm, ga), df_neg(mx)));
-                    } else {
-                        ob[j] = from_df<T>(df_neg(mx));
-                        bool lower = false;
-                        if (need_lu) {
-                            lower = eq_val<T>(vx[w][j], vl[w][j]);
-                            if (lower && eq_val<T>(vl[w][j], vu[w][j]) && A.a) {
-                                // a fixed variable (l = u) is at its lower bound when (a + lambda b)/d <= l
-                                const double aj = (double)static_cast<const T*>(A.a)[q * V + j];
-                                lower = (aj + lam * (double)vb[w][j]) / (double)vd[w][j] <= (double)vl[w][j];
-                            }
-                        }
-                        const T rv = from_df<T>(res);
-                        ol[j] = lower ? rv : T(0);
-                        ou[j] = lower ? T(0) : rv;
-                    }
-                } else if (fr) {
+                if (fr) {
+                    const df G = to_df<T>(vg[w][j]);
                     const bool neg = KIND == kBwdL1 && vx[w][j] < T(0);
                     oa[j] = from_df<T>(df_add(G, neg ? M : df_neg(M)));
                 }
             }
             for (unsigned m = widem; m; m &= m - 1) {
                 const int j = __ffs(m) - 1;
-                const bool fr = (fb >> j) & 1u;
-                const T xj = pick(vx[w], j);
-                bool lower = false;
-                if (KIND == kBwdGeneral && !fr && need_lu) {
-                    const T lj = pick(vl[w], j), uj = pick(vu[w], j);
-                    lower = eq_val<T>(xj, lj);
-                    if (lower && eq_val<T>(lj, uj) && A.a) {
-                        const double aj = (double)static_cast<const T*>(A.a)[q * V + j];
-                        lower = (aj + lam * (double)pick(vb[w], j)) / (double)pick(vd[w], j) <= (double)lj;
-                    }
-                }
                 double o5[5];
-                bwd_map_exact((double)pick(vg[w], j), (double)xj, KIND == kBwdGeneral ? (double)pick(vb[w], j) : 1.0,
-                              KIND == kBwdGeneral ? (double)pick(vd[w], j) : 1.0, fr, lower, mu, lam, KIND, o5);
+                bwd_map_exact((double)pick(vg[w], j), (double)pick(vx[w], j), 1.0, 1.0, (fb >> j) & 1u, false, mu, lam,
+                              KIND, o5);
                 put(oa, j, (T)o5[0]);
-                if (KIND == kBwdGeneral) {
-                    put(ob, j, (T)o5[1]);
-                    put(od, j, (T)o5[2]);
-                    put(ol, j, (T)o5[3]);
-                    put(ou, j, (T)o5[4]);
-                }
             }
             store_or<T>(A.ga, sp, q, aligned, oa);
-            if (KIND == kBwdGeneral) {
-                store_or<T>(A.gb, sp, q, aligned, ob);
-                store_or<T>(A.gd, sp, q, aligned, od);
-                store_or<T>(A.gl, sp, q, aligned, ol);
-                store_or<T>(A.gu, sp, q, aligned, ou);
-            }
         }
     }
     if constexpr (WARP) {
