@@ -71,6 +71,12 @@ constexpr int kGenTileBytes = 16 * NT;
 constexpr int kGenU = 2;
 constexpr int kGenTileBytes = 32 * NT;
 #endif
+constexpr int kCheckAll = 0, kCheckBounds = 1, kChecked = 2;  // per-element checks of a pass (eval_vec)
+// The lambda_0 pass reads l and u too for FP64 data (their checks are integer work that the
+// first Newton pass would otherwise carry); for FP32 data it reads a, b, d only, in kL0Stages32
+// stages of the Newton passes' tile (their shared memory), and the first Newton pass checks l, u
+constexpr int kL0Stages32 = 3;
+constexpr int kRingBars = kL0Stages32 > kStages ? kL0Stages32 : kStages;  // mbarriers per block
 constexpr unsigned kFlagWide = 2u;  // some FP64 value lies outside the df operating range
 constexpr unsigned kFlagLuInf = 4u;  // some bound l_i or u_i is infinite
 // absf: sum |b_i x_i| of the Newton passes after the first, where it only scales the tolerance
@@ -224,6 +230,19 @@ __device__ __forceinline__ bool bad_elem_f(float a, float b, float d, float l, f
            (key(il) > key(iu) && ((il | iu) & 0x7FFFFFFF) != 0);
 }
 
+// the checks of bad_elem_f that concern l and u (NaN, l <= u), and those that concern a, b, d
+__device__ __forceinline__ bool bad_bounds_f(float l, float u) {
+    const int il = __float_as_int(l), iu = __float_as_int(u);
+    auto is_nan = [](int v) { return (v & 0x7FFFFFFF) > 0x7F800000; };
+    auto key = [](int v) { return v >= 0 ? v : (int)(0x80000000u - (unsigned)v) - 1; };
+    return is_nan(il) || is_nan(iu) || (key(il) > key(iu) && ((il | iu) & 0x7FFFFFFF) != 0);
+}
+__device__ __forceinline__ bool bad_abd_f(float a, float b, float d) {
+    const int ia = __float_as_int(a), ib = __float_as_int(b), id = __float_as_int(d);
+    auto pos_finite = [](int v) { return v > 0 && v < 0x7F800000; };
+    return !pos_finite(id) || !pos_finite(ib) || (ia & 0x7F800000) == 0x7F800000;
+}
+
 // ---- FP32 data -----------------------------------------------------------------------------
 // v = a + lambda b with lambda a float pair (TwoProd + TwoSum), rounded once; t = v/d by the
 // MUFU reciprocal and one correction (~1 ulp); the status is read off t against l, u with a
@@ -291,11 +310,13 @@ __device__ __forceinline__ T clamp_exact(T l, T x, T u) {
 // ---- the map of one 16-byte vector of elements (V of them): accumulate (write_x = false)
 // or write x / mask and the sums of the stored x.  q = global vector index, qw = index of the
 // warp's first vector (a multiple of 32).
-// FAST: every FP64 value is known to be valid and inside the df operating range (checked in
-// the first pass), so the per-element checks are skipped.
+// CK, the checks made per element: kCheckAll (every value: the sanity checks of Sec. 5.1.1 when
+// check, infinite bounds, the df operating range of FP64 values), kCheckBounds (a, b, d are
+// known valid and in range, checked by the lambda_0 pass: l and u only), kChecked (every value
+// known valid and in range: no check).
 // TIES: the tie band of the file header is tested (passes whose lambda may sit on a breakpoint:
 // the first, the final pass and those after a breakpoint step); otherwise the plain sign test.
-template <typename T, bool FAST, bool FIN, bool TIES, bool WX>
+template <typename T, int CK, bool FIN, bool TIES, bool WX>
 __device__ __forceinline__ void eval_vec(const GeneralArgs& A, const T (&va)[VecOf<T>::V], const T (&vb)[VecOf<T>::V],
                                          const T (&vd)[VecOf<T>::V], const T (&vl)[VecOf<T>::V],
                                          const T (&vu)[VecOf<T>::V], const bool (&ok)[VecOf<T>::V], int64_t q,
@@ -303,6 +324,7 @@ __device__ __forceinline__ void eval_vec(const GeneralArgs& A, const T (&va)[Vec
                                          const Span& sp) {
     constexpr int V = VecOf<T>::V;
     constexpr bool write_x = WX;
+    constexpr bool FAST = CK == kChecked;
     const bool aligned = A.aligned != 0;
     T* __restrict__ px = static_cast<T*>(A.x);
         T xo[V];
@@ -340,8 +362,9 @@ __device__ __forceinline__ void eval_vec(const GeneralArgs& A, const T (&va)[Vec
                     auto rng = [](unsigned h) { return (((h >> 20) & 0x7FFu) - 963u) <= 120u; };
                     auto zero = [](unsigned h, unsigned lo) { return ((h & 0x7FFFFFFFu) | lo) == 0u; };
                     auto inf = [](unsigned h, unsigned lo) { return (h & 0x7FFFFFFFu) == 0x7FF00000u && lo == 0u; };
-                    const bool inr = lam_ok && ((hb >> 20) - 963u) <= 120u && ((hd >> 20) - 963u) <= 120u &&
-                                     (rng(ha) || zero(ha, la)) && (rng(hl) || zero(hl, ll) || inf(hl, ll)) &&
+                    const bool abd = CK == kCheckBounds || (((hb >> 20) - 963u) <= 120u &&
+                                                            ((hd >> 20) - 963u) <= 120u && (rng(ha) || zero(ha, la)));
+                    const bool inr = lam_ok && abd && (rng(hl) || zero(hl, ll) || inf(hl, ll)) &&
                                      (rng(hu) || zero(hu, lu) || inf(hu, lu));
                     acc.luinf |= inf(hl, ll) || inf(hu, lu);
                     if (!inr) {
@@ -350,8 +373,8 @@ __device__ __forceinline__ void eval_vec(const GeneralArgs& A, const T (&va)[Vec
                         continue;
                     }
                     Ad = split_f64_finite(a);
-                    Bd = split_f64_finite(b);
-                    Dd = split_f64_finite(d);
+                    Bd = CK == kCheckBounds ? split_f64_pos(b) : split_f64_finite(b);
+                    Dd = CK == kCheckBounds ? split_f64_pos(d) : split_f64_finite(d);
                     Ld = split_f64(l);
                     Ud = split_f64(u);
                     if (check) acc.bad |= df_lt(Ud, Ld);
@@ -366,7 +389,8 @@ __device__ __forceinline__ void eval_vec(const GeneralArgs& A, const T (&va)[Vec
                     lazy_add(acc.absbx, bx.hi < 0.0f ? df_neg(bx) : bx);
                 }
             } else {
-                if (!FAST && check) acc.bad |= bad_elem_f(a, b, d, l, u);
+                if (CK == kCheckAll && check) acc.bad |= bad_elem_f(a, b, d, l, u);
+                if (CK == kCheckBounds && check) acc.bad |= bad_bounds_f(l, u);
                 if (!FAST) acc.luinf |= isinf(l) || isinf(u);
                 float bt;
                 xo[j] = elem_f32<FIN, TIES>(a, b, d, l, u, Lm, cl, bx, bt);
@@ -375,7 +399,7 @@ __device__ __forceinline__ void eval_vec(const GeneralArgs& A, const T (&va)[Vec
             fr[j] = cl.c == 0;
             if (!write_x) {
                 lazy_add(acc.phi, bx);
-                if constexpr (FAST) acc.absf += fabsf(bx.hi);  // (a tolerance scale: see EvalAcc)
+                if constexpr (CK != kCheckAll) acc.absf += fabsf(bx.hi);  // (a tolerance scale: see EvalAcc)
                 else lazy_add(acc.absbx, bx.hi < 0.0f ? df_neg(bx) : bx);
                 lazy_add(acc.sfree, fr[j] ? beta[j] : df_make(0.0f));
             }
@@ -453,7 +477,7 @@ __device__ __forceinline__ void eval_vec(const GeneralArgs& A, const T (&va)[Vec
 }
 
 // ---- one pass over all elements with plain loads (arrays not 16-byte aligned)
-template <typename T, bool FAST, bool FIN, bool TIES, bool WX>
+template <typename T, int CK, bool FIN, bool TIES, bool WX>
 __device__ __forceinline__ void eval_pass_plain(const GeneralArgs& A, const Grp& gp, double lam, bool check, bool rev,
                                                 EvalAcc& acc) {
     constexpr int V = VecOf<T>::V;
@@ -489,7 +513,7 @@ __device__ __forceinline__ void eval_pass_plain(const GeneralArgs& A, const Grp&
         }
 #pragma unroll
         for (int w = 0; w < U; w++)
-            eval_vec<T, FAST, FIN, TIES, WX>(A, va[w], vb[w], vd[w], vl[w], vu[w], ok[w], base + w * 32 + lane,
+            eval_vec<T, CK, FIN, TIES, WX>(A, va[w], vb[w], vd[w], vl[w], vu[w], ok[w], base + w * 32 + lane,
                                              base + w * 32, lam, Lm, lam_ok, check, acc, sp);
     }
 }
@@ -498,7 +522,7 @@ __device__ __forceinline__ void eval_pass_plain(const GeneralArgs& A, const Grp&
 template <typename T>
 __host__ __device__ constexpr int stage_tile() { return kGenTileBytes / (int)sizeof(T); }  // elements per array per stage
 
-template <typename T, bool FAST, bool FIN, bool TIES, bool WX>
+template <typename T, int CK, bool FIN, bool TIES, bool WX>
 __device__ __forceinline__ bool eval_pass_staged(const GeneralArgs& A, const Grp& gp, double lam, bool check,
                                                  bool rev, EvalAcc& acc, T* smem, uint64_t* bars, unsigned& parity,
                                                  int* err) {
@@ -555,7 +579,7 @@ __device__ __forceinline__ bool eval_pass_staged(const GeneralArgs& A, const Grp
                 load_vec<T>(src[3], sp, q, false, vl, ok);
                 load_vec<T>(src[4], sp, q, false, vu, ok);
             }
-            eval_vec<T, FAST, FIN, TIES, WX>(A, va, vb, vd, vl, vu, ok, q, qw, lam, Lm, lam_ok, check, acc, sp);
+            eval_vec<T, CK, FIN, TIES, WX>(A, va, vb, vd, vl, vu, ok, q, qw, lam, Lm, lam_ok, check, acc, sp);
         }
         __syncthreads();  // the stage is refilled only after every thread has read it
     }
@@ -565,11 +589,11 @@ __device__ __forceinline__ bool eval_pass_staged(const GeneralArgs& A, const Grp
 
 // one pass over all elements, staged or plain; WX: the final pass (write x, the mask and the
 // sums of the stored x) instead of the accumulation of phi and its slopes
-template <typename T, bool WX, bool FAST, bool FIN = false, bool TIES = true>
+template <typename T, bool WX, int CK, bool FIN = false, bool TIES = true>
 __device__ __forceinline__ bool eval_pass(const GeneralArgs& A, const Grp& gp, double lam, bool check, bool rev,
                                           EvalAcc& acc, T* smem, uint64_t* bars, unsigned& parity, int* err) {
-    if (A.staged) return eval_pass_staged<T, FAST, FIN, TIES, WX>(A, gp, lam, check, rev, acc, smem, bars, parity, err);
-    eval_pass_plain<T, FAST, FIN, TIES, WX>(A, gp, lam, check, rev, acc);
+    if (A.staged) return eval_pass_staged<T, CK, FIN, TIES, WX>(A, gp, lam, check, rev, acc, smem, bars, parity, err);
+    eval_pass_plain<T, CK, FIN, TIES, WX>(A, gp, lam, check, rev, acc);
     return true;
 }
 
@@ -652,8 +676,8 @@ __device__ __forceinline__ void lambda0_vec(const T (&va)[VecOf<T>::V], const T 
             exact |= (inr ? 0u : 1u) << j;
             wide |= (inr && lur ? 0u : 1u) << j;
         } else {
-            if (check) fl.bad |= bad_elem_f(a, b, d, l, u);
-            fl.luinf |= isinf(l) || isinf(u);
+            // (FP32: l and u are checked by the first Newton pass)
+            if (check) fl.bad |= bad_abd_f(a, b, d);
             const float rd = rcp_approx(d);
             float wgt = __fmul_rn(b, rd);
             wgt = fmaf(fmaf(-wgt, d, b), rd, wgt);
@@ -687,6 +711,7 @@ __device__ __forceinline__ bool lambda0_pass(const GeneralArgs& A, const Grp& gp
     const T* __restrict__ pd = static_cast<const T*>(A.d);
     const T* __restrict__ pl = static_cast<const T*>(A.l);
     const T* __restrict__ pu = static_cast<const T*>(A.u);
+    constexpr bool LU0 = sizeof(T) == 8;  // l and u are read here (FP64 data)
     const Span sp = gp.sp;
     LazyDf s{0.0f, 0.0f}, q{0.0f, 0.0f};
     double s64 = 0.0, q64 = 0.0;
@@ -694,17 +719,20 @@ __device__ __forceinline__ bool lambda0_pass(const GeneralArgs& A, const Grp& gp
     if (A.staged) {
         constexpr int TT = stage_tile<T>();
         constexpr int VPT = TT / V / NT;
+        constexpr int NA = LU0 ? 5 : 3;                   // arrays read
+        constexpr int NS = LU0 ? kStages : kL0Stages32;  // stages (the same shared memory)
+        static_assert(NA * NS <= 5 * kStages, "the lambda_0 stages fit the Newton passes' shared memory");
         using VT = typename VecOf<T>::type;
         const T* src[5] = {pa, pb, pd, pl, pu};
-        TileRing<T, 5, TT> ring;
+        TileRing<T, NA, TT> ring;
         ring.setup(sp.lo, sp.hi, smem, bars, gp.member, gp.g);
         ring.parity = parity;
-        for (int st = 0; st < kStages - 1; st++)
+        for (int st = 0; st < NS - 1; st++)
             if (st < ring.count) ring.issue_by_warps(ring.tile(st, false), st, src);
         for (int64_t i = 0; i < ring.count; i++) {
-            const int st = (int)(i % kStages);
-            if (i + kStages - 1 < ring.count)
-                ring.issue_by_warps(ring.tile(i + kStages - 1, false), (int)((i + kStages - 1) % kStages), src);
+            const int st = (int)(i % NS);
+            if (i + NS - 1 < ring.count)
+                ring.issue_by_warps(ring.tile(i + NS - 1, false), (int)((i + NS - 1) % NS), src);
             if (!mbar_wait(&ring.bar[st], (ring.parity >> st) & 1u, err, A.limit_ns, CQK_TIMEOUT)) okw = false;
             ring.parity ^= 1u << st;
             const int64_t c = ring.tile(i, false);
@@ -724,23 +752,31 @@ __device__ __forceinline__ bool lambda0_pass(const GeneralArgs& A, const Grp& gp
                     const VT wa = reinterpret_cast<const VT*>(ring.stage(st, 0))[ql];
                     const VT wb = reinterpret_cast<const VT*>(ring.stage(st, 1))[ql];
                     const VT wd = reinterpret_cast<const VT*>(ring.stage(st, 2))[ql];
-                    const VT wl = reinterpret_cast<const VT*>(ring.stage(st, 3))[ql];
-                    const VT wu = reinterpret_cast<const VT*>(ring.stage(st, 4))[ql];
+                    VT wl, wu;
+                    if constexpr (LU0) {
+                        wl = reinterpret_cast<const VT*>(ring.stage(st, LU0 ? 3 : 0))[ql];
+                        wu = reinterpret_cast<const VT*>(ring.stage(st, LU0 ? 4 : 0))[ql];
+                    }
 #pragma unroll
                     for (int j = 0; j < V; j++) {
                         va[j] = reinterpret_cast<const T*>(&wa)[j];
                         vb[j] = reinterpret_cast<const T*>(&wb)[j];
                         vd[j] = reinterpret_cast<const T*>(&wd)[j];
-                        vl[j] = reinterpret_cast<const T*>(&wl)[j];
-                        vu[j] = reinterpret_cast<const T*>(&wu)[j];
+                        vl[j] = LU0 ? reinterpret_cast<const T*>(&wl)[j] : T(0);
+                        vu[j] = LU0 ? reinterpret_cast<const T*>(&wu)[j] : T(0);
                         ok[j] = true;
                     }
                 } else {
                     load_vec<T>(pa, sp, qg, false, va, ok);
                     load_vec<T>(pb, sp, qg, false, vb, ok);
                     load_vec<T>(pd, sp, qg, false, vd, ok);
-                    load_vec<T>(pl, sp, qg, false, vl, ok);
-                    load_vec<T>(pu, sp, qg, false, vu, ok);
+                    if constexpr (LU0) {
+                        load_vec<T>(pl, sp, qg, false, vl, ok);
+                        load_vec<T>(pu, sp, qg, false, vu, ok);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < V; j++) vl[j] = vu[j] = T(0);
+                    }
                 }
                 lambda0_vec<T>(va, vb, vd, vl, vu, ok, s, q, s64, q64, check, fl);
             }
@@ -767,8 +803,13 @@ __device__ __forceinline__ bool lambda0_pass(const GeneralArgs& A, const Grp& gp
                 load_vec<T>(pa, sp, base + w * 32 + lane, A.aligned != 0, va[w], ok[w]);
                 load_vec<T>(pb, sp, base + w * 32 + lane, A.aligned != 0, vb[w], ok[w]);
                 load_vec<T>(pd, sp, base + w * 32 + lane, A.aligned != 0, vd[w], ok[w]);
-                load_vec<T>(pl, sp, base + w * 32 + lane, A.aligned != 0, vl[w], ok[w]);
-                load_vec<T>(pu, sp, base + w * 32 + lane, A.aligned != 0, vu[w], ok[w]);
+                if constexpr (LU0) {
+                    load_vec<T>(pl, sp, base + w * 32 + lane, A.aligned != 0, vl[w], ok[w]);
+                    load_vec<T>(pu, sp, base + w * 32 + lane, A.aligned != 0, vu[w], ok[w]);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < V; j++) vl[w][j] = vu[w][j] = T(0);
+                }
             }
 #pragma unroll
             for (int w = 0; w < U; w++)
@@ -870,7 +911,7 @@ __device__ __forceinline__ void general_solve(const GeneralArgs& A, const Grp& g
     if (A.phi_only) {  // cqk_phi: one evaluation at A.lambda0 (and x when requested)
         EvalAcc acc;
         acc.init();
-        eval_pass<T, false, false>(A, gp, A.lambda0, false, false, acc, smem, ring_bars, ring_parity, err);
+        eval_pass<T, false, kCheckAll>(A, gp, A.lambda0, false, false, acc, smem, ring_bars, ring_parity, err);
         acc.flush();
         double pv[3] = {acc.phi64, acc.sfree64, acc.absbx64};
         double pt[2] = {acc.satl, acc.satu};
@@ -883,7 +924,7 @@ __device__ __forceinline__ void general_solve(const GeneralArgs& A, const Grp& g
         if (A.x) {
             EvalAcc acc2;
             acc2.init();
-            eval_pass<T, true, false>(A, gp, A.lambda0, false, true, acc2, smem, ring_bars, ring_parity, err);
+            eval_pass<T, true, kCheckAll>(A, gp, A.lambda0, false, true, acc2, smem, ring_bars, ring_parity, err);
         }
         double dummy[1] = {0.0}, tot[1];
         if (last_block_sums<1>(gp.part, gp.member, G, &gp.hdr->ticket, dummy, tot, sh)) {
@@ -903,9 +944,10 @@ __device__ __forceinline__ void general_solve(const GeneralArgs& A, const Grp& g
     double lam0 = A.lambda0;
     int status = CQK_OK;
     bool bad_input = false;
-    bool checked = false;   // the lambda_0 pass has checked the data
-    bool wide_data = true;  // until a pass has checked every value
-    bool fin_data = false;  // every bound finite (known once the data are checked)
+    bool checked = false;      // the lambda_0 pass has checked the data (FP64)
+    bool abd_checked = false;  // the lambda_0 pass has checked a, b, d (FP32): the first pass checks l, u
+    bool wide_data = true;     // until a pass has checked every value
+    bool fin_data = false;     // every bound finite (known once the data are checked)
     if (A.init == CQK_INIT_FORMULA) {
         double s, q;
         DataFlags fl{false, false, false};
@@ -923,9 +965,13 @@ __device__ __forceinline__ void general_solve(const GeneralArgs& A, const Grp& g
         lam0 = (r - red[0]) / red[1];  // eq. (CQKlambda0), J = all variables
         passes++;
         const unsigned fls = __ldcg(&gp.hdr->flags);
-        checked = true;
-        wide_data = (fls & kFlagWide) != 0;
-        fin_data = (fls & kFlagLuInf) == 0;
+        if constexpr (sizeof(T) == 8) {
+            checked = true;
+            wide_data = (fls & kFlagWide) != 0;
+            fin_data = (fls & kFlagLuInf) == 0;
+        } else {
+            abd_checked = true;
+        }
         if (A.validate && (fls & kFlagBadInput)) {
             bad_input = true;
             status = CQK_BAD_INPUT;
@@ -973,16 +1019,20 @@ __device__ __forceinline__ void general_solve(const GeneralArgs& A, const Grp& g
         // the checked fast path: every value valid and in the df range, and |lambda| <= 2^60
         const bool fast = !first && !wide_data && fabs(lam) <= 1.152921504606847e18;
         if (fast && fin_data && !lam_on_bp)
-            eval_pass<T, false, true, true, false>(A, gp, lam, false, rev, acc, smem, ring_bars, ring_parity, err);
+            eval_pass<T, false, kChecked, true, false>(A, gp, lam, false, rev, acc, smem, ring_bars, ring_parity, err);
         else if (fast && fin_data)
-            eval_pass<T, false, true, true, true>(A, gp, lam, false, rev, acc, smem, ring_bars, ring_parity, err);
+            eval_pass<T, false, kChecked, true, true>(A, gp, lam, false, rev, acc, smem, ring_bars, ring_parity, err);
         else if (fast && !lam_on_bp)
-            eval_pass<T, false, true, false, false>(A, gp, lam, false, rev, acc, smem, ring_bars, ring_parity, err);
+            eval_pass<T, false, kChecked, false, false>(A, gp, lam, false, rev, acc, smem, ring_bars, ring_parity, err);
         else if (fast)
-            eval_pass<T, false, true, false, true>(A, gp, lam, false, rev, acc, smem, ring_bars, ring_parity, err);
+            eval_pass<T, false, kChecked, false, true>(A, gp, lam, false, rev, acc, smem, ring_bars, ring_parity, err);
+        else if (sizeof(T) == 4 && first && abd_checked && !lam_on_bp)
+            eval_pass<T, false, kCheckBounds, false, false>(A, gp, lam, chk, rev, acc, smem, ring_bars, ring_parity, err);
+        else if (sizeof(T) == 4 && first && abd_checked)
+            eval_pass<T, false, kCheckBounds, false, true>(A, gp, lam, chk, rev, acc, smem, ring_bars, ring_parity, err);
         else if (!lam_on_bp)
-            eval_pass<T, false, false, false, false>(A, gp, lam, chk, rev, acc, smem, ring_bars, ring_parity, err);
-        else eval_pass<T, false, false, false, true>(A, gp, lam, chk, rev, acc, smem, ring_bars, ring_parity, err);
+            eval_pass<T, false, kCheckAll, false, false>(A, gp, lam, chk, rev, acc, smem, ring_bars, ring_parity, err);
+        else eval_pass<T, false, kCheckAll, false, true>(A, gp, lam, chk, rev, acc, smem, ring_bars, ring_parity, err);
         acc.flush();
         passes++;
         if (__any_sync(0xffffffffu, acc.bad) && (threadIdx.x & 31) == 0) atomicOr(&gp.hdr->flags, kFlagBadInput);
@@ -1151,14 +1201,14 @@ __device__ __forceinline__ void general_solve(const GeneralArgs& A, const Grp& g
         const bool rev = (k & 1) == 1;
         const bool fast = !wide_data && fabs(final_lam) <= 1.152921504606847e18;  // (as in the Newton passes)
         if (fast && fin_data && !ties)
-            eval_pass<T, true, true, true, false>(A, gp, final_lam, false, rev, acc, smem, ring_bars, ring_parity, err);
+            eval_pass<T, true, kChecked, true, false>(A, gp, final_lam, false, rev, acc, smem, ring_bars, ring_parity, err);
         else if (fast && fin_data)
-            eval_pass<T, true, true, true, true>(A, gp, final_lam, false, rev, acc, smem, ring_bars, ring_parity, err);
+            eval_pass<T, true, kChecked, true, true>(A, gp, final_lam, false, rev, acc, smem, ring_bars, ring_parity, err);
         else if (fast && !ties)
-            eval_pass<T, true, true, false, false>(A, gp, final_lam, false, rev, acc, smem, ring_bars, ring_parity, err);
+            eval_pass<T, true, kChecked, false, false>(A, gp, final_lam, false, rev, acc, smem, ring_bars, ring_parity, err);
         else if (fast)
-            eval_pass<T, true, true, false, true>(A, gp, final_lam, false, rev, acc, smem, ring_bars, ring_parity, err);
-        else eval_pass<T, true, false>(A, gp, final_lam, false, rev, acc, smem, ring_bars, ring_parity, err);
+            eval_pass<T, true, kChecked, false, true>(A, gp, final_lam, false, rev, acc, smem, ring_bars, ring_parity, err);
+        else eval_pass<T, true, kCheckAll>(A, gp, final_lam, false, rev, acc, smem, ring_bars, ring_parity, err);
         passes++;
     }
     acc.flush();
@@ -1186,11 +1236,11 @@ __device__ __forceinline__ void general_solve(const GeneralArgs& A, const Grp& g
 template <typename T>
 __global__ void __launch_bounds__(NT, kMinBlocksPerSM) general_kernel(const __grid_constant__ GeneralArgs A) {
     extern __shared__ __align__(128) unsigned char dyn_smem[];
-    __shared__ uint64_t ring_bars[kStages];
+    __shared__ uint64_t ring_bars[kRingBars];
     unsigned ring_parity = 0;
     if (A.staged) {
         if (threadIdx.x == 0) {
-            for (int st = 0; st < kStages; st++) mbar_init(&ring_bars[st], 1);
+            for (int st = 0; st < kRingBars; st++) mbar_init(&ring_bars[st], 1);
             fence_barrier_init();
         }
         __syncthreads();
@@ -1220,11 +1270,11 @@ struct GeneralBatchArgs {
 template <typename T>
 __global__ void __launch_bounds__(NT, kMinBlocksPerSM) general_batched_kernel(const __grid_constant__ GeneralBatchArgs P) {
     extern __shared__ __align__(128) unsigned char dyn_smem[];
-    __shared__ uint64_t ring_bars[kStages];
+    __shared__ uint64_t ring_bars[kRingBars];
     unsigned ring_parity = 0;
     if (P.base.staged) {
         if (threadIdx.x == 0) {
-            for (int st = 0; st < kStages; st++) mbar_init(&ring_bars[st], 1);
+            for (int st = 0; st < kRingBars; st++) mbar_init(&ring_bars[st], 1);
             fence_barrier_init();
         }
         __syncthreads();
