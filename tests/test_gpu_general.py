@@ -157,6 +157,30 @@ def test_infeasible_and_bad_input():
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 @pytest.mark.parametrize("init", ["formula", "given"])
+def test_bad_input_in_every_array(dtype, init):
+    # the sanity checks of Sec. 5.1.1 reject a NaN in any array, d <= 0, b <= 0 and l > u,
+    # whichever pass makes them (the lambda_0 pass, or the first Newton pass for l and u of FP32
+    # data and for a given start); elements past the first tiles exercise every block's checks
+    base = W.uncorrelated_box(20011, seed=31)
+    cases = [("a", 17, float("nan")), ("b", 4001, float("nan")), ("d", 9000, float("nan")),
+             ("l", 12345, float("nan")), ("u", 20010, float("nan")), ("d", 3, 0.0), ("d", 777, -2.0),
+             ("b", 15000, -1.0), ("b", 6, 0.0)]
+    for key, i, val in cases:
+        h = {k: v.clone() if torch.is_tensor(v) else v for k, v in base.items()}
+        h[key][i] = val
+        p = _dev(h, dtype)
+        kw = {} if init == "formula" else dict(init=api.Init.GIVEN, lambda0=0.1)
+        _, info, _ = api.solve(p["a"], p["b"], p["d"], p["l"], p["u"], p["r"], **kw)
+        assert info.status == api.Status.BAD_INPUT, (key, i, val, info)
+    h = {k: v.clone() if torch.is_tensor(v) else v for k, v in base.items()}
+    h["l"][11111] = h["u"][11111] + 0.5
+    p = _dev(h, dtype)
+    _, info, _ = api.solve(p["a"], p["b"], p["d"], p["l"], p["u"], p["r"])
+    assert info.status == api.Status.BAD_INPUT, info
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("init", ["formula", "given"])
 def test_signed_zero_bounds_are_valid(dtype, init):
     # l = +0, u = -0 satisfies l <= u (IEEE: the two zeros are equal), so the sanity check of
     # Sec. 5.1.1 passes and x_i = 0; also with an element outside the double-float range,
