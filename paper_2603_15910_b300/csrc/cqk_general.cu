@@ -79,10 +79,10 @@ constexpr int kL0Stages32 = 3;
 constexpr int kRingBars = kL0Stages32 > kStages ? kL0Stages32 : kStages;  // mbarriers per block
 constexpr unsigned kFlagWide = 2u;  // some FP64 value lies outside the df operating range
 constexpr unsigned kFlagLuInf = 4u;  // some bound l_i or u_i is infinite
-// absf: sum |b_i x_i| of the Newton passes after the first, where it only scales the tolerance
+// absf: sum |b_i x_i| of the Newton passes on checked data, where it only scales the tolerance
 // of stopping criterion 1: summed in float between flushes (relative error below 2^-19 with
-// kFlushEvery tiles of 4 elements per thread).  The stand-alone phi evaluation, the first
-// pass and the final pass (the reported sum) keep the double-float sum.
+// kFlushEvery tiles of 4 elements per thread).  The stand-alone phi evaluation, a pass that
+// makes the full data checks and the final pass (the reported sum) keep the double-float sum.
 struct EvalAcc {
     LazyDf phi, absbx, sfree;
     df mphi, mabsbx, msfree;  // middle level: normalised df sums of the flushed lazy sums
