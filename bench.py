@@ -326,6 +326,22 @@ def _max_err(items):
     return out
 
 
+def job_totals(ms, units, world, device=None):
+    """Whole-job figures of a timed region run by every rank: the longest rank's time (the job
+    ends when its slowest rank does) and the units of work summed over the ranks (each rank
+    projects its own vector, so their Newton iteration counts may differ).  Called by every
+    rank after the closing barrier; with world == 1 it returns its arguments."""
+    if world <= 1:
+        return ms, units
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 # ------------------------------------------------------------------------------ our arm
 def run_ours(args, world, rank, local):
     import torch
@@ -377,15 +393,11 @@ def run_ours(args, world, rank, local):
         torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    ms = t0.elapsed_time(t1)
-    if world > 1:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
     t_s = sum(e[0].elapsed_time(e[1]) for e in evs) / K
     t_l = sum(e[1].elapsed_time(e[2]) for e in evs) / K
     iters = i1.iters + i2.iters
-    value = world * n * iters * K / (ms * 1e-3)
+    ms, units = job_totals(t0.elapsed_time(t1), n * iters * K, world, dev)
+    value = units / (ms * 1e-3)
 
     # roofline of the projection kernel (both launches of the step), live CUDA events
     bytes_s = algorithmic_bytes_projection(n, 8, i1)
@@ -478,12 +490,8 @@ def run_ours(args, world, rank, local):
         e2e_step(k)
     e1.record(s_out)  # after the last copy out (it follows every earlier one on its stream)
     torch.cuda.synchronize()
-    ems = e0.elapsed_time(e1)
-    if world > 1:
-        tt = torch.tensor([ems], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ems = float(tt.item())
-    out["e2e"] = {"value": world * n * iters * Ke / (ems * 1e-3), "unit": UNIT, "h2d_bytes_per_step": 8 * n,
+    ems, e_units = job_totals(e0.elapsed_time(e1), n * iters * Ke, world, dev)
+    out["e2e"] = {"value": e_units / (ems * 1e-3), "unit": UNIT, "h2d_bytes_per_step": 8 * n,
                   "d2h_bytes_per_step": 16 * n, "ms_per_step": ems / Ke,
                   "overlap": "copy in, compute and copy out on three streams, double-buffered"}
     del y_host, xh1, xh2, yd, xo1, xo2
